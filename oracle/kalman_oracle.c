@@ -1,0 +1,387 @@
+/*
+ * FP64 CPU ORACLE for the batched TPC Kalman track fit.  TEST INFRASTRUCTURE:
+ * only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load it.  It shares no code with the CUDA library.
+ *
+ * What it computes.  The paper (Eulisse & Rohr, Sec. 5 and Sec. 6) places full
+ * TPC tracking on the GPU as the dominant synchronous step (Table 1) and the
+ * dominant asynchronous step (Table 2), but it does not write out the fit.  The
+ * fit below is the textbook Kalman filter (Kalman 1960) applied to track
+ * fitting (Fruhwirth 1987, NIM A262 444), with an exact helix in a uniform
+ * solenoid field and PDG Highland multiple scattering, in the local frame of a
+ * TPC sector:
+ *   state p = (y, z, sinphi, tanlambda, q/pT) on the plane of constant x,
+ *   covariance C (5x5), measurement H = [I2 0], V = diag(sy2, sz2).
+ * Plain and slow on purpose: full 5x5 matrices, explicit products, explicit
+ * inverse, one track at a time (a track range per thread).
+ *
+ * Readings where the paper is silent (all listed in the design notes):
+ *   curvature C = -kB*Bz*(q/pT); seed = circle through clusters 0, n/2, n-1;
+ *   seed covariance diag(1,1,0.01,0.01,1); chi2 gate 16 (equality accepts);
+ *   |sinphi| limit 0.999; MS after the (possible) update at every crossed row;
+ *   inward pass restarts from the outward state with a diagonal covariance:
+ *   the outward variances times restart_scale (100), capped at the seed's;
+ *   outputs at the innermost cluster.
+ * Status rule: clusters are validated when the outward pass reaches them, so the
+ * first offending cluster decides; NaN never trips a numerical limit (it flows
+ * to that cluster), and a completed fit with a non-finite state or covariance
+ * is marked NONFINITE.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_KB 0.299792458e-2 /* GeV / (cm T) */
+
+enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5 };
+
+typedef struct {
+  double bz;            /* Tesla */
+  double chi2_max;      /* gate on the 2-dof chi2 of one cluster */
+  double xx0;           /* x/X0 per crossed pad row (0: no scattering) */
+  double mass;          /* GeV, for beta in the Highland formula */
+  double snp_max;       /* |sinphi| limit */
+  double seed_cov[5];   /* diagonal of the seed covariance (also caps the restart covariance) */
+  int32_t min_clusters;
+  int32_t n_rows;
+  const float *row_x;   /* n_rows pad-row plane positions (cm) */
+  double restart_scale; /* inward restart covariance: diag(min(restart_scale * C_out_ii, seed_cov_i)) */
+} orc_config;
+
+typedef struct {
+  double *state;  /* nt*5 */
+  double *cov;    /* nt*15 packed lower triangle (00,10,11,20,...,44) */
+  double *x_ref;  /* nt */
+  double *chi2;   /* nt */
+  int32_t *ndf;   /* nt */
+  int32_t *status;/* nt */
+  uint8_t *accept;/* nc: bit0 outward, bit1 inward */
+  /* optional per-cluster diagnostics (may be NULL) */
+  double *chi2_out_c;  /* nc: chi2 of the cluster in the outward pass (NaN if not reached) */
+  double *chi2_in_c;   /* nc: chi2 of the cluster in the inward pass */
+  double *state_in_c;  /* nc*5: inward state after the cluster's update, before its scattering */
+  double *state_out_t; /* nt*5: outward state the inward pass restarts from */
+  double *restart_t;   /* nt*5: diagonal of the covariance the inward pass restarts with */
+} orc_result;
+
+/* ---------------------------------------------------------------------------
+ * Propagation of the state from plane x1 to plane x2 along the exact helix.
+ * d(sinphi)/dx = C, so sinphi2 = sinphi1 + C dx; y2 - y1 = (r1 - r2)/C written
+ * in the cancellation-free form dx (s1+s2)/(r1+r2); z advances by tanlambda
+ * times the transverse arc length s = L asin(CL/2)/(CL/2), L the chord.
+ * F receives the Jacobian d p2 / d p1 (row-major 5x5), derived analytically.
+ * Returns 0, or ST_SNP_LIMIT if |sinphi1| or |sinphi2| >= snp_max.
+ * ------------------------------------------------------------------------- */
+static double asin_over_u(double u) {
+  /* asin(u)/u, power series near 0 */
+  if (fabs(u) < 1e-3) { double u2 = u * u; return 1.0 + u2 * (1.0 / 6.0 + u2 * (3.0 / 40.0 + u2 * (5.0 / 112.0))); }
+  return asin(u) / u;
+}
+static double dsdc_over_l2u(double u) {
+  /* (1/sqrt(1-u^2) - asin(u)/u) / (2 u^2)  ==  d s / d C divided by L^2 u,
+     series near 0: 1/6 + 3/20 u^2 + 15/112 u^4 + ... */
+  if (fabs(u) < 1e-2) { double u2 = u * u; return 1.0 / 6.0 + u2 * (3.0 / 20.0 + u2 * (15.0 / 112.0 + u2 * (35.0 / 288.0))); }
+  return (1.0 / sqrt(1.0 - u * u) - asin(u) / u) / (2.0 * u * u);
+}
+
+int orc_propagate(const double p1[5], double x1, double x2, double bz, double snp_max, double p2[5], double F[25]) {
+  const double b = -ORC_KB * bz; /* dC/dw */
+  double dx = x2 - x1;
+  double C = b * p1[4];
+  double s1 = p1[2], s2 = s1 + C * dx;
+  /* NaN passes (it is reported where the pass meets the offending input) */
+  if (fabs(s1) >= snp_max || fabs(s2) >= snp_max) return ST_SNP_LIMIT;
+  double r1 = sqrt(1.0 - s1 * s1), r2 = sqrt(1.0 - s2 * s2);
+  double T = (s1 + s2) / (r1 + r2);     /* tan of the mean chord direction */
+  double k = sqrt(1.0 + T * T);
+  double L = dx * k;                    /* signed chord length */
+  double u = 0.5 * C * L;
+  double g = asin_over_u(u);
+  double sT = L * g;                    /* signed transverse arc length */
+  p2[0] = p1[0] + dx * T;
+  p2[1] = p1[1] + p1[3] * sT;
+  p2[2] = s2;
+  p2[3] = p1[3];
+  p2[4] = p1[4];
+  /* Jacobian */
+  double Q = (1.0 + r1 * r2 + s1 * s2) / ((r1 + r2) * (r1 + r2));
+  double dT_ds1 = Q * (1.0 / r1 + 1.0 / r2);       /* includes d s2 / d s1 = 1 */
+  double dT_dw = Q / r2 * (b * dx);                 /* via s2 only */
+  double dL_dT = dx * T / k;
+  double ds_dL = 1.0 / sqrt(1.0 - u * u);
+  double ds_dC = L * L * u * dsdc_over_l2u(u);
+  for (int i = 0; i < 25; ++i) F[i] = 0.0;
+  for (int i = 0; i < 5; ++i) F[i * 5 + i] = 1.0;
+  F[0 * 5 + 2] = dx * dT_ds1;
+  F[0 * 5 + 4] = dx * dT_dw;
+  F[1 * 5 + 2] = p1[3] * ds_dL * dL_dT * dT_ds1;
+  F[1 * 5 + 3] = sT;
+  F[1 * 5 + 4] = p1[3] * (ds_dL * dL_dT * dT_dw + ds_dC * b);
+  F[2 * 5 + 4] = b * dx;
+  return ST_OK;
+}
+
+/* C <- F C F^T, plain 5x5 products. */
+static void cov_transport(double C[25], const double F[25]) {
+  double FC[25], R[25];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 5; ++k) s += F[i * 5 + k] * C[k * 5 + j];
+      FC[i * 5 + j] = s;
+    }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 5; ++k) s += FC[i * 5 + k] * F[j * 5 + k];
+      R[i * 5 + j] = s;
+    }
+  memcpy(C, R, sizeof(R));
+}
+
+/* ---------------------------------------------------------------------------
+ * Kalman update with one (y, z) cluster: S = H C H^T + V, chi2 = r^T S^-1 r,
+ * accept iff chi2 <= chi2_max; then K = C H^T S^-1, p += K r, C -= K (H C),
+ * symmetrised.  Returns 0 or ST_NOT_PD (S not positive definite).
+ * ------------------------------------------------------------------------- */
+int orc_update(double p[5], double C[25], double yc, double zc, double sy2, double sz2, double chi2_max,
+               double *chi2_out, int *accepted) {
+  double S00 = C[0] + sy2, S01 = C[1], S11 = C[6] + sz2;
+  double det = S00 * S11 - S01 * S01;
+  *accepted = 0;
+  if (det <= 0.0 || S00 <= 0.0) { *chi2_out = NAN; return ST_NOT_PD; } /* NaN passes, chi2 NaN is rejected */
+  double Si00 = S11 / det, Si01 = -S01 / det, Si11 = S00 / det;
+  double r0 = yc - p[0], r1 = zc - p[1];
+  double chi2 = r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1);
+  *chi2_out = chi2;
+  if (!(chi2 <= chi2_max)) return ST_OK;
+  double K[10];
+  for (int i = 0; i < 5; ++i) {
+    K[i * 2 + 0] = C[i * 5 + 0] * Si00 + C[i * 5 + 1] * Si01;
+    K[i * 2 + 1] = C[i * 5 + 0] * Si01 + C[i * 5 + 1] * Si11;
+  }
+  double HC[10];
+  for (int j = 0; j < 5; ++j) { HC[0 * 5 + j] = C[0 * 5 + j]; HC[1 * 5 + j] = C[1 * 5 + j]; }
+  for (int i = 0; i < 5; ++i) p[i] += K[i * 2 + 0] * r0 + K[i * 2 + 1] * r1;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) C[i * 5 + j] -= K[i * 2 + 0] * HC[0 * 5 + j] + K[i * 2 + 1] * HC[1 * 5 + j];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < i; ++j) { double m = 0.5 * (C[i * 5 + j] + C[j * 5 + i]); C[i * 5 + j] = C[j * 5 + i] = m; }
+  *accepted = 1;
+  return ST_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Multiple scattering in one pad row (PDG Highland formula): momentum
+ * p = |1/w| sqrt(1+t^2), beta = p / sqrt(p^2+m^2), path through the plane of
+ * constant x: eps = xx0 sqrt(1+t^2)/sqrt(1-sinphi^2),
+ * theta0 = 0.0136/(beta p) sqrt(eps) (1 + 0.038 ln(eps/beta^2)).
+ * Two independent small kicks (in phi and in lambda) at fixed |p| give the
+ * added noise on (sinphi, tanlambda, q/pT).
+ * ------------------------------------------------------------------------- */
+void orc_ms_noise(const double p[5], double C[25], double xx0, double mass) {
+  if (!(xx0 > 0.0)) return;
+  double s = p[2], t = p[3], w = p[4];
+  double tt = 1.0 + t * t;
+  if (w == 0.0) return; /* infinite momentum: no deflection */
+  double mom = sqrt(tt) / fabs(w);
+  double beta = mom / sqrt(mom * mom + mass * mass);
+  double eps = xx0 * sqrt(tt) / sqrt(1.0 - s * s);
+  double th0 = 0.0136 / (beta * mom) * sqrt(eps) * (1.0 + 0.038 * log(eps / (beta * beta)));
+  double th2 = th0 * th0;
+  C[2 * 5 + 2] += th2 * (1.0 - s * s) * tt;
+  C[3 * 5 + 3] += th2 * tt * tt;
+  C[4 * 5 + 4] += th2 * w * w * t * t;
+  C[3 * 5 + 4] += th2 * tt * w * t;
+  C[4 * 5 + 3] += th2 * tt * w * t;
+}
+
+/* ---------------------------------------------------------------------------
+ * Three-point seed: circle through clusters a=0, b=n/2, c=n-1 in the (x, y)
+ * plane.  Signed curvature from the triangle (kappa = 2 cross / (|ab||ac||bc|)),
+ * direction at a from the chord a->c minus half the turned angle,
+ * tanlambda from (z_c - z_a) over the transverse arc a->c, q/pT = -C/(kB Bz).
+ * ------------------------------------------------------------------------- */
+void orc_seed(const double xa[3], const double xb[3], const double xc[3], double bz, double p[5]) {
+  double abx = xb[0] - xa[0], aby = xb[1] - xa[1];
+  double acx = xc[0] - xa[0], acy = xc[1] - xa[1];
+  double bcx = xc[0] - xb[0], bcy = xc[1] - xb[1];
+  double cross = abx * acy - aby * acx;
+  double lab = sqrt(abx * abx + aby * aby), lac = sqrt(acx * acx + acy * acy), lbc = sqrt(bcx * bcx + bcy * bcy);
+  double kappa = 2.0 * cross / (lab * lac * lbc);
+  double u = 0.5 * kappa * lac;
+  if (u > 1.0) u = 1.0;
+  if (u < -1.0) u = -1.0;
+  double phi = atan2(acy, acx) - asin(u);
+  double s_ac = lac * asin_over_u(u);
+  p[0] = xa[1];
+  p[1] = xa[2];
+  p[2] = sin(phi);
+  p[3] = (xc[2] - xa[2]) / s_ac;
+  p[4] = -kappa / (ORC_KB * bz);
+}
+
+static void pack_cov(const double C[25], double *out15) {
+  int k = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) out15[k++] = C[i * 5 + j];
+}
+static void seed_cov(const orc_config *c, double C[25]) {
+  for (int i = 0; i < 25; ++i) C[i] = 0.0;
+  for (int i = 0; i < 5; ++i) C[i * 5 + i] = c->seed_cov[i];
+}
+static int finite_cluster(const float *x, const float *y, const float *z, const float *sy2, const float *sz2, int64_t k) {
+  return isfinite(x[k]) && isfinite(y[k]) && isfinite(z[k]) && isfinite(sy2[k]) && isfinite(sz2[k]);
+}
+
+/* One track: seed, outward pass over every crossed row, restart, inward pass. */
+static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const float *x, const float *y, const float *z,
+                      const float *sy2, const float *sz2, const uint8_t *row, const orc_result *o) {
+  int64_t a = off[t], e = off[t + 1];
+  int64_t n = e - a;
+  double p[5] = {0, 0, 0, 0, 0}, C[25], F[25], pn[5];
+  int status = ST_OK;
+  double chi2_in = 0.0;
+  int nacc_in = 0;
+  for (int64_t k = a; k < e; ++k) {
+    o->accept[k] = 0;
+    if (o->chi2_out_c) o->chi2_out_c[k] = NAN;
+    if (o->chi2_in_c) o->chi2_in_c[k] = NAN;
+    if (o->state_in_c) for (int i = 0; i < 5; ++i) o->state_in_c[5 * k + i] = NAN;
+  }
+  seed_cov(c, C);
+  double xref = (n > 0) ? (double)x[a] : 0.0;
+  if (n < c->min_clusters || n < 3) {
+    status = ST_TOO_FEW;
+    goto emit;
+  }
+  {
+    double A[3] = {x[a], y[a], z[a]}, B[3] = {x[a + n / 2], y[a + n / 2], z[a + n / 2]},
+           D[3] = {x[e - 1], y[e - 1], z[e - 1]};
+    orc_seed(A, B, D, c->bz, p);
+  }
+  if (fabs(p[2]) >= c->snp_max) { status = ST_SNP_LIMIT; goto emit; }
+
+  /* ---- outward pass: rows row[a] .. row[e-1] ---- */
+  double xcur = x[a];
+  for (int64_t k = a; k < e; ++k) {
+    /* validation of cluster k when the pass reaches it */
+    if (row[k] >= c->n_rows || (k > a && row[k] <= row[k - 1])) { status = ST_BAD_INPUT; goto emit; }
+    if (!finite_cluster(x, y, z, sy2, sz2, k)) { status = ST_NONFINITE; goto emit; }
+    if (!(sy2[k] > 0.0f) || !(sz2[k] > 0.0f)) { status = ST_BAD_INPUT; goto emit; }
+    /* rows crossed without a cluster */
+    if (k > a) {
+      for (int r = row[k - 1] + 1; r < row[k]; ++r) {
+        double xr = c->row_x[r];
+        if ((status = orc_propagate(p, xcur, xr, c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+        memcpy(p, pn, sizeof(pn));
+        cov_transport(C, F);
+        xcur = xr;
+        orc_ms_noise(p, C, c->xx0, c->mass);
+      }
+    }
+    if ((status = orc_propagate(p, xcur, x[k], c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+    memcpy(p, pn, sizeof(pn));
+    cov_transport(C, F);
+    xcur = x[k];
+    double chi2;
+    int acc;
+    if ((status = orc_update(p, C, y[k], z[k], sy2[k], sz2[k], c->chi2_max, &chi2, &acc)) != ST_OK) goto emit;
+    if (o->chi2_out_c) o->chi2_out_c[k] = chi2;
+    if (acc) o->accept[k] |= 1;
+    orc_ms_noise(p, C, c->xx0, c->mass);
+  }
+
+  /* ---- inward pass: restart from the outward state with a diagonal covariance,
+     the outward variances inflated by restart_scale and capped at the seed's ---- */
+  if (o->state_out_t) for (int i = 0; i < 5; ++i) o->state_out_t[5 * t + i] = p[i];
+  {
+    double d[5];
+    for (int i = 0; i < 5; ++i) {
+      d[i] = c->restart_scale * C[i * 5 + i];
+      if (!(d[i] <= c->seed_cov[i])) d[i] = c->seed_cov[i];
+    }
+    for (int i = 0; i < 25; ++i) C[i] = 0.0;
+    for (int i = 0; i < 5; ++i) C[i * 5 + i] = d[i];
+    if (o->restart_t) for (int i = 0; i < 5; ++i) o->restart_t[5 * t + i] = d[i];
+  }
+  for (int64_t k = e - 1; k >= a; --k) {
+    if (k < e - 1) {
+      for (int r = row[k + 1] - 1; r > row[k]; --r) {
+        double xr = c->row_x[r];
+        if ((status = orc_propagate(p, xcur, xr, c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+        memcpy(p, pn, sizeof(pn));
+        cov_transport(C, F);
+        xcur = xr;
+        orc_ms_noise(p, C, c->xx0, c->mass);
+      }
+    }
+    if ((status = orc_propagate(p, xcur, x[k], c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+    memcpy(p, pn, sizeof(pn));
+    cov_transport(C, F);
+    xcur = x[k];
+    double chi2;
+    int acc;
+    if ((status = orc_update(p, C, y[k], z[k], sy2[k], sz2[k], c->chi2_max, &chi2, &acc)) != ST_OK) goto emit;
+    if (o->chi2_in_c) o->chi2_in_c[k] = chi2;
+    if (acc) { o->accept[k] |= 2; chi2_in += chi2; ++nacc_in; }
+    if (o->state_in_c) for (int i = 0; i < 5; ++i) o->state_in_c[5 * k + i] = p[i];
+    orc_ms_noise(p, C, c->xx0, c->mass);
+  }
+
+  /* a fit that completed with a non-finite state or covariance */
+  for (int i = 0; i < 25; ++i)
+    if (!isfinite(C[i]) || (i < 5 && !isfinite(p[i]))) { status = ST_NONFINITE; break; }
+
+emit:
+  for (int i = 0; i < 5; ++i) o->state[5 * t + i] = p[i];
+  pack_cov(C, o->cov + 15 * t);
+  o->x_ref[t] = xref;
+  o->chi2[t] = chi2_in;
+  o->ndf[t] = 2 * nacc_in - 5;
+  o->status[t] = status;
+}
+
+typedef struct {
+  const orc_config *c;
+  int64_t nt;
+  const int64_t *off;
+  const float *x, *y, *z, *sy2, *sz2;
+  const uint8_t *row;
+  const orc_result *o;
+  int tid, nth;
+} job_t;
+
+static void *worker(void *arg) {
+  job_t *j = (job_t *)arg;
+  int64_t per = (j->nt + j->nth - 1) / j->nth;
+  int64_t s = (int64_t)j->tid * per, e = s + per < j->nt ? s + per : j->nt;
+  for (int64_t t = s; t < e; ++t) fit_track(j->c, t, j->off, j->x, j->y, j->z, j->sy2, j->sz2, j->row, j->o);
+  return NULL;
+}
+
+/* Frame-level entry.  Returns 0, or -1 if the offsets are malformed
+ * (off[0] != 0, decreasing, or off[nt] != nc): nothing is fitted then. */
+int oracle_fit(const orc_config *c, int64_t nt, int64_t nc, const int64_t *off, const float *x, const float *y,
+               const float *z, const float *sy2, const float *sz2, const uint8_t *row, const orc_result *o,
+               int n_threads) {
+  if (nt < 0 || nc < 0 || !off) return -1;
+  if (off[0] != 0 || off[nt] != nc) return -1;
+  for (int64_t t = 0; t < nt; ++t)
+    if (off[t + 1] < off[t]) return -1;
+  int nth = n_threads > 0 ? n_threads : 1;
+  if (nth > 512) nth = 512;
+  if ((int64_t)nth > nt) nth = nt > 0 ? (int)nt : 1;
+  pthread_t th[512];
+  job_t jobs[512];
+  for (int i = 0; i < nth; ++i) {
+    job_t jj = {c, nt, off, x, y, z, sy2, sz2, row, o, i, nth};
+    jobs[i] = jj;
+    if (nth == 1) worker(&jobs[i]);
+    else pthread_create(&th[i], NULL, worker, &jobs[i]);
+  }
+  if (nth > 1) for (int i = 0; i < nth; ++i) pthread_join(th[i], NULL);
+  return 0;
+}

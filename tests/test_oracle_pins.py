@@ -1,0 +1,311 @@
+"""Pins of the FP64 oracle against mathematics it does not itself contain.
+
+The paper prints no worked example of the fit (it gives no fit formulas at
+all), so every pin here is a closed form, an invariant, an independent
+implementation (the global-circle generator, the global least-squares fit,
+a straight-line regression) or a statistical property of the Kalman filter.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import tpcgen
+from oracle import lsq
+
+RNG = np.random.default_rng(12345)
+
+
+def _random_state(rng):
+    return np.array([rng.uniform(-30, 30), rng.uniform(-100, 100), rng.uniform(-0.6, 0.6),
+                     rng.uniform(-0.9, 0.9), rng.uniform(-5, 5)])
+
+
+# ---------------------------------------------------------------- propagation
+def test_propagation_reproduces_generator_helix():
+    """Chord-form local transport vs the generator's global circle (different representation)."""
+    f = tpcgen.generate("sector1k", n_tracks=200, truth=True, sigma_y=0.0, sigma_z=0.0, seed=5)
+    worst = np.zeros(5)
+    for t in range(f.n_tracks):
+        a, b = f.offsets[t], f.offsets[t + 1]
+        for k in range(a, b - 1):
+            st, p2, _ = oracle.propagate(f.truth[k], float(f.x[k]), float(f.x[k + 1]))
+            assert st == 0
+            worst = np.maximum(worst, np.abs(p2 - f.truth[k + 1]))
+    # cm for y, z; absolute for sinphi, tanlambda, q/pT
+    assert np.all(worst < [1e-9, 1e-9, 1e-12, 1e-12, 1e-12]), worst
+
+
+def test_propagation_round_trip_and_composition():
+    for _ in range(50):
+        p = _random_state(RNG)
+        x1, x2, x3 = 100.0, 100.0 + RNG.uniform(-5, 5), 100.0 + RNG.uniform(-5, 5)
+        st, p2, F12 = oracle.propagate(p, x1, x2)
+        st2, p1b, _ = oracle.propagate(p2, x2, x1)
+        if st or st2:
+            continue
+        assert np.allclose(p1b, p, rtol=0, atol=1e-11)
+        _, p3, F23 = oracle.propagate(p2, x2, x3)
+        _, p3d, F13 = oracle.propagate(p, x1, x3)
+        assert np.allclose(p3, p3d, rtol=0, atol=1e-10)
+        assert np.allclose(F23 @ F12, F13, rtol=1e-8, atol=1e-10)
+
+
+def test_jacobian_matches_finite_differences():
+    for _ in range(50):
+        p = _random_state(RNG)
+        x1, x2 = 120.0, 120.0 + RNG.uniform(-4, 4)
+        st, _, F = oracle.propagate(p, x1, x2)
+        if st:
+            continue
+        Fn = np.zeros((5, 5))
+        for j in range(5):
+            h = 1e-6 * max(1.0, abs(p[j]))
+            dp = np.zeros(5)
+            dp[j] = h
+            Fn[:, j] = (oracle.propagate(p + dp, x1, x2)[1] - oracle.propagate(p - dp, x1, x2)[1]) / (2 * h)
+        assert np.allclose(F, Fn, rtol=1e-6, atol=1e-7)
+
+
+def test_propagation_sinphi_limit():
+    # C = -kB*Bz*w > 0 for w < 0: sinphi grows from 0.99 past the limit
+    st, _, _ = oracle.propagate([0, 0, 0.99, 0, -5.0], 100.0, 110.0, snp_max=0.999)
+    assert st == 2  # SNP_LIMIT
+
+
+# ---------------------------------------------------------------- seed
+def test_seed_exact_on_a_circle():
+    """Three points of a noise-free helix give back its state at the first point."""
+    f = tpcgen.generate("sector1k", n_tracks=100, truth=True, sigma_y=0.0, sigma_z=0.0, seed=9)
+    for t in range(f.n_tracks):
+        a, b = f.offsets[t], f.offsets[t + 1]
+        n = b - a
+        pts = [(float(f.x[k]), f.truth[k, 0], f.truth[k, 1]) for k in (a, a + n // 2, b - 1)]
+        s = oracle.seed(*pts)
+        assert np.allclose(s, f.truth[a], rtol=1e-9, atol=1e-9), (t, s, f.truth[a])
+
+
+# ---------------------------------------------------------------- update
+def test_update_gate_equality_accepts_and_rejects_above():
+    p = np.array([1.0, 2.0, 0.1, 0.2, 0.5])
+    C = np.diag([0.04, 0.05, 1e-3, 1e-3, 1e-2])
+    _, _, _, chi2, acc = oracle.update(p, C, 1.3, 1.9, 0.01, 0.01, chi2_max=1e9)
+    assert acc
+    _, _, _, _, acc_eq = oracle.update(p, C, 1.3, 1.9, 0.01, 0.01, chi2_max=chi2)
+    _, p_rej, C_rej, _, acc_lo = oracle.update(p, C, 1.3, 1.9, 0.01, 0.01, chi2_max=np.nextafter(chi2, 0))
+    assert acc_eq and not acc_lo
+    assert np.array_equal(p_rej, p) and np.array_equal(C_rej, C)
+    # closed form for a diagonal prior: chi2 = r0^2/S00 + r1^2/S11
+    assert chi2 == pytest.approx(0.3 ** 2 / 0.05 + 0.1 ** 2 / 0.06, rel=1e-14)
+
+
+def test_update_equals_information_form():
+    """Kalman gain form == information (inverse covariance) form of the linear update."""
+    for _ in range(20):
+        A = RNG.normal(size=(5, 5))
+        C = A @ A.T + 0.1 * np.eye(5)
+        p = RNG.normal(size=5)
+        m = RNG.normal(size=2)
+        V = np.diag([0.01, 0.02])
+        _, p2, C2, _, acc = oracle.update(p, C, m[0], m[1], V[0, 0], V[1, 1], chi2_max=1e30)
+        assert acc
+        H = np.zeros((2, 5))
+        H[0, 0] = H[1, 1] = 1
+        Ci = np.linalg.inv(C) + H.T @ np.linalg.inv(V) @ H
+        Cpost = np.linalg.inv(Ci)
+        ppost = Cpost @ (np.linalg.solve(C, p) + H.T @ np.linalg.solve(V, m))
+        assert np.allclose(C2, Cpost, rtol=1e-9, atol=1e-12)
+        assert np.allclose(p2, ppost, rtol=1e-9, atol=1e-12)
+
+
+# ---------------------------------------------------------------- scattering
+def test_ms_noise_matches_small_kick_monte_carlo():
+    """Covariance of (sinphi, tanlambda, q/pT) under two perpendicular Gaussian
+    kicks at fixed |p|, sampled with an independent direction-vector model."""
+    p = np.array([3.0, 10.0, 0.3, 0.6, -1.7])
+    C0 = np.zeros((5, 5))
+    C1 = oracle.ms_noise(p, C0, 5e-4)
+    th2 = C1[3, 3] / (1 + p[3] ** 2) ** 2  # theta0^2 implied by the tanlambda entry
+    rng = np.random.default_rng(1)
+    nsamp = 400_000
+    th = np.sqrt(th2)
+    phi, lam = np.arcsin(p[2]), np.arctan(p[3])
+    d = np.array([np.cos(lam) * np.cos(phi), np.cos(lam) * np.sin(phi), np.sin(lam)])
+    e1 = np.array([-np.sin(phi), np.cos(phi), 0.0])
+    e2 = np.array([-np.sin(lam) * np.cos(phi), -np.sin(lam) * np.sin(phi), np.cos(lam)])
+    a1, a2 = rng.normal(0, th, nsamp), rng.normal(0, th, nsamp)
+    dn = d[None, :] + a1[:, None] * e1[None, :] + a2[:, None] * e2[None, :]
+    dn /= np.linalg.norm(dn, axis=1)[:, None]
+    pt = np.hypot(dn[:, 0], dn[:, 1])
+    snp = dn[:, 1] / pt
+    tgl = dn[:, 2] / pt
+    mom = np.sqrt(1 + p[3] ** 2) / abs(p[4])
+    w = np.sign(p[4]) / (mom * pt)
+    emp = np.cov(np.vstack([snp, tgl, w]))
+    ana = C1[2:, 2:]
+    for (i, j) in [(0, 0), (1, 1), (2, 2), (1, 2)]:
+        assert emp[i, j] == pytest.approx(ana[i, j], rel=0.02), (i, j, emp[i, j], ana[i, j])
+    assert abs(emp[0, 1]) < 0.02 * np.sqrt(ana[0, 0] * ana[1, 1])
+    # Highland width ~ 1/(beta p): halving p (doubling q/pT) raises theta0^2 about fourfold
+    p2 = p.copy()
+    p2[4] *= 2
+    assert 3.5 < oracle.ms_noise(p2, C0, 5e-4)[3, 3] / C1[3, 3] < 5.0
+
+
+# ---------------------------------------------------------------- full fits
+def _cfg(**kw):
+    return oracle.FitConfig(**kw)
+
+
+def test_noise_free_fit_recovers_truth():
+    """No noise, no scattering: the fit reproduces the helix at every cluster
+    to the float32 rounding of the stored cluster coordinates."""
+    g = tpcgen.generate("sector1k", truth=True, n_tracks=300, sigma_y=0.0, sigma_z=0.0)
+    r = oracle.fit(g, _cfg(xx0=0.0), diagnostics=True)
+    assert np.all(r["status"] == 0)
+    C = oracle.unpack_cov(r["cov"])
+    s = np.sqrt(np.diagonal(C, axis1=1, axis2=2))
+    d = np.abs(r["state"] - g.truth[g.offsets[:-1]]) / s
+    assert d.max() < 0.05
+    dc = np.abs(r["state_in_c"] - g.truth)
+    assert np.all(dc.max(0) < [5e-5, 5e-5, 5e-5, 5e-5, 5e-2])
+    assert r["chi2"].max() < 0.05
+
+
+def test_kalman_equals_global_least_squares_on_short_tracks():
+    """Inward pass == Gauss-Newton minimum of sum chi2 + prior term (restart
+    covariance at the outermost cluster); the gap is the extended filter's
+    linearisation error, so |dp|/sigma must shrink linearly with sigma_meas."""
+    med = {}
+    for sm in (1e-5, 1e-4):
+        f = tpcgen.generate("sector1k", truth=True, n_tracks=30, n_rows=10, min_clusters=3, sigma_y=sm,
+                            sigma_z=sm, seed=3)
+        cfg = _cfg(xx0=0.0, n_rows=10, min_clusters=3, chi2_max=1e30)
+        r = oracle.fit(f, cfg, diagnostics=True)
+        assert np.all(r["status"] == 0)
+        dp, dc = [], []
+        for t in range(f.n_tracks):
+            a, b = f.offsets[t], f.offsets[t + 1]
+            P0 = np.diag(r["restart_t"][t])
+            p, cov = lsq.fit_inward(*[getattr(f, k)[a:b].astype(float) for k in ("x", "y", "z", "sy2", "sz2")],
+                                    r["state_out_t"][t], P0, cfg.bz, p_start=r["state"][t])
+            s = np.sqrt(np.diag(cov))
+            dp.append(np.max(np.abs(p - r["state"][t]) / s))
+            dc.append(np.max(np.abs(oracle.unpack_cov(r["cov"][t]) - cov) / np.outer(s, s)))
+        med[sm] = np.median(dp)
+        if sm == 1e-5:
+            assert max(dp) < 2e-3 and max(dc) < 5e-5
+    assert 4 < med[1e-4] / med[1e-5] < 25
+
+
+def test_straight_line_equals_weighted_regression():
+    """Bz -> 0, zero slope in y: the (z, tanlambda) block is an exactly linear
+    model, so the fit equals the closed-form weighted regression with the prior."""
+    rng = np.random.default_rng(4)
+    nrow, nt = 60, 40
+    x = (85.0 + np.arange(nrow) * 162.0 / 151.0).astype(np.float32)
+    offs = np.arange(nt + 1, dtype=np.int64) * nrow
+    z0 = rng.uniform(-20, 20, nt)
+    tl = rng.uniform(-0.8, 0.8, nt)
+    zz = (z0[:, None] + tl[:, None] * (x[None, :].astype(float) - 85.0) + rng.normal(0, 0.1, (nt, nrow)))
+    zz = zz.astype(np.float32)
+    frame = type("F", (), {})()
+    frame.offsets = offs
+    frame.x = np.tile(x, nt)
+    frame.y = np.zeros(nt * nrow, np.float32)
+    frame.z = zz.reshape(-1)
+    frame.sy2 = np.full(nt * nrow, 0.01, np.float32)
+    frame.sz2 = np.full(nt * nrow, 0.01, np.float32)
+    frame.row = np.tile(np.arange(nrow, dtype=np.uint8), nt)
+    cfg = _cfg(xx0=0.0, bz=1e-9, chi2_max=1e30)
+    r = oracle.fit(frame, cfg, diagnostics=True)
+    assert np.all(r["status"] == 0)
+    assert np.all(r["state"][:, 0] == 0) and np.all(r["state"][:, 2] == 0)
+    for t in range(nt):
+        xs = x.astype(float) - float(x[0])
+        zt = zz[t].astype(float)
+        pz_prior, pt_prior = r["state_out_t"][t, 1], r["state_out_t"][t, 3]
+        vz, vt = r["restart_t"][t, 1], r["restart_t"][t, 3]
+        A = np.vstack([np.ones(nrow), xs]).T
+        Wm = np.full(nrow, 1 / 0.01)
+        Ap = np.array([[1.0, xs[-1]], [0.0, 1.0]])
+        Wp = np.array([1 / vz, 1 / vt])
+        N = A.T @ (Wm[:, None] * A) + Ap.T @ (Wp[:, None] * Ap)
+        rhs = A.T @ (Wm * zt) + Ap.T @ (Wp * np.array([pz_prior, pt_prior]))
+        theta = np.linalg.solve(N, rhs)
+        cov = np.linalg.inv(N)
+        C = oracle.unpack_cov(r["cov"][t])
+        assert r["state"][t, 1] == pytest.approx(theta[0], abs=1e-9)
+        assert r["state"][t, 3] == pytest.approx(theta[1], abs=1e-11)
+        assert np.allclose([C[1, 1], C[1, 3], C[3, 3]], [cov[0, 0], cov[0, 1], cov[1, 1]], rtol=1e-8)
+
+
+def test_covariance_symmetric_positive_definite():
+    for preset, xx0 in (("sector1k", 0.0), ("detector50k", 5e-4)):
+        f = tpcgen.generate(preset, n_tracks=3000)
+        r = oracle.fit(f, _cfg(xx0=xx0))
+        C = oracle.unpack_cov(r["cov"][r["status"] == 0])
+        assert np.array_equal(C, np.swapaxes(C, 1, 2))
+        np.linalg.cholesky(C)  # raises if any is not positive definite
+
+
+@pytest.mark.parametrize("preset,xx0", [("sector1k", 0.0), ("detector50k", 5e-4)])
+def test_pull_and_chi2_statistics(preset, xx0):
+    """Pulls at the innermost cluster ~ N(0,1) and <chi2/ndf> ~ 1 (no outliers).
+    Tracks with >= 40 clusters: on shorter ones the inward prior, centred on the
+    outward estimate of the same clusters, narrows the covariance measurably."""
+    f = tpcgen.generate(preset, n_tracks=12000, truth=True, p_outlier=0.0, seed=11)
+    r = oracle.fit(f, _cfg(xx0=xx0))
+    n = np.diff(f.offsets)
+    m = (r["status"] == 0) & (n >= 40)
+    assert m.sum() >= 10000
+    C = oracle.unpack_cov(r["cov"])
+    s = np.sqrt(np.diagonal(C, axis1=1, axis2=2))
+    pull = ((r["state"] - f.truth[f.offsets[:-1]]) / s)[m]
+    assert np.all(np.abs(pull.mean(0)) < 0.05), pull.mean(0)
+    assert np.all(np.abs(pull.std(0) - 1) < 0.05), pull.std(0)
+    assert abs((r["chi2"][m] / r["ndf"][m]).mean() - 1) < 0.03
+
+
+def test_outliers_rejected_by_the_gate():
+    f = tpcgen.generate("detector50k", n_tracks=20000, truth=True)
+    r = oracle.fit(f, _cfg())
+    disp = np.maximum(np.abs(f.y - f.truth[:, 0]), np.abs(f.z - f.truth[:, 1]))
+    big = (f.flags == 1) & (disp > 1.0)
+    inward = (r["accept"] >> 1) & 1
+    assert 1 - inward[big].mean() >= 0.99
+    assert inward[f.flags == 0].mean() >= 0.99
+
+
+# ---------------------------------------------------------------- status / edge cases
+def test_status_codes_and_validation_order():
+    f = tpcgen.generate("sector1k", n_tracks=6, seed=2)
+    y = f.y.copy()
+    row = f.row.copy()
+    offs = f.offsets
+    y[offs[1] + 5] = np.nan                       # track 1: non-finite
+    row[offs[2] + 7] = row[offs[2] + 6]           # track 2: rows not ascending
+    row[offs[3] + 3] = row[offs[3] + 2]           # track 3: row problem before ...
+    y[offs[3] + 9] = np.inf                       # ... a non-finite value: first in pass order wins
+    g = tpcgen.Frame(offs, f.x, y, f.z, f.sy2, f.sz2, row, f.sector)
+    r = oracle.fit(g, _cfg(xx0=0.0))
+    assert list(r["status"][:4]) == [0, 4, 5, 5]
+    short = f.subset(0, 1)
+    keep = np.arange(short.n_clusters) < 9
+    s2 = tpcgen.Frame(np.array([0, 9]), *(getattr(short, k)[keep] for k in ("x", "y", "z", "sy2", "sz2", "row")),
+                      short.sector)
+    assert oracle.fit(s2, _cfg())["status"][0] == 1  # TOO_FEW
+    bad = tpcgen.Frame(np.array([0, 5, 3]), f.x[:3], f.y[:3], f.z[:3], f.sy2[:3], f.sz2[:3], f.row[:3], f.sector[:2])
+    with pytest.raises(ValueError):
+        oracle.fit(bad, _cfg())
+
+
+def test_empty_frame_and_thread_invariance():
+    e = tpcgen.Frame(np.zeros(1, np.int64), *(np.zeros(0, np.float32),) * 5, np.zeros(0, np.uint8),
+                     np.zeros(0, np.uint8))
+    r = oracle.fit(e, _cfg())
+    assert r["state"].shape == (0, 5)
+    f = tpcgen.generate("detector50k", n_tracks=500)
+    a = oracle.fit(f, _cfg(), threads=1)
+    b = oracle.fit(f, _cfg(), threads=7)
+    for k in ("state", "cov", "chi2", "ndf", "status", "accept"):
+        assert np.array_equal(a[k], b[k])
