@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the batched TPC Kalman track fit on GB300.
+
+One step = one pass of the whole hot path (offset/input checks, 3-point seeds,
+longest-first sort, outward + inward Kalman passes, outputs) over one
+Pb-Pb-scale synthetic time frame: 2,000,000 tracks, ~192 M clusters (seed 0,
+exponential pT spectrum with mean 0.6 GeV/c, scattering, 5 % dropout, 1 %
+outliers).  The frame (4.2 GB of cluster SoA) is larger than the 129 MB L2, so
+no flush is needed between steps.
+
+Prints one JSON line: clusters/s with the frame resident in HBM (``value``),
+clusters/s through the C-ABI with pinned host buffers including the copies
+(``e2e``), the fit kernel's roofline fraction, and the FP64 oracle timed on a
+bounded sample of the same frame on the host cores (``cpu_baseline``).
+
+``--impl reference`` times the FP64 oracle (the reference arm of this
+project) on the host cores on bounded samples of the same workload.
+Multi-GPU (torchrun): every rank fits its own frame (independent time frames,
+no data exchange), max time over ranks, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import tpcgen  # noqa: E402
+
+WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT (mean 0.6 GeV/c), 36 sectors, "
+                       "x/X0 5e-4 per row, 5% dropout, 1% outliers, seed 0"}
+FP64_PER_CLUSTER = 21         # FP64 pipe instructions per cluster: 10 (outward update) + 11 (inward update + sum)
+BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
+BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_2402_01205_gb300", "csrc", "fit_kernels.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic(n_clusters_fitted: int):
+    """DRAM bytes per fit-kernel launch from the committed ncu summary, scaled to
+    this launch by clusters; None when the kernel changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "fit_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_sha256_16") != kernel_source_hash():
+        return None, "kernel changed since the ncu capture"
+    return d["dram_bytes_per_cluster"] * n_clusters_fitted, d.get("capture")
+
+
+def cpu_baseline(frame, seconds_target: float = 15.0, max_tracks: int = 400_000):
+    """Time the FP64 oracle on the first tracks of the frame with every host core."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n = min(20_000, frame.n_tracks)
+    sub = frame.subset(0, n)
+    t0 = time.perf_counter()
+    oracle.fit(sub, oracle.FitConfig(), threads=cores)
+    dt = time.perf_counter() - t0
+    rate = sub.n_clusters / max(dt, 1e-9)
+    n2 = int(min(max_tracks, frame.n_tracks, max(n, n * seconds_target / max(dt, 1e-6))))
+    sub = frame.subset(0, n2)
+    t0 = time.perf_counter()
+    r = oracle.fit(sub, oracle.FitConfig(), threads=cores)
+    dt = time.perf_counter() - t0
+    rate = sub.n_clusters / dt
+    return {"value": rate, "unit": "clusters/s", "cores": int(r["threads"]), "kind": "oracle",
+            "sample": f"first {n2} tracks ({sub.n_clusters} clusters) of the same frame, FP64 C oracle, "
+                      f"{dt:.1f} s, one pthread per host core", "tracks_per_s": n2 / dt}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 oracle on bounded samples of the workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n = args.ref_tracks
+    frame = tpcgen.generate(args.workload, n_tracks=n, seed=0)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.fit(frame.subset(0, min(n, 2000)), oracle.FitConfig(), threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fit(frame, oracle.FitConfig(), threads=cores)
+    dt = time.perf_counter() - t0
+    value = frame.n_clusters * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "clusters/s fitted (FP64 oracle on host cores)", "value": value,
+        "unit": "clusters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                   "sample": f"first {n} tracks ({frame.n_clusters} clusters) of the frame per step"},
+        "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {n} tracks ({frame.n_clusters} clusters) per step"},
+        "e2e": {"value": value, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pbpb2m", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-tracks", type=int, default=None, help="override the workload's track count (testing)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-tracks", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import paper_2402_01205_gb300 as T
+    from paper_2402_01205_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    probe = T.probe_fma_rates(local)
+    kw = {} if args.n_tracks is None else {"n_tracks": args.n_tracks}
+    frame = tpcgen.generate(args.workload, seed=rank, **kw)
+    nt, nc = frame.n_tracks, frame.n_clusters
+    names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
+
+    class F:
+        pass
+
+    dev = F()
+    for k in names:
+        setattr(dev, k, torch.from_numpy(np.ascontiguousarray(getattr(frame, k))).cuda())
+    fx = T.Fitter(device=local)
+    res = T.alloc_result(nt, nc, device=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        fx.fit_async(dev, res, stream=stream)
+    fx.sync()
+    fx.reset_timing()
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fx.fit_async(dev, res, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    tm = fx.timing()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([float(nc)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tot)
+        nc_all = float(tot.item())
+    else:
+        nc_all = float(nc)
+    value = nc_all * args.steps / (ms * 1e-3)
+    status = res["status"].cpu().numpy()
+    ok = status == 0
+    lens = np.diff(frame.offsets)
+    nc_fit = int(lens[ok].sum())
+    fit_s = tm["fit_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
+    peaks, peak_src = measured_peaks()
+    fp64_peak = probe["fp64_fma_per_s"]
+    achieved = FP64_PER_CLUSTER * nc_fit / fit_s
+    traffic, traffic_note = profiled_traffic(nc_fit)
+    hbm_achieved = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
+    roofline = {
+        "bound": "alu", "kernel": "k_fit",
+        "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
+        "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "frac": achieved / fp64_peak,
+        "peak_source": "measured live: FP64 FMA chain probe in libtpcfit (tpcfit_probe_fma_rates)",
+        "traffic": traffic, "traffic_note": traffic_note,
+        "fit_ms_avg": fit_s * 1e3, "fp64_inst_per_cluster": FP64_PER_CLUSTER,
+        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
+                "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
+        "fp32_fma_peak_per_s": probe["fp32_fma_per_s"],
+    }
+    # end to end through the C-ABI: pinned host frame in, pinned host results out
+    e2e = None
+    if args.e2e_steps > 0:
+        host = F()
+        for k in names:
+            t = torch.empty(getattr(dev, k).shape, dtype=getattr(dev, k).dtype, pin_memory=True)
+            t.copy_(torch.from_numpy(np.ascontiguousarray(getattr(frame, k))))
+            setattr(host, k, t)
+        hres = T.alloc_result(nt, nc, pinned=True)
+        fx.fit(host, hres)  # warm-up (staging buffers)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fx.fit(host, hres)
+            _ = float(hres["chi2"][0])  # the step's result read on the host
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": nc_all * args.e2e_steps / dt, "unit": "clusters/s",
+               "h2d_bytes_per_step": int(21 * nc + 8 * (nt + 1)), "d2h_bytes_per_step": int(100 * nt + nc),
+               "ms_per_step": dt / args.e2e_steps * 1e3, "path": "tpcfit_fit, TPCFIT_MEM_HOST pinned, chunked overlap"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(frame)
+    if rank == 0:
+        line = {
+            "metric": "clusters/s fitted on 1 GB300 (FP32 fit, FP64 innovation inverse and chi2)",
+            "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n_tracks": nt,
+                       "n_clusters": nc, "tracks_fitted_ok": int(ok.sum()), "l2": "inputs 4.2 GB > L2; no flush",
+                       "parallelism": f"replicas x{ws}", "fit_grid": tm["fit_grid"], "fit_block": tm["fit_block"],
+                       "fit_regs": tm["fit_regs"]},
+            "tracks_per_s": nt * ws * args.steps / (ms * 1e-3),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(tm["kernel_launches"]) * args.steps,
+            "clocks": clk,
+            "kernel_ms": {"prepare": tm["prepare_ms_sum"] / tm["n_timed"], "sort": tm["sort_ms_sum"] / tm["n_timed"],
+                          "fit": tm["fit_ms_sum"] / tm["n_timed"], "sequence": tm["total_ms_sum"] / tm["n_timed"]},
+        }
+        print(json.dumps(line), flush=True)
+    fx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

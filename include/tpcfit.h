@@ -1,0 +1,199 @@
+/*
+ * tpcfit: batched Kalman-filter fit of TPC tracks on one GB300 (sm_103a).
+ *
+ * The paper (Eulisse & Rohr, "The O2 software framework and GPU usage in ALICE
+ * online and offline reconstruction in Run 3") identifies TPC tracking as the
+ * step that dominates synchronous processing (Sec. 5, Table 1: TPC processing
+ * 99.37 %) and asynchronous processing (Table 2: 61.41 %), and runs it on GPUs
+ * (Sec. 6).  It does not write the fit out; this library implements the
+ * textbook Kalman track fit (state y, z, sinphi, tanlambda, q/pT on pad-row
+ * planes of a sector, exact helix in a uniform Bz field, chi2-gated cluster
+ * updates, Highland multiple scattering, an outward then an inward pass).
+ *
+ * Conventions for every entry point:
+ *  - return TPCFIT_OK (0) or a negative TPCFIT_E_* code; tpcfit_strerror()
+ *    names it and tpcfit_last_error_message() gives detail for the calling
+ *    thread;
+ *  - the caller owns every frame and result buffer; the library owns its
+ *    handle, device scratch pools, streams and events;
+ *  - numerical failures of one track never fail a call: they are reported in
+ *    that track's status (TPCFIT_TRACK_*);
+ *  - one handle is driven by one caller thread at a time.
+ *
+ * Data layout (structure of arrays, one frame = one time frame or event batch):
+ *  clusters of track t are indices [track_offsets[t], track_offsets[t+1]) of
+ *  x, y, z, sy2, sz2 (float32, cm and cm^2) and row (uint8 pad-row index,
+ *  strictly ascending within a track); track_offsets is int64[n_tracks+1]
+ *  with track_offsets[0] == 0 and track_offsets[n_tracks] == n_clusters.
+ *  Results: state float32[n_tracks*5] = (y, z, sinphi, tanlambda, q/pT) at
+ *  x_ref (the innermost cluster's x); cov float32[n_tracks*15] packed lower
+ *  triangle (00,10,11,20,21,22,30,...,44); chi2 float64 (inward pass); ndf
+ *  int32 = 2*accepted_inward - 5; status int32; accept uint8[n_clusters]
+ *  (bit0 accepted in the outward pass, bit1 in the inward pass).
+ */
+#ifndef TPCFIT_H
+#define TPCFIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPCFIT_OK 0
+#define TPCFIT_E_INVAL (-1)    /* bad argument or malformed frame (offsets) */
+#define TPCFIT_E_NOMEM (-2)    /* device allocation failed, or a frame larger than the HBM budget */
+#define TPCFIT_E_CUDA (-3)     /* a CUDA runtime call failed */
+#define TPCFIT_E_TIMEOUT (-4)  /* a bounded wait expired */
+#define TPCFIT_E_BUSY (-5)     /* no free serving slot and the queue is full */
+#define TPCFIT_E_NOTFOUND (-6) /* unknown ticket */
+#define TPCFIT_E_NODEV (-7)    /* no CUDA device, or not an sm_103 device */
+
+#define TPCFIT_MEM_HOST 0      /* pointers are host memory (pinned gives overlapped copies) */
+#define TPCFIT_MEM_DEVICE 1    /* pointers are device memory of the handle's device */
+
+/* per-track status */
+#define TPCFIT_TRACK_OK 0
+#define TPCFIT_TRACK_TOO_FEW 1    /* fewer than max(min_clusters, 3) clusters */
+#define TPCFIT_TRACK_SNP_LIMIT 2  /* |sinphi| reached snp_max */
+#define TPCFIT_TRACK_NOT_PD 3     /* innovation matrix not positive definite */
+#define TPCFIT_TRACK_NONFINITE 4  /* non-finite cluster value, or non-finite fitted state */
+#define TPCFIT_TRACK_BAD_INPUT 5  /* rows not ascending, row >= n_rows, variance <= 0, bad offsets */
+
+/* ticket states for tpcfit_poll */
+#define TPCFIT_PENDING 0
+#define TPCFIT_DONE 1
+#define TPCFIT_FAILED 2
+
+typedef struct tpcfit_handle tpcfit_handle; /* opaque, library-owned */
+
+/* Fit and runtime parameters.  The fit parameters are readings of the method
+ * (the paper gives none): see tpcfit_default_config for the values used. */
+typedef struct tpcfit_config {
+  float bz_tesla;         /* solenoid field (0.5 T) */
+  float chi2_max;         /* gate on the 2-dof chi2 of one cluster; equality accepts (16) */
+  float xx0_per_row;      /* radiation length fraction per crossed pad row (5e-4; 0 disables scattering) */
+  float mass_gev;         /* particle mass for beta in the Highland formula (pion, 0.13957) */
+  float snp_max;          /* |sinphi| limit (0.999) */
+  float seed_cov[5];      /* seed covariance diagonal (1, 1, 0.01, 0.01, 1) */
+  float restart_scale;    /* inward restart covariance: diag(min(scale*C_out, seed_cov)) (100) */
+  int32_t min_clusters;   /* tracks with fewer clusters are not fitted (10) */
+  int32_t n_rows;         /* pad rows (152, at most 256) */
+  float row_x0_cm;        /* x of pad row 0 (85 cm) */
+  float row_pitch_cm;     /* row spacing (162/151 cm); row r lies at float(x0 + r*pitch) */
+  uint64_t hbm_budget_bytes; /* serving: device bytes that resident frames may use (120 GB) */
+  int32_t max_slots;      /* serving: frames resident at once (8) */
+  int32_t device;         /* CUDA device ordinal (0) */
+  int32_t block_threads;  /* fit kernel block size, 0 = tuned default */
+  int32_t blocks_per_sm;  /* fit kernel resident blocks per SM, 0 = occupancy maximum */
+  int32_t sort_tracks;    /* 1: fit tracks longest-first (default); 0: in frame order */
+  int32_t reserved[7];
+  int64_t host_chunk_clusters; /* host frames are copied and fitted in chunks of about this many clusters (16M) */
+} tpcfit_config;
+
+typedef struct tpcfit_frame {
+  int64_t n_tracks, n_clusters;
+  const int64_t *track_offsets; /* n_tracks+1 */
+  const float *x, *y, *z, *sy2, *sz2; /* n_clusters each */
+  const uint8_t *row;             /* n_clusters */
+  const uint8_t *sector;          /* n_tracks, may be NULL (informational only) */
+  int32_t mem;                    /* TPCFIT_MEM_HOST or TPCFIT_MEM_DEVICE */
+} tpcfit_frame;
+
+typedef struct tpcfit_result {
+  float *state;   /* n_tracks*5 */
+  float *cov;     /* n_tracks*15 */
+  float *x_ref;   /* n_tracks */
+  double *chi2;   /* n_tracks */
+  int32_t *ndf;   /* n_tracks */
+  int32_t *status;/* n_tracks */
+  uint8_t *accept;/* n_clusters */
+  int32_t mem;    /* TPCFIT_MEM_HOST or TPCFIT_MEM_DEVICE */
+  /* optional per-cluster chi2 of the outward and inward pass (NaN where the
+   * pass did not reach the cluster); NULL = not written.  Device results of
+   * tpcfit_fit / tpcfit_fit_async only (a host frame with these set is
+   * TPCFIT_E_INVAL; serving ignores them). */
+  double *chi2_out_cluster; /* n_clusters */
+  double *chi2_in_cluster;  /* n_clusters */
+} tpcfit_result;
+
+/* Kernel timings of the last completed fit on a handle (CUDA events on the
+ * stream the kernels ran on), in milliseconds. */
+typedef struct tpcfit_timing {
+  float prepare_ms, sort_ms, fit_ms, total_ms; /* last completed timed call */
+  int32_t kernel_launches;  /* kernels launched by the last call */
+  int32_t fit_grid, fit_block;
+  int32_t fit_regs;         /* registers per thread of the fit kernel */
+  int64_t n_timed;          /* timed calls accumulated since tpcfit_reset_timing */
+  double prepare_ms_sum, sort_ms_sum, fit_ms_sum, total_ms_sum;
+} tpcfit_timing;
+
+/* Fill *cfg with the defaults listed above.  Never fails. */
+void tpcfit_default_config(tpcfit_config *cfg);
+
+/* Create a handle on cfg->device (cfg NULL = defaults).  Fails with
+ * TPCFIT_E_NODEV if the device is missing or not compute capability 10.3,
+ * TPCFIT_E_INVAL on out-of-range parameters.  *out is set only on success. */
+int tpcfit_create(const tpcfit_config *cfg, tpcfit_handle **out);
+
+/* Fit one frame and block until the results are in *res (Sec. 5/6: the TPC
+ * track fit of one time frame).  Host frames are copied to device scratch in
+ * chunks overlapped with the fit; device frames are read in place.  Returns
+ * TPCFIT_E_INVAL for malformed offsets (results undefined), TPCFIT_E_NOMEM if
+ * scratch cannot be allocated. */
+int tpcfit_fit(tpcfit_handle *h, const tpcfit_frame *frame, tpcfit_result *res);
+
+/* Enqueue the fit of a DEVICE frame into DEVICE results on a caller stream
+ * (a cudaStream_t passed as void*, NULL = the handle's stream) and return
+ * without waiting.  The caller keeps the buffers alive until the stream
+ * reaches this point.  Offsets are checked on the device: a malformed frame
+ * marks its tracks BAD_INPUT and is reported by the next tpcfit_sync. */
+int tpcfit_fit_async(tpcfit_handle *h, const tpcfit_frame *frame, tpcfit_result *res, void *stream);
+
+/* Wait (bounded by timeout_s; < 0 = no bound) for the handle's enqueued work
+ * and report a malformed-frame error seen since the last sync. */
+int tpcfit_sync(tpcfit_handle *h, double timeout_s);
+
+/* Serving (Sec. 4 horizontal parallelism, Sec. 7 rate limiting by frames in
+ * flight): copy a host frame into a library-owned resident slot when the HBM
+ * budget and a slot allow, fit it overlapped with frames already on the
+ * device, and copy the results into *res (host memory).  Returns at once with
+ * a ticket; a frame larger than the whole budget fails with TPCFIT_E_NOMEM.
+ * *frame's and *res's buffers must stay valid until the ticket is DONE or
+ * FAILED. */
+int tpcfit_submit(tpcfit_handle *h, const tpcfit_frame *frame, tpcfit_result *res, uint64_t *ticket);
+
+/* State of a ticket: TPCFIT_PENDING, TPCFIT_DONE or TPCFIT_FAILED, and when
+ * done the completion time in seconds on the library's monotonic clock
+ * (tpcfit_now).  A finished ticket is forgotten after it is reported. */
+int tpcfit_poll(tpcfit_handle *h, uint64_t ticket, int *state, double *t_done_s);
+
+/* Block until a ticket finishes (bounded by timeout_s; < 0 = no bound). */
+int tpcfit_wait(tpcfit_handle *h, uint64_t ticket, double timeout_s, int *state, double *t_done_s);
+
+/* Library monotonic clock, seconds. */
+double tpcfit_now(void);
+
+/* Timings of the last completed device-frame fit (tpcfit_fit, or
+ * tpcfit_fit_async after the work completed) and sums over every timed call
+ * since tpcfit_reset_timing.  Waits for the handle's timed work to finish.
+ * TPCFIT_E_INVAL if nothing was timed yet. */
+int tpcfit_last_timing(tpcfit_handle *h, tpcfit_timing *out);
+
+/* Clear the accumulated timing sums. */
+int tpcfit_reset_timing(tpcfit_handle *h);
+
+/* Wait for all work, release every device resource and the handle. */
+int tpcfit_destroy(tpcfit_handle *h);
+
+/* Static description of an error code; never NULL. */
+const char *tpcfit_strerror(int code);
+
+/* Detail of the last error on the calling thread; never NULL. */
+const char *tpcfit_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPCFIT_H */

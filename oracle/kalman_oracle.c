@@ -21,6 +21,8 @@
  *   |sinphi| limit 0.999; MS after the (possible) update at every crossed row;
  *   inward pass restarts from the outward state with a diagonal covariance:
  *   the outward variances times restart_scale (100), capped at the seed's;
+ *   if the outward pass accepted fewer than half of the clusters it restarts
+ *   instead from a fresh three-point seed at the outermost cluster;
  *   outputs at the innermost cluster.
  * Status rule: clusters are validated when the outward pass reaches them, so the
  * first offending cluster decides; NaN never trips a numerical limit (it flows
@@ -62,7 +64,7 @@ typedef struct {
   double *chi2_out_c;  /* nc: chi2 of the cluster in the outward pass (NaN if not reached) */
   double *chi2_in_c;   /* nc: chi2 of the cluster in the inward pass */
   double *state_in_c;  /* nc*5: inward state after the cluster's update, before its scattering */
-  double *state_out_t; /* nt*5: outward state the inward pass restarts from */
+  double *state_out_t; /* nt*5: state the inward pass restarts from */
   double *restart_t;   /* nt*5: diagonal of the covariance the inward pass restarts with */
 } orc_result;
 
@@ -294,18 +296,36 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
     orc_ms_noise(p, C, c->xx0, c->mass);
   }
 
-  /* ---- inward pass: restart from the outward state with a diagonal covariance,
-     the outward variances inflated by restart_scale and capped at the seed's ---- */
-  if (o->state_out_t) for (int i = 0; i < 5; ++i) o->state_out_t[5 * t + i] = p[i];
+  /* ---- inward pass restart.  If the outward pass accepted at least half of
+     the clusters: from the outward state with a diagonal covariance, the
+     outward variances inflated by restart_scale and capped at the seed's.
+     Otherwise the outward pass is not trusted: a fresh three-point seed at the
+     outermost cluster (circle through clusters n-1, n/2, 0, taken for motion
+     from the outer end, then reversed) with the seed covariance. ---- */
   {
-    double d[5];
-    for (int i = 0; i < 5; ++i) {
-      d[i] = c->restart_scale * C[i * 5 + i];
-      if (!(d[i] <= c->seed_cov[i])) d[i] = c->seed_cov[i];
+    int nacc_out = 0;
+    for (int64_t k = a; k < e; ++k) nacc_out += o->accept[k] & 1;
+    if (2 * nacc_out < n) {
+      double A[3] = {x[e - 1], y[e - 1], z[e - 1]}, B[3] = {x[a + n / 2], y[a + n / 2], z[a + n / 2]},
+             D[3] = {x[a], y[a], z[a]};
+      orc_seed(A, B, D, c->bz, p);
+      /* the seed describes motion towards cluster 0: reversing the motion
+         flips the direction (sinphi), the dip (tanlambda) and the curvature */
+      p[2] = -p[2];
+      p[3] = -p[3];
+      p[4] = -p[4];
+      seed_cov(c, C);
+    } else {
+      double d[5];
+      for (int i = 0; i < 5; ++i) {
+        d[i] = c->restart_scale * C[i * 5 + i];
+        if (!(d[i] <= c->seed_cov[i])) d[i] = c->seed_cov[i];
+      }
+      for (int i = 0; i < 25; ++i) C[i] = 0.0;
+      for (int i = 0; i < 5; ++i) C[i * 5 + i] = d[i];
     }
-    for (int i = 0; i < 25; ++i) C[i] = 0.0;
-    for (int i = 0; i < 5; ++i) C[i * 5 + i] = d[i];
-    if (o->restart_t) for (int i = 0; i < 5; ++i) o->restart_t[5 * t + i] = d[i];
+    if (o->state_out_t) for (int i = 0; i < 5; ++i) o->state_out_t[5 * t + i] = p[i];
+    if (o->restart_t) for (int i = 0; i < 5; ++i) o->restart_t[5 * t + i] = C[i * 5 + i];
   }
   for (int64_t k = e - 1; k >= a; --k) {
     if (k < e - 1) {

@@ -1,0 +1,356 @@
+"""Batched TPC Kalman track fit on GB300: Python binding of libtpcfit (ctypes).
+
+Argument marshalling only: every step of the fit runs in the CUDA library
+(``csrc/``).  The functions mirror the C-ABI of ``include/tpcfit.h``
+(``create``, ``fit``, ``fit_async``, ``sync``, ``submit``, ``poll``, ``wait``,
+``destroy``); ``Fitter`` wraps a handle.  Frames are objects with ``offsets``,
+``x``, ``y``, ``z``, ``sy2``, ``sz2``, ``row`` arrays: CUDA torch tensors are
+passed as device memory, numpy arrays / CPU tensors as host memory.  PyTorch
+provides device memory and streams only.
+
+The library must be built (``_build.build()``); there is no fallback: a
+missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["TpcfitError", "Config", "default_config", "create", "destroy", "fit", "fit_async", "sync", "submit",
+           "poll", "wait", "last_timing", "reset_timing", "probe_fma_rates", "strerror", "now", "Fitter",
+           "library_path", "alloc_result", "STATUS_NAMES"]
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_NOTFOUND, E_NODEV = 0, -1, -2, -3, -4, -5, -6, -7
+MEM_HOST, MEM_DEVICE = 0, 1
+PENDING, DONE, FAILED = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT"}
+
+
+class TpcfitError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tpcfit error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("bz_tesla", ctypes.c_float), ("chi2_max", ctypes.c_float), ("xx0_per_row", ctypes.c_float),
+        ("mass_gev", ctypes.c_float), ("snp_max", ctypes.c_float), ("seed_cov", ctypes.c_float * 5),
+        ("restart_scale", ctypes.c_float), ("min_clusters", ctypes.c_int32), ("n_rows", ctypes.c_int32),
+        ("row_x0_cm", ctypes.c_float), ("row_pitch_cm", ctypes.c_float), ("hbm_budget_bytes", ctypes.c_uint64),
+        ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32), ("sort_tracks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("host_chunk_clusters", ctypes.c_int64),
+    ]
+
+
+class _Frame(ctypes.Structure):
+    _fields_ = [("n_tracks", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("track_offsets", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("sy2", ctypes.c_void_p),
+                ("sz2", ctypes.c_void_p), ("row", ctypes.c_void_p), ("sector", ctypes.c_void_p),
+                ("mem", ctypes.c_int32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("x_ref", ctypes.c_void_p),
+                ("chi2", ctypes.c_void_p), ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("accept", ctypes.c_void_p), ("mem", ctypes.c_int32), ("chi2_out_cluster", ctypes.c_void_p),
+                ("chi2_in_cluster", ctypes.c_void_p)]
+
+
+class _Timing(ctypes.Structure):
+    _fields_ = [("prepare_ms", ctypes.c_float), ("sort_ms", ctypes.c_float), ("fit_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int32), ("fit_grid", ctypes.c_int32),
+                ("fit_block", ctypes.c_int32), ("fit_regs", ctypes.c_int32), ("n_timed", ctypes.c_int64),
+                ("prepare_ms_sum", ctypes.c_double), ("sort_ms_sum", ctypes.c_double),
+                ("fit_ms_sum", ctypes.c_double), ("total_ms_sum", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libtpcfit.so is not built ({_build.LIB}); run paper_2402_01205_gb300._build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    H = ctypes.c_void_p
+    lib.tpcfit_default_config.argtypes = [ctypes.POINTER(Config)]
+    lib.tpcfit_default_config.restype = None
+    lib.tpcfit_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(H)]
+    lib.tpcfit_fit.argtypes = [H, ctypes.POINTER(_Frame), ctypes.POINTER(_Result)]
+    lib.tpcfit_fit_async.argtypes = [H, ctypes.POINTER(_Frame), ctypes.POINTER(_Result), ctypes.c_void_p]
+    lib.tpcfit_sync.argtypes = [H, ctypes.c_double]
+    lib.tpcfit_submit.argtypes = [H, ctypes.POINTER(_Frame), ctypes.POINTER(_Result), ctypes.POINTER(ctypes.c_uint64)]
+    lib.tpcfit_poll.argtypes = [H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.tpcfit_wait.argtypes = [H, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_double)]
+    lib.tpcfit_last_timing.argtypes = [H, ctypes.POINTER(_Timing)]
+    lib.tpcfit_reset_timing.argtypes = [H]
+    lib.tpcfit_probe_fma_rates.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    lib.tpcfit_destroy.argtypes = [H]
+    lib.tpcfit_strerror.argtypes = [ctypes.c_int]
+    lib.tpcfit_strerror.restype = ctypes.c_char_p
+    lib.tpcfit_last_error_message.argtypes = []
+    lib.tpcfit_last_error_message.restype = ctypes.c_char_p
+    lib.tpcfit_now.argtypes = []
+    lib.tpcfit_now.restype = ctypes.c_double
+    for fn in ("tpcfit_create", "tpcfit_fit", "tpcfit_fit_async", "tpcfit_sync", "tpcfit_submit", "tpcfit_poll",
+               "tpcfit_wait", "tpcfit_last_timing", "tpcfit_reset_timing", "tpcfit_destroy",
+               "tpcfit_probe_fma_rates"):
+        getattr(lib, fn).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        lib = _load()
+        raise TpcfitError(rc, f"{lib.tpcfit_strerror(rc).decode()}: {lib.tpcfit_last_error_message().decode()}")
+    return rc
+
+
+def strerror(code: int) -> str:
+    return _load().tpcfit_strerror(code).decode()
+
+
+def now() -> float:
+    return _load().tpcfit_now()
+
+
+def default_config(**overrides) -> Config:
+    cfg = Config()
+    _load().tpcfit_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "seed_cov":
+            cfg.seed_cov = (ctypes.c_float * 5)(*v)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return a.ctypes.data
+
+
+_DT = {"offsets": "int64", "x": "float32", "y": "float32", "z": "float32", "sy2": "float32", "sz2": "float32",
+       "row": "uint8"}
+
+
+def _mem_of(arrs) -> int:
+    dev = [_is_torch(a) and a.is_cuda for a in arrs]
+    if all(dev):
+        return MEM_DEVICE
+    if not any(dev):
+        return MEM_HOST
+    raise ValueError("frame arrays must all be on the GPU or all on the host")
+
+
+def _check_dtypes(obj, names):
+    for k in names:
+        a = getattr(obj, k)
+        dt = str(a.dtype).replace("torch.", "")
+        if dt != _DT.get(k, dt):
+            raise TypeError(f"{k} must be {_DT[k]}, got {dt}")
+
+
+def _frame_struct(frame) -> tuple:
+    names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
+    arrs = [getattr(frame, k) for k in names]
+    _check_dtypes(frame, names)
+    mem = _mem_of(arrs)
+    nt = int(arrs[0].shape[0]) - 1
+    nc = int(arrs[1].shape[0])
+    for k, a in zip(names[1:], arrs[1:]):
+        if int(a.shape[0]) != nc:
+            raise ValueError(f"{k} has {a.shape[0]} entries, x has {nc}")
+    f = _Frame(nt, nc, _ptr(arrs[0]), *[_ptr(a) for a in arrs[1:]], 0, mem)
+    return f, mem, nt, nc
+
+
+def alloc_result(n_tracks: int, n_clusters: int, device=None, pinned: bool = False) -> dict:
+    """Result buffers: torch tensors on ``device`` (CUDA) or numpy arrays on the host."""
+    if device is not None:
+        import torch
+        mk = lambda shape, dt: torch.empty(shape, dtype=dt, device=device)  # noqa: E731
+        return dict(state=mk((n_tracks, 5), torch.float32), cov=mk((n_tracks, 15), torch.float32),
+                    x_ref=mk((n_tracks,), torch.float32), chi2=mk((n_tracks,), torch.float64),
+                    ndf=mk((n_tracks,), torch.int32), status=mk((n_tracks,), torch.int32),
+                    accept=mk((n_clusters,), torch.uint8))
+    if pinned:
+        import torch
+        mk = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True)  # noqa: E731
+        return dict(state=mk((n_tracks, 5), torch.float32), cov=mk((n_tracks, 15), torch.float32),
+                    x_ref=mk((n_tracks,), torch.float32), chi2=mk((n_tracks,), torch.float64),
+                    ndf=mk((n_tracks,), torch.int32), status=mk((n_tracks,), torch.int32),
+                    accept=mk((n_clusters,), torch.uint8))
+    return dict(state=np.empty((n_tracks, 5), np.float32), cov=np.empty((n_tracks, 15), np.float32),
+                x_ref=np.empty(n_tracks, np.float32), chi2=np.empty(n_tracks, np.float64),
+                ndf=np.empty(n_tracks, np.int32), status=np.empty(n_tracks, np.int32),
+                accept=np.empty(n_clusters, np.uint8))
+
+
+def _result_struct(res: dict) -> tuple:
+    names = ("state", "cov", "x_ref", "chi2", "ndf", "status", "accept")
+    arrs = [res[k] for k in names]
+    mem = _mem_of(arrs)
+    extra = [_ptr(res.get(k)) for k in ("chi2_out_cluster", "chi2_in_cluster")]
+    return _Result(*[_ptr(a) for a in arrs], mem, *extra), mem
+
+
+# ---------------------------------------------------------------- C-ABI mirror
+def create(config: Optional[Config] = None) -> int:
+    lib = _load()
+    h = ctypes.c_void_p()
+    _check(lib.tpcfit_create(ctypes.byref(config) if config is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def destroy(handle: int) -> None:
+    _check(_load().tpcfit_destroy(handle))
+
+
+def fit(handle: int, frame, res: dict) -> dict:
+    f, _, _, _ = _frame_struct(frame)
+    r, _ = _result_struct(res)
+    _check(_load().tpcfit_fit(handle, ctypes.byref(f), ctypes.byref(r)))
+    return res
+
+
+def fit_async(handle: int, frame, res: dict, stream=None) -> dict:
+    """Enqueue on a torch.cuda.Stream (or raw cudaStream_t int, or None)."""
+    f, _, _, _ = _frame_struct(frame)
+    r, _ = _result_struct(res)
+    s = getattr(stream, "cuda_stream", stream)
+    _check(_load().tpcfit_fit_async(handle, ctypes.byref(f), ctypes.byref(r), s))
+    return res
+
+
+def sync(handle: int, timeout_s: float = -1.0) -> None:
+    _check(_load().tpcfit_sync(handle, timeout_s))
+
+
+def submit(handle: int, frame, res: dict) -> int:
+    f, _, _, _ = _frame_struct(frame)
+    r, _ = _result_struct(res)
+    t = ctypes.c_uint64()
+    _check(_load().tpcfit_submit(handle, ctypes.byref(f), ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def poll(handle: int, ticket: int) -> tuple:
+    st, td = ctypes.c_int(), ctypes.c_double()
+    _check(_load().tpcfit_poll(handle, ticket, ctypes.byref(st), ctypes.byref(td)))
+    return st.value, td.value
+
+
+def wait(handle: int, ticket: int, timeout_s: float = -1.0) -> tuple:
+    st, td = ctypes.c_int(), ctypes.c_double()
+    _check(_load().tpcfit_wait(handle, ticket, timeout_s, ctypes.byref(st), ctypes.byref(td)))
+    return st.value, td.value
+
+
+def last_timing(handle: int) -> dict:
+    t = _Timing()
+    _check(_load().tpcfit_last_timing(handle, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in _Timing._fields_}
+
+
+def reset_timing(handle: int) -> None:
+    _check(_load().tpcfit_reset_timing(handle))
+
+
+def probe_fma_rates(device: int = 0) -> dict:
+    """Measured FP64 / FP32 FMA lane-operations per second and the SM clock (kHz)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(_load().tpcfit_probe_fma_rates(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(fp64_fma_per_s=a.value, fp32_fma_per_s=b.value, sm_clock_khz=c.value)
+
+
+class Fitter:
+    """Owns one library handle."""
+
+    def __init__(self, config: Optional[Config] = None, **overrides):
+        if config is None:
+            config = default_config(**overrides)
+        self.config = config
+        self.handle = create(config)
+        self._inflight = {}  # ticket -> (frame, result): buffers must outlive the ticket
+
+    def fit(self, frame, res: Optional[dict] = None) -> dict:
+        f, mem, nt, nc = _frame_struct(frame)
+        if res is None:
+            res = alloc_result(nt, nc, device=frame.x.device if mem == MEM_DEVICE else None)
+        return fit(self.handle, frame, res)
+
+    def fit_async(self, frame, res: dict, stream=None) -> dict:
+        return fit_async(self.handle, frame, res, stream)
+
+    def sync(self, timeout_s: float = -1.0) -> None:
+        sync(self.handle, timeout_s)
+
+    def submit(self, frame, res: dict) -> int:
+        t = submit(self.handle, frame, res)
+        self._inflight[t] = (frame, res)
+        return t
+
+    def poll(self, ticket: int) -> tuple:
+        st = poll(self.handle, ticket)
+        if st[0] != PENDING:
+            self._inflight.pop(ticket, None)
+        return st
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> tuple:
+        st = wait(self.handle, ticket, timeout_s)
+        if st[0] != PENDING:
+            self._inflight.pop(ticket, None)
+        return st
+
+    def timing(self) -> dict:
+        return last_timing(self.handle)
+
+    def reset_timing(self) -> None:
+        reset_timing(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            destroy(self.handle)  # waits for every ticket
+            self.handle = None
+            self._inflight.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,687 @@
+// CUDA kernels of the batched TPC Kalman track fit (sm_103a).
+//
+// The paper (Sec. 5, Tables 1-2; Sec. 6) puts full TPC tracking on the GPU as
+// the dominant reconstruction step; the fit computed here is the textbook
+// Kalman track fit (Fruhwirth 1987) with an exact helix in a uniform field and
+// PDG Highland scattering, in an outward then an inward pass.
+//
+// Launch sequence of one frame:
+//   k_prepare   thread per track: offset checks, 3-point seed, status preset,
+//               sort key (cluster count) histogram
+//   k_sort_*    counting sort of tracks by cluster count, longest first
+//   k_fit       persistent grid; each warp claims 32 consecutive tracks of the
+//               sorted order, one thread per track, and steps cluster by
+//               cluster through the outward and the inward pass.
+//
+// Precision: propagation, covariance transport and the gain/update are FP32.
+// The innovation-matrix determinant and reciprocal, the quadratic form
+// chi2 = r^T S^-1 r, the gate decision and the chi2 sum are FP64.  GB300
+// executes FP64 at ~1/64 of the FP32 rate and a warp-wide FP64 instruction
+// costs the same with one active lane as with 32, so the FP64 island is kept
+// to 11 instructions per update, every FP32->FP64 widening is done exactly
+// with integer operations, and warps are filled with tracks of equal length
+// so that every FP64 instruction serves 32 updates.
+//
+// Track positions are carried as FP32 offsets (dy, dz) from the last
+// cluster's coordinates: residuals are then formed from small numbers and the
+// chi2 near the gate keeps FP64-level agreement with an FP64 fit.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tpcfit_internal.h"
+
+namespace tpcfit {
+
+enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5 };
+
+constexpr int kFitBlock = 256;
+constexpr int kWarpsPerBlock = kFitBlock / 32;
+constexpr int kBitWords = kMaxRows / 32;  // outward accept bits of one track (<= 256 clusters)
+constexpr int kChunk = 4;                 // clusters per staged chunk (per lane)
+constexpr int kStageArrays = 5;           // x, y, z, sy2, sz2
+// dynamic shared memory of k_fit: row table, outward accept bits, staged clusters
+constexpr size_t kSmemRowx = kMaxRows * sizeof(float);
+constexpr size_t kSmemBits = (size_t)kWarpsPerBlock * kBitWords * 32 * sizeof(uint32_t);
+constexpr size_t kSmemStage = (size_t)2 * kStageArrays * kChunk * kFitBlock * sizeof(float);
+constexpr size_t kFitSmem = kSmemRowx + kSmemBits + kSmemStage;
+
+// 4-byte asynchronous global->shared copy (zero-fill when !valid; the source
+// address is then still a valid element and is not read).
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Exact binary32 -> binary64 widening with integer operations (IEEE 754: the
+// exponent is re-biased by 1023-127 = 896, the 23-bit fraction moves to the
+// top of the 52-bit fraction).  Zero and subnormal inputs give a signed zero;
+// Inf/NaN keep their class.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t mag = u & 0x7fffffffu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint64_t bias = (mag >= 0x7f800000u) ? (1792ull << 23) : (896ull << 23);
+  uint64_t d = (((uint64_t)mag + bias) << 29) | sign;
+  d = (mag < 0x00800000u) ? sign : d;
+  return __longlong_as_double((long long)d);
+}
+
+// Non-negative binary64 -> binary32, round to nearest even, with integer
+// operations only: values below the binary32 normal range flush to zero,
+// values above it give +Inf, NaN stays NaN.  (The inputs are reciprocals of
+// positive determinants.)
+__device__ __forceinline__ float narrow_pos(double v) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  const uint32_t ex = (uint32_t)(b >> 52);
+  const uint64_t r = b + 0x0FFFFFFFull + ((b >> 29) & 1ull);
+  uint32_t f = (uint32_t)(r >> 29) - (896u << 23);
+  f = (ex > 1150u) ? 0x7f800000u : f;
+  f = (ex < 897u) ? 0u : f;
+  f = (b > 0x7ff0000000000000ull) ? 0x7fc00000u : f;
+  return __uint_as_float(f);
+}
+
+// Error-free sum of two binary32 numbers (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// ---------------------------------------------------------------------------
+// Seed: circle through three clusters (a, b, c) in the (x, y) plane; state at a.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float asin_over_u_f(float u) {
+  const float u2 = u * u;
+  if (fabsf(u) < 0.1f) return 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
+  return asinf(u) / u;
+}
+
+__device__ __noinline__ void seed3(float xa, float ya, float za, float xb, float yb, float xc, float yc, float zc, float b,
+                      float p[5]) {
+  const float abx = xb - xa, aby = yb - ya, acx = xc - xa, acy = yc - ya, bcx = xc - xb, bcy = yc - yb;
+  const float cross = abx * acy - aby * acx;
+  const float lab = sqrtf(abx * abx + aby * aby), lac = sqrtf(acx * acx + acy * acy),
+              lbc = sqrtf(bcx * bcx + bcy * bcy);
+  const float kappa = 2.0f * cross / (lab * lac * lbc);
+  float u = 0.5f * kappa * lac;
+  u = fminf(1.0f, fmaxf(-1.0f, u));
+  const float phi = atan2f(acy, acx) - asinf(u);
+  const float s_ac = lac * asin_over_u_f(u);
+  p[0] = ya;
+  p[1] = za;
+  p[2] = sinf(phi);
+  p[3] = (zc - za) / s_ac;
+  p[4] = kappa / b;  // q/pT = -kappa/(kB Bz) = kappa / b
+}
+
+// ---------------------------------------------------------------------------
+// k_prepare: per-track offset checks, status preset, seed, key histogram.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_prepare(FitArgs A) {
+  __shared__ uint32_t s_hist[kKeyBins];
+  for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < A.n_tracks) {
+    if (t == 0 && (A.off[0] - A.off_base != 0 || A.off[A.n_tracks] - A.off_base != A.n_clusters))
+      atomicOr(A.frame_error, 1);
+    const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
+    int st = ST_OK;
+    int64_t n = 0;
+    if (a < 0 || e < a || e > A.n_clusters) {
+      st = ST_BAD_INPUT;
+      atomicOr(A.frame_error, 1);
+    } else {
+      n = e - a;
+      if (n < A.min_clusters || n < 3) st = ST_TOO_FEW;
+    }
+    float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (st == ST_OK) {
+      const int64_t m = a + n / 2, l = e - 1;
+      seed3(A.x[a], A.y[a], A.z[a], A.x[m], A.y[m], A.x[l], A.y[l], A.z[l], A.b, p);
+      if (fabsf(p[2]) >= A.snp_max) st = ST_SNP_LIMIT;  // NaN passes
+    }
+    float *sd = A.seed + 5 * t;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) sd[i] = p[i];
+    A.status[t] = st;
+    const int key = (st == ST_OK) ? (int)(n < kMaxRows ? n : kMaxRows) : 0;
+    atomicAdd(&s_hist[key], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(&A.hist[i], s_hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Counting sort by key, descending: exclusive scan of the histogram (one block)
+// then a block-aggregated scatter.
+// ---------------------------------------------------------------------------
+__global__ void k_sort_scan(uint32_t *hist) {
+  // hist[0..kKeyBins) counts -> hist[kKeyBins..2*kKeyBins) start positions, key descending
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int k = kKeyBins - 1; k >= 0; --k) {
+      hist[kKeyBins + k] = acc;
+      acc += hist[k];
+    }
+  }
+}
+
+__device__ __forceinline__ int track_key(const FitArgs &A, int64_t t) {
+  if (A.status[t] != ST_OK) return 0;
+  const int64_t n = A.off[t + 1] - A.off[t];
+  return (int)(n < kMaxRows ? n : kMaxRows);
+}
+
+__global__ void __launch_bounds__(256) k_sort_scatter(FitArgs A) {
+  __shared__ uint32_t s_cnt[kKeyBins];
+  __shared__ uint32_t s_base[kKeyBins];
+  for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int key = 0;
+  uint32_t rank = 0;
+  if (t < A.n_tracks) {
+    key = track_key(A, t);
+    rank = atomicAdd(&s_cnt[key], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x)
+    s_base[i] = s_cnt[i] ? atomicAdd(&A.hist[kKeyBins + i], s_cnt[i]) : 0u;
+  __syncthreads();
+  if (t < A.n_tracks) A.perm[s_base[key] + rank] = (int32_t)t;
+}
+
+// ---------------------------------------------------------------------------
+// Fit of one track: device helpers.
+// ---------------------------------------------------------------------------
+// Track state in FP32 with extended precision where the Kalman recursion
+// accumulates many small increments onto a large value:
+//  - y, z:       offsets (dy, dz) from the last cluster's coordinates (ya, za)
+//  - sinphi:     compensated sum sp + spl (TwoSum on every increment)
+//  - tanlambda:  anchor tl0 + offset dtl;  q/pT: anchor w0 + offset dw
+struct Trk {
+  float dy, dz, sp, spl, tl0, dtl, w0, dw;
+  float ya, za;
+  float c[15];  // covariance, packed lower triangle
+  __device__ __forceinline__ float tl() const { return tl0 + dtl; }
+  __device__ __forceinline__ float w() const { return w0 + dw; }
+  __device__ __forceinline__ float snp() const { return sp + spl; }
+};
+
+// Exact helix transport x1 -> x1+dx with Jacobian applied to the covariance.
+// Returns false on the |sinphi| limit (NaN passes).
+__device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_max) {
+  const float tl = T.tl();
+  const float C = b * T.w();
+  const float s1 = T.snp(), s2 = fmaf(C, dx, s1);
+  if (fabsf(s1) >= snp_max || fabsf(s2) >= snp_max) return false;
+  const float q1 = fmaf(-s1, s1, 1.0f), q2 = fmaf(-s2, s2, 1.0f);
+  const float ic1 = rsqrtf(q1), ic2 = rsqrtf(q2);
+  const float c1 = q1 * ic1, c2 = q2 * ic2;  // cos phi at both planes
+  const float iB = __frcp_rn(c1 + c2);
+  const float Tn = (s1 + s2) * iB;           // tangent of the chord direction
+  const float kk2 = fmaf(Tn, Tn, 1.0f);
+  const float ik = rsqrtf(kk2);
+  const float L = dx * (kk2 * ik);           // signed chord
+  const float u = 0.5f * C * L;
+  const float u2 = u * u;
+  float g, h;
+  if (fabsf(u) < 0.1f) {
+    g = 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
+    h = 1.0f / 6.0f + u2 * (3.0f / 20.0f + u2 * (15.0f / 112.0f + u2 * (35.0f / 288.0f)));
+  } else {
+    g = asinf(u) / u;
+    h = (rsqrtf(1.0f - u2) - g) / (2.0f * u2);
+  }
+  const float sT = L * g;                    // signed transverse arc length
+  T.dy = fmaf(dx, Tn, T.dy);
+  T.dz = fmaf(tl, sT, T.dz);
+  {  // sinphi += C dx, compensated
+    float hi, e;
+    two_sum(T.sp, C * dx, hi, e);
+    T.sp = hi;
+    T.spl += e;
+  }
+  // Jacobian
+  const float Q = fmaf(c1, c2, fmaf(s1, s2, 1.0f)) * iB * iB;
+  const float dTds = Q * (ic1 + ic2);
+  const float bdx = b * dx;
+  const float dTdw = Q * ic2 * bdx;
+  const float Jys = dx * dTds, Jyw = dx * dTdw;
+  const float dsdL = rsqrtf(fmaf(-u, u, 1.0f));
+  const float dLdT = dx * Tn * ik;
+  const float dsdC = L * L * u * h;
+  const float a1 = dsdL * dLdT;
+  const float Jzs = tl * a1 * dTds;
+  const float Jzt = sT;
+  const float Jzw = tl * fmaf(a1, dTdw, dsdC * b);
+  const float Jsw = bdx;
+  float *c = T.c;
+  // F C (rows 0..2 differ from C), entries needed by F C F^T
+  const float FC00 = fmaf(Jys, c[3], fmaf(Jyw, c[10], c[0]));
+  const float FC02 = fmaf(Jys, c[5], fmaf(Jyw, c[12], c[3]));
+  const float FC04 = fmaf(Jys, c[12], fmaf(Jyw, c[14], c[10]));
+  const float FC10 = fmaf(Jzs, c[3], fmaf(Jzt, c[6], fmaf(Jzw, c[10], c[1])));
+  const float FC11 = fmaf(Jzs, c[4], fmaf(Jzt, c[7], fmaf(Jzw, c[11], c[2])));
+  const float FC12 = fmaf(Jzs, c[5], fmaf(Jzt, c[8], fmaf(Jzw, c[12], c[4])));
+  const float FC13 = fmaf(Jzs, c[8], fmaf(Jzt, c[9], fmaf(Jzw, c[13], c[7])));
+  const float FC14 = fmaf(Jzs, c[12], fmaf(Jzt, c[13], fmaf(Jzw, c[14], c[11])));
+  const float FC20 = fmaf(Jsw, c[10], c[3]);
+  const float FC21 = fmaf(Jsw, c[11], c[4]);
+  const float FC22 = fmaf(Jsw, c[12], c[5]);
+  const float FC23 = fmaf(Jsw, c[13], c[8]);
+  const float FC24 = fmaf(Jsw, c[14], c[12]);
+  // (F C) F^T, lower triangle; rows 3 and 4 of F C equal those of C
+  const float n30 = fmaf(Jys, c[8], fmaf(Jyw, c[13], c[6]));
+  const float n31 = fmaf(Jzs, c[8], fmaf(Jzt, c[9], fmaf(Jzw, c[13], c[7])));
+  const float n32 = fmaf(Jsw, c[13], c[8]);
+  const float n40 = fmaf(Jys, c[12], fmaf(Jyw, c[14], c[10]));
+  const float n41 = fmaf(Jzs, c[12], fmaf(Jzt, c[13], fmaf(Jzw, c[14], c[11])));
+  const float n42 = fmaf(Jsw, c[14], c[12]);
+  c[0] = fmaf(Jys, FC02, fmaf(Jyw, FC04, FC00));
+  c[1] = fmaf(Jys, FC12, fmaf(Jyw, FC14, FC10));
+  c[2] = fmaf(Jzs, FC12, fmaf(Jzt, FC13, fmaf(Jzw, FC14, FC11)));
+  c[3] = fmaf(Jys, FC22, fmaf(Jyw, FC24, FC20));
+  c[4] = fmaf(Jzs, FC22, fmaf(Jzt, FC23, fmaf(Jzw, FC24, FC21)));
+  c[5] = fmaf(Jsw, FC24, FC22);
+  c[6] = n30;
+  c[7] = n31;
+  c[8] = n32;
+  c[10] = n40;
+  c[11] = n41;
+  c[12] = n42;
+  // c[9], c[13], c[14] unchanged
+  return true;
+}
+
+// Highland multiple-scattering noise of one pad row.
+__device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
+  const float s = T.snp(), t = T.tl(), w = T.w();
+  const float tt = fmaf(t, t, 1.0f);
+  const float cs2 = fmaf(-s, s, 1.0f);
+  const float itt = __frcp_rn(tt);
+  const float pinv2 = w * w * itt;                  // 1/p^2
+  const float ib2 = fmaf(mass2, pinv2, 1.0f);       // 1/beta^2
+  const float eps = xx0 * sqrtf(tt * __frcp_rn(cs2));
+  const float lg = fmaf(0.038f, __logf(eps * ib2), 1.0f);
+  const float th2 = (0.0136f * 0.0136f) * pinv2 * ib2 * eps * lg * lg;
+  T.c[5] = fmaf(th2, cs2 * tt, T.c[5]);
+  T.c[9] = fmaf(th2, tt * tt, T.c[9]);
+  T.c[14] = fmaf(th2, w * w * t * t, T.c[14]);
+  T.c[13] = fmaf(th2, tt * w * t, T.c[13]);
+}
+
+// Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: det,
+// reciprocal (Newton step from an FP32 seed), quadratic form, chi2 product,
+// gate; the chi2 sum is done by the caller.  Returns the status (OK / NOT_PD).
+__device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, long long gate_bits,
+                                      bool &acc, double &chi2) {
+  float *c = T.c;
+  const float r0 = (yc - T.ya) - T.dy;
+  const float r1 = (zc - T.za) - T.dz;
+  const float S00 = c[0] + vy, S10 = c[1], S11 = c[2] + vz;
+  // ---- FP64 island ----
+  const double s00 = widen(S00), s10 = widen(S10), s11 = widen(S11);
+  const double m2s10 = widen(-2.0f * S10);  // exact: scaling by -2
+  const double q0 = widen(r0), q1 = widen(r1);
+  const double det = fma(s00, s11, -(s10 * s10));
+  const long long db = __double_as_longlong(det);
+  const bool notpd = (db <= 0ll && (db & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) || S00 <= 0.0f;
+  const float det32 = fmaf(S00, S11, -(S10 * S10));
+  const double y0 = widen(__frcp_rn(det32));
+  const double ey = fma(-det, y0, 1.0);
+  const double inv = fma(y0, ey, y0);      // 1/det, one Newton step
+  double qf = fma(m2s10, q1, s11 * q0);    // s11 r0 - 2 s10 r1
+  qf = q0 * qf;
+  qf = fma(s00 * q1, q1, qf);              // r^T adj(S) r
+  chi2 = qf * inv;
+  const long long cb = __double_as_longlong(chi2);
+  acc = (cb <= gate_bits) && ((cb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll);
+  // ---- back to FP32 ----
+  if (notpd) {
+    acc = false;
+    return ST_NOT_PD;
+  }
+  const float i32 = narrow_pos(inv);
+  const float Si00 = S11 * i32, Si10 = -S10 * i32, Si11 = S00 * i32;
+  if (acc) {
+    float K0[5], K1[5];
+    const int col0[5] = {0, 1, 3, 6, 10}, col1[5] = {1, 2, 4, 7, 11};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const float ci0 = c[col0[i]], ci1 = c[col1[i]];
+      K0[i] = fmaf(ci0, Si00, ci1 * Si10);
+      K1[i] = fmaf(ci0, Si10, ci1 * Si11);
+    }
+    // new position offsets relative to this cluster (the new anchor)
+    T.dy = fmaf(K0[0] - 1.0f, r0, K1[0] * r1);
+    T.dz = fmaf(K0[1], r0, (K1[1] - 1.0f) * r1);
+    {
+      float hi, e;
+      two_sum(T.sp, fmaf(K0[2], r0, fmaf(K1[2], r1, T.spl)), hi, e);
+      T.sp = hi;
+      T.spl = e;
+    }
+    T.dtl = fmaf(K0[3], r0, fmaf(K1[3], r1, T.dtl));
+    T.dw = fmaf(K0[4], r0, fmaf(K1[4], r1, T.dw));
+    // C -= K (H C).  For the measured columns (j = y, z) this equals K V
+    // exactly (C_iH - C_iH S^-1 C_HH = C_iH S^-1 V), computed without
+    // cancellation; the angle block uses the subtraction form.
+    float h0[5], h1[5];
+#pragma unroll
+    for (int j = 2; j < 5; ++j) {
+      h0[j] = c[col0[j]];
+      h1[j] = c[col1[j]];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      c[col0[i]] = K0[i] * vy;  // C'(i,0)
+      if (i >= 1) c[col1[i]] = K1[i] * vz;  // C'(i,1)
+    }
+    c[5] = fmaf(-K0[2], h0[2], fmaf(-K1[2], h1[2], c[5]));
+    c[8] = fmaf(-K0[3], h0[2], fmaf(-K1[3], h1[2], c[8]));
+    c[9] = fmaf(-K0[3], h0[3], fmaf(-K1[3], h1[3], c[9]));
+    c[12] = fmaf(-K0[4], h0[2], fmaf(-K1[4], h1[2], c[12]));
+    c[13] = fmaf(-K0[4], h0[3], fmaf(-K1[4], h1[3], c[13]));
+    c[14] = fmaf(-K0[4], h0[4], fmaf(-K1[4], h1[4], c[14]));
+  } else {
+    T.dy = -r0;
+    T.dz = -r1;
+  }
+  T.ya = yc;
+  T.za = zc;
+  return ST_OK;
+}
+
+__device__ __forceinline__ bool finite5(float a, float b, float c, float d, float e) {
+  return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e);
+}
+
+// ---------------------------------------------------------------------------
+// k_fit: persistent warps over the (sorted) track list.
+// ---------------------------------------------------------------------------
+// Issue the copies of chunk c (clusters a+4c .. a+4c+3, clipped to the track)
+// into buffer c&1 of this lane's staging columns; returns the chunk's rows
+// packed in one word (loaded now, used one chunk later).
+__device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, float *stg) {
+  const int buf = c & 1;
+  uint32_t rows = 0;
+#pragma unroll
+  for (int s = 0; s < kChunk; ++s) {
+    const int64_t k = a + (int64_t)kChunk * c + s;
+    const bool v = k < e;
+    const int64_t kk = v ? k : e - 1;
+    float *dst = stg + ((buf * kStageArrays) * kChunk + s) * kFitBlock;
+    cp_async4(dst + 0 * kChunk * kFitBlock, A.x + kk, v);
+    cp_async4(dst + 1 * kChunk * kFitBlock, A.y + kk, v);
+    cp_async4(dst + 2 * kChunk * kFitBlock, A.z + kk, v);
+    cp_async4(dst + 3 * kChunk * kFitBlock, A.sy2 + kk, v);
+    cp_async4(dst + 4 * kChunk * kFitBlock, A.sz2 + kk, v);
+    rows |= (v ? (uint32_t)A.row[kk] : 0u) << (8 * s);
+  }
+  cp_async_commit();
+  return rows;
+}
+
+__device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
+  const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
+  const int st0 = A.status[t];
+  const float *sd = A.seed + 5 * t;
+  Trk T;
+  T.sp = sd[2];
+  T.spl = 0.f;
+  T.tl0 = sd[3];
+  T.dtl = 0.f;
+  T.w0 = sd[4];
+  T.dw = 0.f;
+  T.dy = 0.f;
+  T.dz = 0.f;
+  T.ya = 0.f;
+  T.za = 0.f;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+  T.c[0] = A.seed_cov[0];
+  T.c[2] = A.seed_cov[1];
+  T.c[5] = A.seed_cov[2];
+  T.c[9] = A.seed_cov[3];
+  T.c[14] = A.seed_cov[4];
+  int st = st0;
+  double chi2sum = 0.0;
+  int nacc = 0;
+  float xref = 0.f;
+  if (st0 != ST_BAD_INPUT) {  // BAD_INPUT here = offsets out of range: touch nothing of the frame
+    const int n = (int)(e - a);
+    if (n > 0) {
+      T.ya = A.y[a];
+      T.za = A.z[a];
+      xref = A.x[a];
+    }
+    float xcur = xref;
+#pragma unroll
+    for (int w = 0; w < kBitWords; ++w) bits[32 * w] = 0u;
+    int done = 0;     // clusters (from the outer end) whose accept byte is final
+    int out_done = 0; // clusters the outward pass updated with
+    int nacc_out = 0; // ... and accepted
+    if (st0 == ST_OK) {
+      const long long gate_bits = __double_as_longlong(A.chi2_max_d);
+      int rprev = -1;
+      // clusters staged through shared memory, two chunks of kChunk in flight
+      const int nch = (n + kChunk - 1) / kChunk;
+      uint32_t rows_cur = stage_chunk(A, a, e, 0, stg), rows_next = 0;
+      cp_async_wait_all();
+      if (nch > 1) rows_next = stage_chunk(A, a, e, 1, stg);
+      for (int j = 0; j < 2 * n; ++j) {
+        const bool inward = j >= n;
+        const int lk = inward ? (2 * n - 1 - j) : j;
+        const int64_t k = a + lk;
+        const int ch = lk / kChunk, slot = lk % kChunk;
+        if (!inward) {
+          if (slot == 0 && j > 0) {  // entering chunk ch from ch-1
+            cp_async_wait_all();
+            rows_cur = rows_next;
+            if (ch + 1 < nch) rows_next = stage_chunk(A, a, e, ch + 1, stg);
+          }
+        } else if (j == n) {  // still in the last chunk; restage the one before it
+          if (nch > 1) rows_next = stage_chunk(A, a, e, nch - 2, stg);
+        } else if (slot == kChunk - 1) {  // entering chunk ch from ch+1
+          cp_async_wait_all();
+          rows_cur = rows_next;
+          if (ch > 0) rows_next = stage_chunk(A, a, e, ch - 1, stg);
+        }
+        const float *src = stg + (((ch & 1) * kStageArrays) * kChunk + slot) * kFitBlock;
+        const float xk = src[0], yk = src[kChunk * kFitBlock], zk = src[2 * kChunk * kFitBlock];
+        const float vyk = src[3 * kChunk * kFitBlock], vzk = src[4 * kChunk * kFitBlock];
+        const int rk = (rows_cur >> (8 * slot)) & 0xffu;
+        if (!inward) {  // validation when the outward pass reaches the cluster
+          if (rk >= A.n_rows || rk <= rprev) { st = ST_BAD_INPUT; break; }
+          if (!finite5(xk, yk, zk, vyk, vzk)) { st = ST_NONFINITE; break; }
+          if (!(vyk > 0.f) || !(vzk > 0.f)) { st = ST_BAD_INPUT; break; }
+        }
+        if (j == n) {
+          if (2 * nacc_out < n) {
+            // the outward pass accepted fewer than half of the clusters: re-seed
+            // at the outermost cluster (circle through clusters n-1, n/2, 0 for
+            // motion towards cluster 0, reversed) with the seed covariance
+            float p[5];
+            const int64_t m = a + n / 2;
+            seed3(xk, yk, zk, A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
+            T.sp = -p[2];
+            T.spl = 0.f;
+            T.tl0 = -p[3];
+            T.dtl = 0.f;
+            T.w0 = -p[4];
+            T.dw = 0.f;
+            T.ya = yk;
+            T.za = zk;
+            T.dy = 0.f;
+            T.dz = 0.f;
+#pragma unroll
+            for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+            T.c[0] = A.seed_cov[0];
+            T.c[2] = A.seed_cov[1];
+            T.c[5] = A.seed_cov[2];
+            T.c[9] = A.seed_cov[3];
+            T.c[14] = A.seed_cov[4];
+          } else {
+            // inward restart: diagonal, outward variances inflated, capped at the seed's
+            const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
+            const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
+            const float d2 = fminf(A.restart_scale * T.c[5], A.seed_cov[2]);
+            const float d3 = fminf(A.restart_scale * T.c[9], A.seed_cov[3]);
+            const float d4 = fminf(A.restart_scale * T.c[14], A.seed_cov[4]);
+#pragma unroll
+            for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+            T.c[0] = d0;
+            T.c[2] = d1;
+            T.c[5] = d2;
+            T.c[9] = d3;
+            T.c[14] = d4;
+          }
+        } else if (j != 0) {
+          // crossed rows without a cluster (validated: rows strictly monotone)
+          const int dir = inward ? -1 : 1;
+          bool ok = true;
+          for (int r = rprev + dir; r != rk; r += dir) {
+            const float xr = s_rowx[r];
+            if (!propagate(T, xr - xcur, A.b, A.snp_max)) { ok = false; break; }
+            xcur = xr;
+            if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
+          }
+          if (!ok) { st = ST_SNP_LIMIT; break; }
+        }
+        if (!propagate(T, xk - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
+        xcur = xk;
+        rprev = rk;
+        bool acc;
+        double chi2;
+        const int ust = update(T, yk, zk, vyk, vzk, gate_bits, acc, chi2);
+        if (ust != ST_OK) { st = ust; break; }
+        if (!inward) {
+          if (acc) bits[32 * (lk >> 5)] |= 1u << (lk & 31);
+          if (A.chi2_out_c) A.chi2_out_c[k] = chi2;
+          ++out_done;
+          nacc_out += acc ? 1 : 0;
+        } else {
+          if (A.chi2_in_c) A.chi2_in_c[k] = chi2;
+          chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
+          nacc += acc ? 1 : 0;
+          const uint32_t ob = (bits[32 * (lk >> 5)] >> (lk & 31)) & 1u;
+          A.accept[k] = (uint8_t)(ob | (acc ? 2u : 0u));
+          ++done;
+        }
+        if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
+      }
+      cp_async_wait_all();  // no copy may land in the columns after this track
+      if (st == ST_OK) {
+        bool fin = isfinite(T.dy) && isfinite(T.dz) && isfinite(T.snp()) && isfinite(T.tl()) && isfinite(T.w());
+#pragma unroll
+        for (int i = 0; i < 15; ++i) fin = fin && isfinite(T.c[i]);
+        if (!fin) st = ST_NONFINITE;
+      }
+    }
+    // accept bytes not written by the inward pass (failed or unfitted tracks): outward bits only
+    for (int64_t k = a; k < e - done; ++k) {
+      const int lk = (int)(k - a);
+      A.accept[k] = (lk < kMaxRows) ? (uint8_t)((bits[32 * (lk >> 5)] >> (lk & 31)) & 1u) : (uint8_t)0;
+    }
+    if (A.chi2_in_c)
+      for (int64_t k = a; k < e - done; ++k) A.chi2_in_c[k] = __longlong_as_double(0x7ff8000000000000ll);
+    if (A.chi2_out_c)
+      for (int64_t k = a + out_done; k < e; ++k) A.chi2_out_c[k] = __longlong_as_double(0x7ff8000000000000ll);
+  }
+  A.x_ref[t] = xref;
+  float *ps = A.state + 5 * t;
+  ps[0] = T.ya + T.dy;
+  ps[1] = T.za + T.dz;
+  ps[2] = T.snp();
+  ps[3] = T.tl();
+  ps[4] = T.w();
+  float *pc = A.cov + 15 * t;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) pc[i] = T.c[i];
+  A.chi2[t] = chi2sum;
+  A.ndf[t] = 2 * nacc - 5;
+  A.status[t] = st;
+}
+
+__global__ void __launch_bounds__(kFitBlock, 2) k_fit(FitArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *s_rowx = reinterpret_cast<float *>(smem);
+  uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + kSmemRowx);
+  float *s_stage = reinterpret_cast<float *>(smem + kSmemRowx + kSmemBits);
+  for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) s_rowx[i] = A.row_x[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t *bits = s_bits + wib * kBitWords * 32 + lane;  // word w of this lane at bits[32*w]
+  float *stg = s_stage + threadIdx.x;                      // this lane's staging column
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(A.work, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= (unsigned long long)A.n_tracks) break;
+    const int64_t i = (int64_t)base + lane;
+    if (i < A.n_tracks) {
+      const int64_t t = A.perm ? (int64_t)A.perm[i] : i;
+      fit_track(A, t, bits, s_rowx, stg);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  const int64_t blocks = (a.n_tracks + 255) / 256;
+  k_prepare<<<(unsigned)blocks, 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches) {
+  if (a.n_tracks <= 0 || !a.perm) return cudaSuccess;
+  k_sort_scan<<<1, 32, 0, stream>>>(a.hist);
+  const int64_t blocks = (a.n_tracks + 255) / 256;
+  k_sort_scatter<<<(unsigned)blocks, 256, 0, stream>>>(a);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  (void)block;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFitSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_fit<<<grid, kFitBlock, kFitSmem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+int fit_blocks_per_sm(int block) {
+  (void)block;
+  int n = 0;
+  cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFitSmem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit, kFitBlock, kFitSmem) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+int fit_regs_per_thread() {
+  cudaFuncAttributes at;
+  if (cudaFuncGetAttributes(&at, k_fit) != cudaSuccess) return -1;
+  return at.numRegs;
+}
+
+}  // namespace tpcfit

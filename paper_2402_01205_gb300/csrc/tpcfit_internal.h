@@ -1,0 +1,50 @@
+// Internal interface between the C-ABI runtime and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tpcfit {
+
+constexpr int kMaxRows = 256;        // row index is uint8
+constexpr int kKeyBins = kMaxRows + 1; // sort key: cluster count clamped to [0, 256]
+
+// Everything one fit launch sequence needs; passed by value to the kernels.
+struct FitArgs {
+  // frame (device pointers); cluster arrays start at the frame's first cluster
+  int64_t n_tracks, n_clusters;
+  const int64_t *off;      // n_tracks+1 offsets
+  int64_t off_base;        // value subtracted from every offset (chunked host frames)
+  const float *x, *y, *z, *sy2, *sz2;
+  const uint8_t *row;
+  // results (device pointers, same indexing as the frame)
+  float *state, *cov, *x_ref;
+  double *chi2;
+  int32_t *ndf, *status;
+  uint8_t *accept;
+  double *chi2_out_c, *chi2_in_c;  // optional per-cluster chi2 (nullptr: not written)
+  // scratch (device)
+  float *seed;                   // n_tracks*5
+  int32_t *perm;                 // n_tracks (sorted order), or nullptr for frame order
+  uint32_t *hist;                // kKeyBins histogram, then bin cursors
+  unsigned long long *work;      // persistent-kernel work counter
+  int32_t *frame_error;          // bit0: malformed offsets
+  const float *row_x;            // kMaxRows pad-row plane positions
+  // fit parameters
+  float b;                       // -kB * Bz: d(curvature)/d(q/pT)
+  float chi2_max;
+  double chi2_max_d;
+  float xx0, mass2, snp_max, restart_scale;
+  float seed_cov[5];
+  int32_t min_clusters, n_rows;
+};
+
+// Launch helpers (all asynchronous on `stream`); each returns the CUDA error
+// of its launch.
+cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream);
+cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches);
+cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream);
+// Occupancy-derived resident blocks per SM for the fit kernel at `block` threads.
+int fit_blocks_per_sm(int block);
+int fit_regs_per_thread();
+
+}  // namespace tpcfit

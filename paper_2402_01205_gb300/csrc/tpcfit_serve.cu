@@ -1,0 +1,352 @@
+// Serving runtime: time frames submitted from the host are admitted into
+// resident device slots as slots and HBM budget free up, fitted on one stream
+// per slot (so the copies and kernels of different frames overlap on the
+// device), and their results copied back into the caller's buffers.
+//
+// The paper's asynchronous reconstruction limits the number of time frames in
+// flight and throttles their injection (Sec. 7) and processes several time
+// frames at once ("horizontal" parallelism, Sec. 4); here that becomes
+// admission by slot count and device-memory budget.
+//
+// Admission is FIFO with bounded backfill: a later, smaller frame may overtake
+// the head of the queue while the head does not fit, but only for
+// kBackfillWindow seconds after the head first failed to fit, so a large frame
+// cannot starve.
+
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/tpcfit.h"
+#include "tpcfit_internal.h"
+
+using namespace tpcfit;
+
+// from tpcfit_api.cu
+struct ServeState;
+struct Scratch;
+cudaStream_t handle_stream(tpcfit_handle *h);
+int handle_device(tpcfit_handle *h);
+const tpcfit_config &handle_config(tpcfit_handle *h);
+ServeState *&handle_serve(tpcfit_handle *h);
+int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *dev_frame, tpcfit_result *dev_res, void *scratch_base,
+                       cudaStream_t st, const int32_t **err_dev);
+size_t serve_scratch_bytes(int64_t n_tracks);
+void serve_stop(tpcfit_handle *h);
+
+namespace {
+
+bool debug_on() {
+  static const bool on = std::getenv("TPCFIT_DEBUG") != nullptr;
+  return on;
+}
+
+constexpr double kBackfillWindow = 0.050;  // seconds a blocked queue head may be overtaken
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device bytes one resident frame occupies: inputs, results, fit scratch.
+size_t frame_bytes(int64_t nt, int64_t nc) {
+  return a256((size_t)(nt + 1) * 8) + 5 * a256((size_t)nc * 4) + 2 * a256((size_t)nc) + a256((size_t)nt * 20) +
+         a256((size_t)nt * 60) + a256((size_t)nt * 4) + a256((size_t)nt * 8) + 2 * a256((size_t)nt * 4) +
+         serve_scratch_bytes(nt);
+}
+
+struct Request {
+  tpcfit_frame frame;
+  tpcfit_result res;
+  size_t bytes = 0;
+  int state = TPCFIT_PENDING;
+  double t_submit = 0, t_done = 0;
+  int slot = -1;
+};
+
+struct Slot {
+  bool busy = false;
+  uint64_t ticket = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  void *mem = nullptr;
+  size_t bytes = 0;
+  int32_t *h_err = nullptr;  // pinned
+  bool failed = false;
+};
+
+}  // namespace
+
+struct ServeState {
+  tpcfit_handle *h = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, Request> reqs;
+  std::vector<Slot> slots;
+  size_t used = 0, budget = 0;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  double head_blocked_since = -1.0;
+  cudaMemPool_t pool = nullptr;
+};
+
+// Carve one allocation into the frame and result arrays of a resident frame.
+static void carve(void *mem, int64_t nt, int64_t nc, tpcfit_frame *df, tpcfit_result *dr, void **scratch) {
+  char *p = (char *)mem;
+  auto take = [&](size_t b) {
+    char *q = p;
+    p += a256(b);
+    return q;
+  };
+  df->track_offsets = (const int64_t *)take((size_t)(nt + 1) * 8);
+  df->x = (const float *)take((size_t)nc * 4);
+  df->y = (const float *)take((size_t)nc * 4);
+  df->z = (const float *)take((size_t)nc * 4);
+  df->sy2 = (const float *)take((size_t)nc * 4);
+  df->sz2 = (const float *)take((size_t)nc * 4);
+  df->row = (const uint8_t *)take((size_t)nc);
+  df->sector = nullptr;
+  df->n_tracks = nt;
+  df->n_clusters = nc;
+  df->mem = TPCFIT_MEM_DEVICE;
+  dr->state = (float *)take((size_t)nt * 20);
+  dr->cov = (float *)take((size_t)nt * 60);
+  dr->x_ref = (float *)take((size_t)nt * 4);
+  dr->chi2 = (double *)take((size_t)nt * 8);
+  dr->ndf = (int32_t *)take((size_t)nt * 4);
+  dr->status = (int32_t *)take((size_t)nt * 4);
+  dr->accept = (uint8_t *)take((size_t)nc);
+  dr->mem = TPCFIT_MEM_DEVICE;
+  dr->chi2_out_cluster = dr->chi2_in_cluster = nullptr;
+  *scratch = p;
+}
+
+// Enqueue copy-in, fit and copy-out of request `tk` on slot `si` (lock held).
+static bool launch(ServeState *S, uint64_t tk, int si) {
+  Request &R = S->reqs[tk];
+  Slot &L = S->slots[si];
+  const int64_t nt = R.frame.n_tracks, nc = R.frame.n_clusters;
+  if (cudaError_t e = cudaMallocFromPoolAsync(&L.mem, R.bytes, S->pool, L.stream); e != cudaSuccess) {
+    cudaGetLastError();
+    if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: pool allocation of %zu bytes failed: %s\n",
+                                 (unsigned long long)tk, R.bytes, cudaGetErrorString(e));
+    return false;
+  }
+  L.bytes = R.bytes;
+  L.busy = true;
+  L.ticket = tk;
+  L.failed = false;
+  R.slot = si;
+  S->used += R.bytes;
+  tpcfit_frame df;
+  tpcfit_result dr;
+  void *scratch = nullptr;
+  carve(L.mem, nt, nc, &df, &dr, &scratch);
+  const tpcfit_frame &F = R.frame;
+  bool ok = true;
+  auto cp = [&](const void *dst, const void *src, size_t b, cudaMemcpyKind k) {
+    if (!b || !ok) return;
+    if (cudaError_t e = cudaMemcpyAsync((void *)dst, src, b, k, L.stream); e != cudaSuccess) {
+      ok = false;
+      if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: copy of %zu bytes failed: %s\n",
+                                   (unsigned long long)tk, b, cudaGetErrorString(e));
+    }
+  };
+  cp(df.track_offsets, F.track_offsets, (size_t)(nt + 1) * 8, cudaMemcpyHostToDevice);
+  cp(df.x, F.x, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.y, F.y, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.z, F.z, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.sy2, F.sy2, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.sz2, F.sz2, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.row, F.row, (size_t)nc, cudaMemcpyHostToDevice);
+  const int32_t *err_dev = nullptr;
+  if (ok && serve_launch_frame(S->h, &df, &dr, scratch, L.stream, &err_dev) != TPCFIT_OK) ok = false;
+  if (ok) cp(L.h_err, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  const tpcfit_result &O = R.res;
+  cp(O.state, dr.state, (size_t)nt * 20, cudaMemcpyDeviceToHost);
+  cp(O.cov, dr.cov, (size_t)nt * 60, cudaMemcpyDeviceToHost);
+  cp(O.x_ref, dr.x_ref, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+  cp(O.chi2, dr.chi2, (size_t)nt * 8, cudaMemcpyDeviceToHost);
+  cp(O.ndf, dr.ndf, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+  cp(O.status, dr.status, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+  cp(O.accept, dr.accept, (size_t)nc, cudaMemcpyDeviceToHost);
+  if (!ok) cudaGetLastError();
+  L.failed = !ok;
+  cudaFreeAsync(L.mem, L.stream);  // released in stream order after the copies
+  cudaEventRecord(L.done, L.stream);
+  return true;
+}
+
+static void worker_loop(ServeState *S) {
+  cudaSetDevice(handle_device(S->h));
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (!S->stop) {
+    bool progress = false;
+    // completions
+    for (size_t i = 0; i < S->slots.size(); ++i) {
+      Slot &L = S->slots[i];
+      if (!L.busy) continue;
+      cudaError_t q = cudaEventQuery(L.done);
+      if (q == cudaErrorNotReady) continue;
+      Request &R = S->reqs[L.ticket];
+      R.t_done = tpcfit_now();
+      R.state = (q == cudaSuccess && !L.failed && *L.h_err == 0) ? TPCFIT_DONE : TPCFIT_FAILED;
+      if (R.state == TPCFIT_FAILED && debug_on())
+        std::fprintf(stderr, "tpcfit serve: ticket %llu failed: event %s, enqueue %s, frame error word %d\n",
+                     (unsigned long long)L.ticket, cudaGetErrorString(q), L.failed ? "failed" : "ok", *L.h_err);
+      if (q != cudaSuccess) cudaGetLastError();
+      S->used -= L.bytes;
+      L.busy = false;
+      L.mem = nullptr;
+      progress = true;
+    }
+    if (progress) S->cv_done.notify_all();
+    // admissions
+    const double now = tpcfit_now();
+    for (auto it = S->queue.begin(); it != S->queue.end();) {
+      int free_slot = -1;
+      for (size_t i = 0; i < S->slots.size(); ++i)
+        if (!S->slots[i].busy) {
+          free_slot = (int)i;
+          break;
+        }
+      if (free_slot < 0) break;
+      Request &R = S->reqs[*it];
+      const bool is_head = (it == S->queue.begin());
+      if (S->used + R.bytes <= S->budget) {
+        if (!launch(S, *it, free_slot)) {
+          R.state = TPCFIT_FAILED;
+          R.t_done = tpcfit_now();
+          S->cv_done.notify_all();
+        }
+        if (is_head) S->head_blocked_since = -1.0;
+        it = S->queue.erase(it);
+        progress = true;
+        continue;
+      }
+      if (is_head) {
+        if (S->head_blocked_since < 0) S->head_blocked_since = now;
+        if (now - S->head_blocked_since > kBackfillWindow) break;  // no more overtaking
+      }
+      ++it;
+    }
+    bool busy = false;
+    for (auto &L : S->slots) busy |= L.busy;
+    if (!progress) {
+      if (busy) {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
+      } else {
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+      }
+    }
+  }
+}
+
+int serve_start(tpcfit_handle *h) {
+  ServeState *S = new ServeState();
+  S->h = h;
+  const tpcfit_config &c = handle_config(h);
+  S->budget = (size_t)c.hbm_budget_bytes;
+  cudaSetDevice(handle_device(h));
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = handle_device(h);
+  if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    delete S;
+    return TPCFIT_E_CUDA;
+  }
+  uint64_t keep = (uint64_t)S->budget;
+  cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  S->slots.resize((size_t)c.max_slots);
+  for (auto &L : S->slots) {
+    if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&L.h_err, sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      handle_serve(h) = S;
+      serve_stop(h);
+      return TPCFIT_E_CUDA;
+    }
+    *L.h_err = 0;
+  }
+  handle_serve(h) = S;
+  S->worker = std::thread(worker_loop, S);
+  return TPCFIT_OK;
+}
+
+void serve_stop(tpcfit_handle *h) {
+  ServeState *S = handle_serve(h);
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (auto &L : S->slots) {
+    if (L.stream) cudaStreamSynchronize(L.stream);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.stream) cudaStreamDestroy(L.stream);
+    if (L.h_err) cudaFreeHost(L.h_err);
+  }
+  if (S->pool) cudaMemPoolDestroy(S->pool);
+  handle_serve(h) = nullptr;
+  delete S;
+}
+
+int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint64_t *ticket) {
+  ServeState *S = handle_serve(h);
+  const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters);
+  if (bytes > S->budget) return TPCFIT_E_NOMEM;
+  std::lock_guard<std::mutex> lk(S->mu);
+  const uint64_t tk = S->next_ticket++;
+  Request &R = S->reqs[tk];
+  R.frame = *f;
+  R.res = *r;
+  R.bytes = bytes;
+  R.t_submit = tpcfit_now();
+  if (f->n_tracks == 0) {
+    R.state = TPCFIT_DONE;
+    R.t_done = R.t_submit;
+  } else {
+    S->queue.push_back(tk);
+  }
+  *ticket = tk;
+  S->cv_work.notify_one();
+  return TPCFIT_OK;
+}
+
+int serve_poll(tpcfit_handle *h, uint64_t ticket, int *state, double *t_done, double timeout_s, bool wait) {
+  ServeState *S = handle_serve(h);
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return TPCFIT_E_NOTFOUND;
+  if (wait) {
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s < 0 ? 1e9 : timeout_s);
+    while (it->second.state == TPCFIT_PENDING) {
+      if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && it->second.state == TPCFIT_PENDING) {
+        *state = TPCFIT_PENDING;
+        return TPCFIT_E_TIMEOUT;
+      }
+      it = S->reqs.find(ticket);
+      if (it == S->reqs.end()) return TPCFIT_E_NOTFOUND;
+    }
+  }
+  *state = it->second.state;
+  if (t_done) *t_done = it->second.t_done;
+  if (it->second.state != TPCFIT_PENDING) S->reqs.erase(it);
+  return TPCFIT_OK;
+}

@@ -1,0 +1,79 @@
+"""C-ABI library: builds, loads and exports every declared entry point (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            src = open(os.path.join(inc, fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(tpcfit_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2402_01205_gb300 import _build
+    _build.build()
+    return ctypes.CDLL(_build.LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"tpcfit_create", "tpcfit_fit", "tpcfit_submit", "tpcfit_poll", "tpcfit_destroy"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_default_config_and_errors_without_gpu(lib):
+    import paper_2402_01205_gb300 as T
+    cfg = T.default_config()
+    assert cfg.bz_tesla == pytest.approx(0.5) and cfg.chi2_max == 16.0 and cfg.min_clusters == 10
+    assert cfg.n_rows == 152 and cfg.restart_scale == 100.0 and cfg.sort_tracks == 1
+    assert list(cfg.seed_cov) == pytest.approx([1, 1, 0.01, 0.01, 1])
+    assert T.strerror(T.E_NODEV).startswith("no usable CUDA device")
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(T.TpcfitError) as ei:
+            T.create(cfg)
+        assert ei.value.code == T.E_NODEV
+    bad = T.default_config(n_rows=300)
+    with pytest.raises(T.TpcfitError) as ei:
+        T.create(bad)
+    assert ei.value.code == T.E_INVAL
+
+
+def test_struct_layout_matches_header(lib, tmp_path):
+    """ctypes mirrors of the C structs have the C compiler's offsets and sizes."""
+    import subprocess
+    import paper_2402_01205_gb300 as T
+    structs = {"tpcfit_config": T.Config, "tpcfit_frame": T._Frame, "tpcfit_result": T._Result,
+               "tpcfit_timing": T._Timing}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tpcfit.h"', "int main(void){"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            c, f, v = ln.split()
+            got[(c, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

@@ -1,0 +1,199 @@
+"""CUDA fit vs FP64 oracle, element by element, through the C-ABI.
+
+Sizes span many warps and blocks and end on ragged tails; the Pb-Pb-scale
+frame (2,000,000 tracks) is fitted whole on the GPU in the benchmark's launch
+configuration and compared on sampled blocks of tracks that the oracle fits.
+"""
+import types
+
+import numpy as np
+import pytest
+
+import oracle
+import tpcgen
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_01205_gb300 as T
+    from paper_2402_01205_gb300 import _build
+    _build.build()
+    return T
+
+
+def dev_frame(f):
+    g = types.SimpleNamespace()
+    for k in ("offsets", "x", "y", "z", "sy2", "sz2", "row"):
+        setattr(g, k, torch.from_numpy(np.ascontiguousarray(getattr(f, k))).cuda())
+    return g
+
+
+def fit_gpu(T, f, **cfg):
+    with T.Fitter(**cfg) as fx:
+        res = fx.fit(dev_frame(f))
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in res.items()}
+
+
+def orc_cfg(xx0):
+    return oracle.FitConfig(xx0=xx0)
+
+
+def check(f, gpu, orc, track_ids=None, min_compared=0.97):
+    rep = compare(f.offsets, gpu, orc, track_ids=track_ids)
+    print(rep.summary())
+    assert not rep.status_mismatch, rep.status_mismatch[:10]
+    assert not rep.accept_mismatch, rep.accept_mismatch[:10]
+    assert rep.ndf_mismatch == 0
+    assert rep.max_state < 1e-3, rep.worst
+    assert rep.max_cov < 1e-4, rep.worst
+    assert rep.max_chi2 < 1e-4, rep.worst
+    n_ok = int(((gpu["status"] == 0) & (orc["status"] == 0)).sum()) if track_ids is None else None
+    if n_ok:
+        assert rep.n_compared >= min_compared * n_ok
+    return rep
+
+
+def test_parity_single_sector_1k(T):
+    f = tpcgen.generate("sector1k")
+    gpu = fit_gpu(T, f, xx0_per_row=0.0)
+    orc = oracle.fit(f, orc_cfg(0.0), diagnostics=True)
+    assert np.all(orc["status"] == 0)
+    check(f, gpu, orc)
+
+
+def test_parity_detector_50k(T):
+    f = tpcgen.generate("detector50k")
+    gpu = fit_gpu(T, f)
+    orc = oracle.fit(f, orc_cfg(5e-4), diagnostics=True)
+    check(f, gpu, orc)
+
+
+def test_parity_pbpb_spectrum_200k(T):
+    f = tpcgen.generate("pbpb2m", n_tracks=200_003)  # ragged tail
+    gpu = fit_gpu(T, f)
+    orc = oracle.fit(f, orc_cfg(5e-4), diagnostics=True)
+    check(f, gpu, orc)
+
+
+def test_parity_full_size_pbpb_frame_sampled(T):
+    """2,000,000 tracks fitted whole (benchmark launch); oracle on 8 blocks of 2,500 tracks."""
+    f = tpcgen.generate("pbpb2m")
+    gpu = fit_gpu(T, f)
+    nt = f.n_tracks
+    for b0 in np.linspace(0, nt - 2500, 8).astype(int):
+        sub = f.subset(int(b0), int(b0) + 2500)
+        orc = oracle.fit(sub, orc_cfg(5e-4), diagnostics=True)
+        a, e = f.offsets[b0], f.offsets[b0 + 2500]
+        g = dict(state=gpu["state"][b0:b0 + 2500], cov=gpu["cov"][b0:b0 + 2500], chi2=gpu["chi2"][b0:b0 + 2500],
+                 ndf=gpu["ndf"][b0:b0 + 2500], status=gpu["status"][b0:b0 + 2500], accept=gpu["accept"][a:e],
+                 x_ref=gpu["x_ref"][b0:b0 + 2500])
+        check(sub, g, orc)
+    # whole-frame properties at full size: every track has a status, finite outputs for OK tracks
+    ok = gpu["status"] == 0
+    assert ok.mean() > 0.99
+    assert np.isfinite(gpu["state"][ok]).all() and np.isfinite(gpu["cov"][ok]).all()
+    assert np.all(gpu["x_ref"] == f.x[f.offsets[:-1]])
+
+
+def test_host_path_chunked_equals_device_path(T):
+    f = tpcgen.generate("detector50k", n_tracks=20_011)
+    dev = fit_gpu(T, f)
+    with T.Fitter(host_chunk_clusters=300_000) as fx:
+        host = fx.fit(f)  # numpy arrays: host frame, copied in chunks
+    for k in dev:
+        assert np.array_equal(dev[k], host[k], equal_nan=k in ('state', 'cov')), k
+
+
+def test_sorted_and_unsorted_orders_agree(T):
+    f = tpcgen.generate("detector50k", n_tracks=10_000)
+    a = fit_gpu(T, f, sort_tracks=1)
+    b = fit_gpu(T, f, sort_tracks=0)
+    for k in a:
+        assert np.array_equal(a[k], b[k], equal_nan=k in ('state', 'cov')), k
+
+
+def test_async_on_torch_stream_and_determinism(T):
+    f = tpcgen.generate("detector50k", n_tracks=8_000)
+    ref = fit_gpu(T, f)
+    g = dev_frame(f)
+    s = torch.cuda.Stream()
+    with T.Fitter() as fx:
+        outs = []
+        for _ in range(3):
+            res = T.alloc_result(f.n_tracks, f.n_clusters, device="cuda")
+            fx.fit_async(g, res, stream=s)
+            outs.append(res)
+        fx.sync()
+        tm = fx.timing()
+    assert tm["kernel_launches"] == 4 and tm["fit_ms"] > 0 and tm["n_timed"] >= 3
+    for res in outs:
+        for k in ref:
+            assert np.array_equal(ref[k], res[k].cpu().numpy(), equal_nan=k in ('state', 'cov')), k
+
+
+def test_edge_cases_match_oracle(T):
+    f = tpcgen.generate("detector50k", n_tracks=67, seed=4)
+    y, row, z = f.y.copy(), f.row.copy(), f.z.copy()
+    sy2 = f.sy2.copy()
+    o = f.offsets
+    y[o[1] + 5] = np.nan                 # NONFINITE
+    row[o[2] + 7] = row[o[2] + 6]        # BAD_INPUT (rows not ascending)
+    row[o[3] + 3] = row[o[3] + 2]        # first offending cluster decides ...
+    z[o[3] + 9] = np.inf                 # ... over a later non-finite value
+    sy2[o[4] + 2] = 0.0                  # BAD_INPUT (variance)
+    row[o[5] + 4] = 200                  # BAD_INPUT (row >= n_rows)
+    g = tpcgen.Frame(o, f.x, y, z, sy2, f.sz2, row, f.sector)
+    gpu = fit_gpu(T, g)
+    orc = oracle.fit(g, orc_cfg(5e-4), diagnostics=True)
+    assert list(gpu["status"][1:6]) == [4, 5, 5, 5, 5]
+    check(g, gpu, orc)
+    # a frame with a too-short track, a single track frame and an empty frame
+    short = tpcgen.Frame(np.array([0, 5, 5 + int(f.offsets[2] - f.offsets[1])]), *(
+        np.concatenate([getattr(f, k)[:5], getattr(f, k)[f.offsets[1]:f.offsets[2]]])
+        for k in ("x", "y", "z", "sy2", "sz2", "row")), f.sector[:2])
+    gs = fit_gpu(T, short)
+    os_ = oracle.fit(short, orc_cfg(5e-4), diagnostics=True)
+    assert list(gs["status"]) == list(os_["status"]) == [1, 0]
+    assert np.all(gs["accept"][:5] == 0)
+    check(short, gs, os_)
+    one = f.subset(10, 11)
+    check(one, fit_gpu(T, one), oracle.fit(one, orc_cfg(5e-4), diagnostics=True))
+    empty = tpcgen.Frame(np.zeros(1, np.int64), *(np.zeros(0, np.float32),) * 5, np.zeros(0, np.uint8),
+                         np.zeros(0, np.uint8))
+    with T.Fitter() as fx:
+        r = fx.fit(empty)
+    assert r["state"].shape == (0, 5)
+
+
+def test_malformed_offsets_rejected(T):
+    f = tpcgen.generate("sector1k", n_tracks=100)
+    bad = tpcgen.Frame(f.offsets.copy(), f.x, f.y, f.z, f.sy2, f.sz2, f.row, f.sector)
+    bad.offsets[50] = bad.offsets[52]  # decreasing at 51
+    with T.Fitter() as fx:
+        with pytest.raises(T.TpcfitError) as ei:
+            fx.fit(dev_frame(bad))
+        assert ei.value.code == T.E_INVAL
+        with pytest.raises(T.TpcfitError) as ei:
+            fx.fit(bad)  # host frame: rejected before any copy
+        assert ei.value.code == T.E_INVAL
+        # the handle stays usable
+        ok = fx.fit(dev_frame(f))
+        torch.cuda.synchronize()
+        assert (ok["status"] == 0).all()
+
+
+def test_noise_free_gpu_fit_recovers_truth(T):
+    f = tpcgen.generate("sector1k", truth=True, n_tracks=500, sigma_y=0.0, sigma_z=0.0)
+    gpu = fit_gpu(T, f, xx0_per_row=0.0)
+    assert np.all(gpu["status"] == 0)
+    tr = f.truth[f.offsets[:-1]]
+    d = np.abs(gpu["state"].astype(np.float64) - tr)
+    assert np.all(d.max(0) < [1e-4, 1e-4, 1e-5, 1e-5, 5e-2])

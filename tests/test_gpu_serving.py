@@ -1,0 +1,116 @@
+"""Serving through the C-ABI: resident slots, HBM-budget admission, overlap,
+and results identical alone and in the mix."""
+import time
+import types
+
+import numpy as np
+import pytest
+
+import tpcgen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_01205_gb300 as T
+    from paper_2402_01205_gb300 import _build
+    _build.build()
+    return T
+
+
+def pinned_frame(f):
+    g = types.SimpleNamespace()
+    for k in ("offsets", "x", "y", "z", "sy2", "sz2", "row"):
+        a = torch.from_numpy(np.ascontiguousarray(getattr(f, k)))
+        setattr(g, k, a.pin_memory())
+    return g
+
+
+def frames_of_uneven_size(seed=0):
+    pool = tpcgen.generate("detector50k", n_tracks=60_000, seed=seed)
+    sizes = [800, 25_000, 3_000, 12_000, 150, 9_000]
+    out, t0 = [], 0
+    for s in sizes:
+        out.append(pool.subset(t0, t0 + s))
+        t0 += s
+    return out
+
+
+def alone(T, f):
+    with T.Fitter() as fx:
+        return fx.fit(f)
+
+
+def test_results_identical_alone_and_in_the_mix(T):
+    frames = frames_of_uneven_size()
+    ref = [alone(T, f) for f in frames]
+    with T.Fitter(max_slots=3) as fx:
+        res = [T.alloc_result(f.n_tracks, f.n_clusters, pinned=True) for f in frames]
+        tickets = [fx.submit(pinned_frame(f), r) for f, r in zip(frames, res)]
+        for tk in tickets:
+            st, t_done = fx.wait(tk, timeout_s=60)
+            assert st == T.DONE and t_done > 0
+    for r, rf in zip(res, ref):
+        for k in rf:
+            assert np.array_equal(r[k].numpy(), rf[k], equal_nan=k in ('state', 'cov')), k
+
+
+def test_budget_admission_and_rejection(T):
+    frames = frames_of_uneven_size(seed=1)
+    big = max(frames, key=lambda f: f.n_clusters)
+    # budget for about one large frame: frames are admitted one by one and all finish
+    budget = int(big.n_clusters * 24 + big.n_tracks * 140 + (4 << 20))
+    with T.Fitter(hbm_budget_bytes=budget, max_slots=4) as fx:
+        res = [T.alloc_result(f.n_tracks, f.n_clusters, pinned=True) for f in frames]
+        tickets = [fx.submit(pinned_frame(f), r) for f, r in zip(frames, res)]
+        states = [fx.wait(tk, timeout_s=60)[0] for tk in tickets]
+        assert states == [T.DONE] * len(frames)
+        # a frame larger than the whole budget is refused at submission
+        huge = tpcgen.generate("detector50k", n_tracks=40_000, seed=2)
+        with pytest.raises(T.TpcfitError) as ei:
+            fx.submit(pinned_frame(huge), T.alloc_result(huge.n_tracks, huge.n_clusters, pinned=True))
+        assert ei.value.code == T.E_NOMEM
+    for r, f in zip(res, frames):
+        assert np.array_equal(r["status"].numpy(), alone(T, f)["status"])
+
+
+def test_malformed_frame_rejected_neighbours_succeed(T):
+    frames = frames_of_uneven_size(seed=3)[:3]
+    bad = tpcgen.Frame(frames[1].offsets.copy(), *(getattr(frames[1], k) for k in ("x", "y", "z", "sy2", "sz2", "row")),
+                       frames[1].sector)
+    bad.offsets[5] = bad.offsets[7]
+    with T.Fitter() as fx:
+        r0 = T.alloc_result(frames[0].n_tracks, frames[0].n_clusters, pinned=True)
+        t0 = fx.submit(pinned_frame(frames[0]), r0)
+        with pytest.raises(T.TpcfitError) as ei:
+            fx.submit(pinned_frame(bad), T.alloc_result(bad.n_tracks, bad.n_clusters, pinned=True))
+        assert ei.value.code == T.E_INVAL
+        r2 = T.alloc_result(frames[2].n_tracks, frames[2].n_clusters, pinned=True)
+        t2 = fx.submit(pinned_frame(frames[2]), r2)
+        assert fx.wait(t0, 60)[0] == T.DONE and fx.wait(t2, 60)[0] == T.DONE
+        # a reported ticket is forgotten; unknown tickets are reported as such
+        with pytest.raises(T.TpcfitError) as ei:
+            fx.poll(t0)
+        assert ei.value.code == T.E_NOTFOUND
+
+
+def test_poll_pending_then_done_and_wait_timeout(T):
+    f = tpcgen.generate("pbpb2m", n_tracks=300_000, seed=4)
+    with T.Fitter() as fx:
+        r = T.alloc_result(f.n_tracks, f.n_clusters, pinned=True)
+        tk = fx.submit(pinned_frame(f), r)
+        st, _ = fx.poll(tk)
+        assert st in (T.PENDING, T.DONE)
+        if st == T.PENDING:
+            with pytest.raises(T.TpcfitError) as ei:
+                fx.wait(tk, timeout_s=1e-6)
+            assert ei.value.code in (T.E_TIMEOUT,)
+        deadline = time.time() + 60
+        while st == T.PENDING and time.time() < deadline:
+            st, t_done = fx.poll(tk)
+            time.sleep(0.001)
+        assert st == T.DONE

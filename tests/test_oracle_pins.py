@@ -84,6 +84,40 @@ def test_seed_exact_on_a_circle():
         assert np.allclose(s, f.truth[a], rtol=1e-9, atol=1e-9), (t, s, f.truth[a])
 
 
+def test_reversed_seed_gives_state_at_the_outer_end():
+    """The inward re-seed: circle through (last, middle, first) taken for motion
+    towards the first cluster, then reversed (sinphi, tanlambda, q/pT negated),
+    is the helix state at the outermost cluster."""
+    f = tpcgen.generate("sector1k", n_tracks=100, truth=True, sigma_y=0.0, sigma_z=0.0, seed=13)
+    for t in range(f.n_tracks):
+        a, b = f.offsets[t], f.offsets[t + 1]
+        n = b - a
+        pts = [(float(f.x[k]), f.truth[k, 0], f.truth[k, 1]) for k in (b - 1, a + n // 2, a)]
+        s = oracle.seed(*pts)
+        s[2:] = -s[2:]
+        assert np.allclose(s, f.truth[b - 1], rtol=1e-9, atol=1e-9), (t, s, f.truth[b - 1])
+
+
+def test_first_cluster_outlier_does_not_derail_the_fit():
+    """An outlier at the innermost cluster anchors the outward pass (its residual
+    is zero by construction); the inward pass then re-seeds at the outer end
+    and rejects it."""
+    f = tpcgen.generate("detector50k", n_tracks=3000, truth=True, p_outlier=0.0, seed=21)
+    y, z = f.y.copy(), f.z.copy()
+    rng = np.random.default_rng(5)
+    first = f.offsets[:-1]
+    y[first] += rng.choice([-1, 1], f.n_tracks) * rng.uniform(1.5, 2.0, f.n_tracks)
+    z[first] += rng.choice([-1, 1], f.n_tracks) * rng.uniform(1.5, 2.0, f.n_tracks)
+    g = tpcgen.Frame(f.offsets, f.x, y, z, f.sy2, f.sz2, f.row, f.sector)
+    r = oracle.fit(g, _cfg())
+    ok = r["status"] == 0
+    inward = (r["accept"] >> 1) & 1
+    nacc = np.add.reduceat(inward, f.offsets[:-1])
+    n = np.diff(f.offsets)
+    assert (nacc[ok] < 0.7 * n[ok]).mean() < 0.01
+    assert inward[first[ok]].mean() < 0.01  # the displaced first clusters are rejected
+
+
 # ---------------------------------------------------------------- update
 def test_update_gate_equality_accepts_and_rejects_above():
     p = np.array([1.0, 2.0, 0.1, 0.2, 0.5])
