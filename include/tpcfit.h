@@ -116,6 +116,9 @@ typedef struct tpcfit_result {
    * TPCFIT_E_INVAL; serving ignores them). */
   double *chi2_out_cluster; /* n_clusters */
   double *chi2_in_cluster;  /* n_clusters */
+  /* optional: state (y, z, sinphi, tanlambda, q/pT) the inward pass restarted
+   * from, at the outermost cluster; NULL = not written (same rules as above) */
+  float *restart_state;     /* n_tracks*5 */
 } tpcfit_result;
 
 /* Kernel timings of the last completed fit on a handle (CUDA events on the

@@ -21,8 +21,10 @@
  *   |sinphi| limit 0.999; MS after the (possible) update at every crossed row;
  *   inward pass restarts from the outward state with a diagonal covariance:
  *   the outward variances times restart_scale (100), capped at the seed's;
- *   if the outward pass accepted fewer than half of the clusters it restarts
- *   instead from a fresh three-point seed at the outermost cluster;
+ *   if the outward pass accepted fewer than 90 % of the clusters (a pass that
+ *   lost the track for a stretch, typically after an outlier at the first
+ *   cluster) it restarts instead from a fresh three-point seed at the
+ *   outermost cluster;
  *   outputs at the innermost cluster.
  * Status rule: clusters are validated when the outward pass reaches them, so the
  * first offending cluster decides; NaN never trips a numerical limit (it flows
@@ -296,7 +298,7 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
     orc_ms_noise(p, C, c->xx0, c->mass);
   }
 
-  /* ---- inward pass restart.  If the outward pass accepted at least half of
+  /* ---- inward pass restart.  If the outward pass accepted at least 90 % of
      the clusters: from the outward state with a diagonal covariance, the
      outward variances inflated by restart_scale and capped at the seed's.
      Otherwise the outward pass is not trusted: a fresh three-point seed at the
@@ -305,7 +307,7 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
   {
     int nacc_out = 0;
     for (int64_t k = a; k < e; ++k) nacc_out += o->accept[k] & 1;
-    if (2 * nacc_out < n) {
+    if (10 * (int64_t)nacc_out < 9 * n) {
       double A[3] = {x[e - 1], y[e - 1], z[e - 1]}, B[3] = {x[a + n / 2], y[a + n / 2], z[a + n / 2]},
              D[3] = {x[a], y[a], z[a]};
       orc_seed(A, B, D, c->bz, p);

@@ -60,7 +60,7 @@ class _Result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("x_ref", ctypes.c_void_p),
                 ("chi2", ctypes.c_void_p), ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p),
                 ("accept", ctypes.c_void_p), ("mem", ctypes.c_int32), ("chi2_out_cluster", ctypes.c_void_p),
-                ("chi2_in_cluster", ctypes.c_void_p)]
+                ("chi2_in_cluster", ctypes.c_void_p), ("restart_state", ctypes.c_void_p)]
 
 
 class _Timing(ctypes.Structure):
@@ -219,7 +219,7 @@ def _result_struct(res: dict) -> tuple:
     names = ("state", "cov", "x_ref", "chi2", "ndf", "status", "accept")
     arrs = [res[k] for k in names]
     mem = _mem_of(arrs)
-    extra = [_ptr(res.get(k)) for k in ("chi2_out_cluster", "chi2_in_cluster")]
+    extra = [_ptr(res.get(k)) for k in ("chi2_out_cluster", "chi2_in_cluster", "restart_state")]
     return _Result(*[_ptr(a) for a in arrs], mem, *extra), mem
 
 

@@ -209,10 +209,14 @@ __global__ void __launch_bounds__(256) k_sort_scatter(FitArgs A) {
 //  - y, z:       offsets (dy, dz) from the last cluster's coordinates (ya, za)
 //  - sinphi:     compensated sum sp + spl (TwoSum on every increment)
 //  - tanlambda:  anchor tl0 + offset dtl;  q/pT: anchor w0 + offset dw
+//  - variances of tanlambda and q/pT: compensated sums c[9] + c9l, c[14] + c14l
+//    (transport leaves them unchanged; after a restart they shrink by orders of
+//    magnitude through many small decrements)
 struct Trk {
   float dy, dz, sp, spl, tl0, dtl, w0, dw;
   float ya, za;
   float c[15];  // covariance, packed lower triangle
+  float c9l, c14l;
   __device__ __forceinline__ float tl() const { return tl0 + dtl; }
   __device__ __forceinline__ float w() const { return w0 + dw; }
   __device__ __forceinline__ float snp() const { return sp + spl; }
@@ -316,8 +320,8 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   const float lg = fmaf(0.038f, __logf(eps * ib2), 1.0f);
   const float th2 = (0.0136f * 0.0136f) * pinv2 * ib2 * eps * lg * lg;
   T.c[5] = fmaf(th2, cs2 * tt, T.c[5]);
-  T.c[9] = fmaf(th2, tt * tt, T.c[9]);
-  T.c[14] = fmaf(th2, w * w * t * t, T.c[14]);
+  two_sum(T.c[9], fmaf(th2, tt * tt, T.c9l), T.c[9], T.c9l);
+  two_sum(T.c[14], fmaf(th2, w * w * t * t, T.c14l), T.c[14], T.c14l);
   T.c[13] = fmaf(th2, tt * w * t, T.c[13]);
 }
 
@@ -390,10 +394,10 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
     }
     c[5] = fmaf(-K0[2], h0[2], fmaf(-K1[2], h1[2], c[5]));
     c[8] = fmaf(-K0[3], h0[2], fmaf(-K1[3], h1[2], c[8]));
-    c[9] = fmaf(-K0[3], h0[3], fmaf(-K1[3], h1[3], c[9]));
+    two_sum(c[9], T.c9l - fmaf(K0[3], h0[3], K1[3] * h1[3]), c[9], T.c9l);
     c[12] = fmaf(-K0[4], h0[2], fmaf(-K1[4], h1[2], c[12]));
     c[13] = fmaf(-K0[4], h0[3], fmaf(-K1[4], h1[3], c[13]));
-    c[14] = fmaf(-K0[4], h0[4], fmaf(-K1[4], h1[4], c[14]));
+    two_sum(c[14], T.c14l - fmaf(K0[4], h0[4], K1[4] * h1[4]), c[14], T.c14l);
   } else {
     T.dy = -r0;
     T.dz = -r1;
@@ -455,6 +459,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   T.c[5] = A.seed_cov[2];
   T.c[9] = A.seed_cov[3];
   T.c[14] = A.seed_cov[4];
+  T.c9l = 0.f;
+  T.c14l = 0.f;
   int st = st0;
   double chi2sum = 0.0;
   int nacc = 0;
@@ -508,8 +514,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           if (!(vyk > 0.f) || !(vzk > 0.f)) { st = ST_BAD_INPUT; break; }
         }
         if (j == n) {
-          if (2 * nacc_out < n) {
-            // the outward pass accepted fewer than half of the clusters: re-seed
+          if (10 * nacc_out < 9 * n) {
+            // the outward pass accepted fewer than 90 % of the clusters: re-seed
             // at the outermost cluster (circle through clusters n-1, n/2, 0 for
             // motion towards cluster 0, reversed) with the seed covariance
             float p[5];
@@ -532,13 +538,15 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             T.c[5] = A.seed_cov[2];
             T.c[9] = A.seed_cov[3];
             T.c[14] = A.seed_cov[4];
+            T.c9l = 0.f;
+            T.c14l = 0.f;
           } else {
             // inward restart: diagonal, outward variances inflated, capped at the seed's
             const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
             const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
             const float d2 = fminf(A.restart_scale * T.c[5], A.seed_cov[2]);
-            const float d3 = fminf(A.restart_scale * T.c[9], A.seed_cov[3]);
-            const float d4 = fminf(A.restart_scale * T.c[14], A.seed_cov[4]);
+            const float d3 = fminf(A.restart_scale * (T.c[9] + T.c9l), A.seed_cov[3]);
+            const float d4 = fminf(A.restart_scale * (T.c[14] + T.c14l), A.seed_cov[4]);
 #pragma unroll
             for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
             T.c[0] = d0;
@@ -546,6 +554,16 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             T.c[5] = d2;
             T.c[9] = d3;
             T.c[14] = d4;
+            T.c9l = 0.f;
+            T.c14l = 0.f;
+          }
+          if (A.restart_state) {
+            float *rs = A.restart_state + 5 * t;
+            rs[0] = T.ya + T.dy;
+            rs[1] = T.za + T.dz;
+            rs[2] = T.snp();
+            rs[3] = T.tl();
+            rs[4] = T.w();
           }
         } else if (j != 0) {
           // crossed rows without a cluster (validated: rows strictly monotone)
@@ -607,6 +625,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   ps[3] = T.tl();
   ps[4] = T.w();
   float *pc = A.cov + 15 * t;
+  T.c[9] += T.c9l;
+  T.c[14] += T.c14l;
 #pragma unroll
   for (int i = 0; i < 15; ++i) pc[i] = T.c[i];
   A.chi2[t] = chi2sum;

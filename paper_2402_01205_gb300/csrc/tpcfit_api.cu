@@ -365,6 +365,7 @@ FitArgs make_args(tpcfit_handle *h, const tpcfit_frame *f, const tpcfit_result *
   a.ndf = r->ndf; a.status = r->status; a.accept = r->accept;
   a.chi2_out_c = r->chi2_out_cluster;
   a.chi2_in_c = r->chi2_in_cluster;
+  a.restart_state = r->restart_state;
   a.seed = s.seed;
   a.perm = c.sort_tracks ? s.perm : nullptr;
   a.hist = s.hist;
@@ -513,8 +514,8 @@ static int validate_host_offsets(const tpcfit_frame *f) {
 // host frame (and host or device results): chunks of tracks, copies and fits
 // of consecutive chunks overlapped (two staging buffers).
 static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
-  if (r->chi2_out_cluster || r->chi2_in_cluster)
-    return fail(TPCFIT_E_INVAL, "per-cluster chi2 outputs need a device frame and device results");
+  if (r->chi2_out_cluster || r->chi2_in_cluster || r->restart_state)
+    return fail(TPCFIT_E_INVAL, "diagnostic outputs need a device frame and device results");
   int rc = validate_host_offsets(f);
   if (rc) return rc;
   const int64_t *off = f->track_offsets;
@@ -571,6 +572,7 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     cf.x = S.x; cf.y = S.y; cf.z = S.z; cf.sy2 = S.sy2; cf.sz2 = S.sz2; cf.row = S.row;
     tpcfit_result cr = *r;
     cr.chi2_out_cluster = cr.chi2_in_cluster = nullptr;
+    cr.restart_state = nullptr;
     cr.state = S.state; cr.cov = S.cov; cr.x_ref = S.xref; cr.chi2 = S.chi2; cr.ndf = S.ndf;
     cr.status = S.status; cr.accept = S.accept;
     FitArgs a = make_args(h, &cf, &cr, h->scratch, c0);

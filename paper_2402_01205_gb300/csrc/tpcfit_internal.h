@@ -22,6 +22,7 @@ struct FitArgs {
   int32_t *ndf, *status;
   uint8_t *accept;
   double *chi2_out_c, *chi2_in_c;  // optional per-cluster chi2 (nullptr: not written)
+  float *restart_state;            // optional inward restart state (nullptr: not written)
   // scratch (device)
   float *seed;                   // n_tracks*5
   int32_t *perm;                 // n_tracks (sorted order), or nullptr for frame order

@@ -126,6 +126,7 @@ static void carve(void *mem, int64_t nt, int64_t nc, tpcfit_frame *df, tpcfit_re
   dr->accept = (uint8_t *)take((size_t)nc);
   dr->mem = TPCFIT_MEM_DEVICE;
   dr->chi2_out_cluster = dr->chi2_in_cluster = nullptr;
+  dr->restart_state = nullptr;
   *scratch = p;
 }
 
