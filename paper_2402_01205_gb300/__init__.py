@@ -292,6 +292,27 @@ def probe_fma_rates(device: int = 0) -> dict:
     return dict(fp64_fma_per_s=a.value, fp32_fma_per_s=b.value, sm_clock_khz=c.value)
 
 
+def fit_noalloc(frame, res: dict, config: Optional[Config] = None, stream=None) -> dict:
+    """tpcfit_fit_noalloc: fit a device frame without allocating device memory.
+
+    For callers that cannot allocate while they run (their device memory is
+    owned by another allocator, or their steady-state loop forbids
+    allocation).  Scratch comes from a static device array sized for
+    TPCFIT_NOALLOC_MAX_TRACKS (65536) tracks, shared by all calls: calls must
+    not overlap on the GPU.  Blocks until the fit is done."""
+    lib = _load()
+    fn = lib.tpcfit_fit_noalloc
+    fn.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_Frame), ctypes.POINTER(_Result), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    f, _, _, _ = _frame_struct(frame)
+    r, _ = _result_struct(res)
+    s = getattr(stream, "cuda_stream", stream)
+    rc = fn(ctypes.byref(config) if config is not None else None, ctypes.byref(f), ctypes.byref(r), s)
+    if rc < 0:
+        raise TpcfitError(rc, strerror(rc))
+    return res
+
+
 class Fitter:
     """Owns one library handle."""
 

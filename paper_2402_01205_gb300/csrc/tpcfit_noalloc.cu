@@ -1,0 +1,168 @@
+// Allocation-free fit entry point (declared in include/tpcfit_noalloc.h).
+//
+// Some callers cannot call cudaMalloc while they fit: an application whose
+// device memory is entirely reserved by another allocator (a framework's
+// caching pool that already owns the HBM, where an extra cudaMalloc fails or
+// fragments it), or a steady-state online loop that forbids allocation to keep
+// its latency predictable.  This entry point serves them: the caller passes
+// device-resident inputs and outputs, and every scratch buffer the fit needs
+// (seeds, sort permutation and histogram, work counter, error word, pad-row
+// table) lives in one file-scope device array of fixed size.  Nothing is
+// allocated, neither here nor in any library routine it calls.
+//
+// Limits and sharing: frames of at most TPCFIT_NOALLOC_MAX_TRACKS tracks.  The
+// array is shared by every call in the process on a given device and keeps the
+// last call's contents; each call clears the parts that must start at zero.
+// Calls that overlap on the GPU (two calls in flight at once, on any streams)
+// race on the array and give wrong results.
+
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "../../include/tpcfit.h"
+#include "../../include/tpcfit_noalloc.h"
+#include "tpcfit_internal.h"
+
+using namespace tpcfit;
+
+namespace {
+
+constexpr size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Layout of the static scratch (byte offsets).
+constexpr size_t kHistOff = 0;                                                     // 2*kKeyBins uint32
+constexpr size_t kWorkOff = a256(2 * kKeyBins * sizeof(uint32_t));                // u64 work counter
+constexpr size_t kErrOff = kWorkOff + 16;                                          // int32 frame error
+constexpr size_t kZeroBytes = kErrOff + 16;                                        // cleared per call
+constexpr size_t kRowxOff = a256(kZeroBytes);                                      // kMaxRows floats
+constexpr size_t kSeedOff = kRowxOff + a256(kMaxRows * sizeof(float));             // max_tracks*5 floats
+constexpr size_t kPermOff = kSeedOff + a256((size_t)TPCFIT_NOALLOC_MAX_TRACKS * 5 * sizeof(float));
+constexpr size_t kScratchBytes = kPermOff + a256((size_t)TPCFIT_NOALLOC_MAX_TRACKS * sizeof(int32_t));
+
+}  // namespace
+
+// The scratch array: every GPU that loads the library holds it until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void *g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// Error codes only: this entry point keeps no message state.
+int fail(int code, const char *) { return code; }
+
+// Pad-row plane positions, float-rounded from double, written into the scratch.
+__global__ void k_noalloc_rowx(float *rowx, double x0, double pitch) {
+  const int r = threadIdx.x;
+  if (r < kMaxRows) rowx[r] = (float)(x0 + (double)r * pitch);
+}
+
+// Per-device set-up, once per device with that device current: the host needs
+// the array's device address to hand it to the kernels.
+int setup(int device, void **addr) {
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (g_scratch_addr[device]) {
+    *addr = g_scratch_addr[device];
+    return TPCFIT_OK;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return fail(TPCFIT_E_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+  }
+  g_scratch_addr[device] = p;
+  *addr = p;
+  return TPCFIT_OK;
+}
+
+}  // namespace
+
+extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_frame *f, tpcfit_result *r,
+                                  void *stream) {
+  tpcfit_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else tpcfit_default_config(&cfg);
+  if (!f || !r) return fail(TPCFIT_E_INVAL, "frame or result is NULL");
+  if (f->mem != TPCFIT_MEM_DEVICE || r->mem != TPCFIT_MEM_DEVICE)
+    return fail(TPCFIT_E_INVAL, "tpcfit_fit_noalloc takes device frames and device results");
+  if (f->n_tracks < 0 || f->n_clusters < 0 || !f->track_offsets)
+    return fail(TPCFIT_E_INVAL, "bad frame sizes or NULL offsets");
+  if (f->n_tracks > TPCFIT_NOALLOC_MAX_TRACKS)
+    return fail(TPCFIT_E_INVAL, "frame has more tracks than TPCFIT_NOALLOC_MAX_TRACKS (65536); split it");
+  if (f->n_clusters > 0 && (!f->x || !f->y || !f->z || !f->sy2 || !f->sz2 || !f->row || !r->accept))
+    return fail(TPCFIT_E_INVAL, "NULL cluster or accept array");
+  if (f->n_tracks > 0 && (!r->state || !r->cov || !r->x_ref || !r->chi2 || !r->ndf || !r->status))
+    return fail(TPCFIT_E_INVAL, "NULL result array");
+  if (cfg.n_rows < 1 || cfg.n_rows > kMaxRows || !(cfg.snp_max > 0.f && cfg.snp_max < 1.f) ||
+      !(cfg.chi2_max > 0.f) || cfg.device < 0 || cfg.device >= kMaxDevices)
+    return fail(TPCFIT_E_INVAL, "configuration out of range");
+  if (cudaSetDevice(cfg.device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TPCFIT_E_NODEV, "cannot select the CUDA device");
+  }
+  void *base = nullptr;
+  int rc = setup(cfg.device, &base);
+  if (rc) return rc;
+  if (f->n_tracks == 0) return TPCFIT_OK;
+  char *sc = static_cast<char *>(base);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  FitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_tracks = f->n_tracks;
+  a.n_clusters = f->n_clusters;
+  a.off = f->track_offsets;
+  a.off_base = 0;
+  a.x = f->x; a.y = f->y; a.z = f->z; a.sy2 = f->sy2; a.sz2 = f->sz2; a.row = f->row;
+  a.state = r->state; a.cov = r->cov; a.x_ref = r->x_ref; a.chi2 = r->chi2;
+  a.ndf = r->ndf; a.status = r->status; a.accept = r->accept;
+  a.chi2_out_c = r->chi2_out_cluster;
+  a.chi2_in_c = r->chi2_in_cluster;
+  a.restart_state = r->restart_state;
+  a.hist = reinterpret_cast<uint32_t *>(sc + kHistOff);
+  a.work = reinterpret_cast<unsigned long long *>(sc + kWorkOff);
+  a.frame_error = reinterpret_cast<int32_t *>(sc + kErrOff);
+  a.seed = reinterpret_cast<float *>(sc + kSeedOff);
+  a.perm = cfg.sort_tracks ? reinterpret_cast<int32_t *>(sc + kPermOff) : nullptr;
+  a.row_x = reinterpret_cast<const float *>(sc + kRowxOff);
+  a.b = (float)(-0.299792458e-2 * (double)cfg.bz_tesla);
+  a.chi2_max = cfg.chi2_max;
+  a.chi2_max_d = (double)cfg.chi2_max;
+  a.xx0 = cfg.xx0_per_row;
+  a.mass2 = cfg.mass_gev * cfg.mass_gev;
+  a.snp_max = cfg.snp_max;
+  a.restart_scale = cfg.restart_scale;
+  for (int i = 0; i < 5; ++i) a.seed_cov[i] = cfg.seed_cov[i];
+  a.min_clusters = cfg.min_clusters;
+  a.n_rows = cfg.n_rows;
+
+  // the row table as the handle-based path builds it (exact 162/151 pitch for the default geometry)
+  double pitch = (double)cfg.row_pitch_cm;
+  if (cfg.row_x0_cm == 85.0f && cfg.row_pitch_cm == (float)(162.0 / 151.0)) pitch = 162.0 / 151.0;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device);
+  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_blocks_per_sm(256);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(sc, 0, kZeroBytes, st)) != cudaSuccess) goto cuda_fail;
+  k_noalloc_rowx<<<1, kMaxRows, 0, st>>>(reinterpret_cast<float *>(sc + kRowxOff), (double)cfg.row_x0_cm, pitch);
+  if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
+  if ((e = launch_prepare(a, st)) != cudaSuccess) goto cuda_fail;
+  if ((e = launch_sort(a, st, nullptr)) != cudaSuccess) goto cuda_fail;
+  if ((e = launch_fit(a, sms * bps, 256, st)) != cudaSuccess) goto cuda_fail;
+  {
+    int32_t err_host = 0;
+    if ((e = cudaMemcpyAsync(&err_host, a.frame_error, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      goto cuda_fail;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) goto cuda_fail;
+    if (err_host) return fail(TPCFIT_E_INVAL, "malformed track offsets");
+  }
+  return TPCFIT_OK;
+cuda_fail:
+  cudaGetLastError();
+  return e == cudaSuccess ? TPCFIT_OK : TPCFIT_E_CUDA;
+}
