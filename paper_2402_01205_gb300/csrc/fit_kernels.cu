@@ -7,11 +7,12 @@
 //
 // Launch sequence of one frame:
 //   k_prepare   thread per track: offset checks, 3-point seed, status preset,
-//               sort key (cluster count) histogram
-//   k_sort_*    counting sort of tracks by cluster count, longest first
+//               sort key (pad rows crossed) histogram
+//   k_sort_*    counting sort of tracks by pad rows crossed, longest first
 //   k_fit       persistent grid; each warp claims 32 consecutive tracks of the
-//               sorted order, one thread per track, and steps cluster by
-//               cluster through the outward and the inward pass.
+//               sorted order, one thread per track, and steps pad row by pad
+//               row through the outward and the inward pass (every lane
+//               propagates each step; lanes with a cluster on the row update).
 //
 // Precision: propagation, covariance transport and the gain/update are FP32.
 // The innovation-matrix determinant and reciprocal, the quadratic form
@@ -20,7 +21,7 @@
 // costs the same with one active lane as with 32, so the FP64 island is kept
 // to 11 instructions per update, every FP32->FP64 widening is done exactly
 // with integer operations, and warps are filled with tracks of equal length
-// so that every FP64 instruction serves 32 updates.
+// so that the FP64 instructions of a step serve (almost) every lane.
 //
 // Track positions are carried as FP32 offsets (dy, dz) from the last
 // cluster's coordinates: residuals are then formed from small numbers and the
@@ -56,7 +57,6 @@ __device__ __forceinline__ void cp_async4(float *smem, const float *gmem, bool v
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // ---------------------------------------------------------------------------
 // Exact binary32 -> binary64 widening with integer operations (IEEE 754: the
 // exponent is re-biased by 1023-127 = 896, the 23-bit fraction moves to the
@@ -73,18 +73,50 @@ __device__ __forceinline__ double widen(float f) {
   return __longlong_as_double((long long)d);
 }
 
+// The decisions and conversions below work on the two 32-bit halves of a
+// binary64 value.  The halves are taken with an opaque move so that the
+// compiler keeps integer operations and does not turn the tests back into
+// FP64-pipe instructions (which cost as much as the arithmetic they guard).
+__device__ __forceinline__ void split64(double x, uint32_t &hi, uint32_t &lo) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+}
+__device__ __forceinline__ bool is_nan64(uint32_t hi, uint32_t lo) {
+  const uint32_t ha = hi & 0x7fffffffu;
+  return ha > 0x7ff00000u || (ha == 0x7ff00000u && lo != 0u);
+}
+// x <= g for a positive, finite g given as (ghi, glo); IEEE semantics for x.
+__device__ __forceinline__ bool le64(double x, uint32_t ghi, uint32_t glo) {
+  uint32_t hi, lo;
+  split64(x, hi, lo);
+  if (is_nan64(hi, lo)) return false;
+  if (hi >> 31) return true;  // negative (or -0)
+  return hi < ghi || (hi == ghi && lo <= glo);
+}
+// x <= 0 (NaN: false).
+__device__ __forceinline__ bool le0_64(double x) {
+  uint32_t hi, lo;
+  split64(x, hi, lo);
+  if (is_nan64(hi, lo)) return false;
+  return (hi >> 31) || ((hi | lo) == 0u);
+}
+
 // Non-negative binary64 -> binary32, round to nearest even, with integer
 // operations only: values below the binary32 normal range flush to zero,
 // values above it give +Inf, NaN stays NaN.  (The inputs are reciprocals of
 // positive determinants.)
 __device__ __forceinline__ float narrow_pos(double v) {
-  const uint64_t b = (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
-  const uint32_t ex = (uint32_t)(b >> 52);
-  const uint64_t r = b + 0x0FFFFFFFull + ((b >> 29) & 1ull);
-  uint32_t f = (uint32_t)(r >> 29) - (896u << 23);
+  uint32_t hi, lo;
+  split64(v, hi, lo);
+  hi &= 0x7fffffffu;
+  const uint32_t ex = hi >> 20;
+  // exponent and top 23 fraction bits; the bias change wraps correctly mod 2^32
+  uint32_t m = (hi << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1fffffffu;
+  m += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  uint32_t f = m - (896u << 23);
   f = (ex > 1150u) ? 0x7f800000u : f;
   f = (ex < 897u) ? 0u : f;
-  f = (b > 0x7ff0000000000000ull) ? 0x7fc00000u : f;
+  f = is_nan64(hi, lo) ? 0x7fc00000u : f;
   return __uint_as_float(f);
 }
 
@@ -153,7 +185,11 @@ __global__ void __launch_bounds__(256) k_prepare(FitArgs A) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) sd[i] = p[i];
     A.status[t] = st;
-    const int key = (st == ST_OK) ? (int)(n < kMaxRows ? n : kMaxRows) : 0;
+    int key = 0;  // rows crossed, so that warps get tracks with the same number of row steps
+    if (st == ST_OK) {
+      const int rr = (int)A.row[e - 1] - (int)A.row[a] + 1;
+      key = rr < 1 ? 1 : (rr > kMaxRows ? kMaxRows : rr);
+    }
     atomicAdd(&s_hist[key], 1u);
   }
   __syncthreads();
@@ -178,8 +214,9 @@ __global__ void k_sort_scan(uint32_t *hist) {
 
 __device__ __forceinline__ int track_key(const FitArgs &A, int64_t t) {
   if (A.status[t] != ST_OK) return 0;
-  const int64_t n = A.off[t + 1] - A.off[t];
-  return (int)(n < kMaxRows ? n : kMaxRows);
+  const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
+  const int rr = (int)A.row[e - 1] - (int)A.row[a] + 1;
+  return rr < 1 ? 1 : (rr > kMaxRows ? kMaxRows : rr);
 }
 
 __global__ void __launch_bounds__(256) k_sort_scatter(FitArgs A) {
@@ -232,7 +269,7 @@ __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_m
   const float q1 = fmaf(-s1, s1, 1.0f), q2 = fmaf(-s2, s2, 1.0f);
   const float ic1 = rsqrtf(q1), ic2 = rsqrtf(q2);
   const float c1 = q1 * ic1, c2 = q2 * ic2;  // cos phi at both planes
-  const float iB = __frcp_rn(c1 + c2);
+  const float iB = __fdividef(1.0f, c1 + c2);
   const float Tn = (s1 + s2) * iB;           // tangent of the chord direction
   const float kk2 = fmaf(Tn, Tn, 1.0f);
   const float ik = rsqrtf(kk2);
@@ -313,10 +350,10 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   const float s = T.snp(), t = T.tl(), w = T.w();
   const float tt = fmaf(t, t, 1.0f);
   const float cs2 = fmaf(-s, s, 1.0f);
-  const float itt = __frcp_rn(tt);
+  const float itt = __fdividef(1.0f, tt);
   const float pinv2 = w * w * itt;                  // 1/p^2
   const float ib2 = fmaf(mass2, pinv2, 1.0f);       // 1/beta^2
-  const float eps = xx0 * sqrtf(tt * __frcp_rn(cs2));
+  const float eps = xx0 * (tt * rsqrtf(tt * cs2));  // xx0 sqrt(tt / cs2)
   const float lg = fmaf(0.038f, __logf(eps * ib2), 1.0f);
   const float th2 = (0.0136f * 0.0136f) * pinv2 * ib2 * eps * lg * lg;
   T.c[5] = fmaf(th2, cs2 * tt, T.c[5]);
@@ -328,8 +365,8 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
 // Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: det,
 // reciprocal (Newton step from an FP32 seed), quadratic form, chi2 product,
 // gate; the chi2 sum is done by the caller.  Returns the status (OK / NOT_PD).
-__device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, long long gate_bits,
-                                      bool &acc, double &chi2) {
+__device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, uint32_t gate_hi,
+                                      uint32_t gate_lo, bool &acc, double &chi2) {
   float *c = T.c;
   const float r0 = (yc - T.ya) - T.dy;
   const float r1 = (zc - T.za) - T.dz;
@@ -339,18 +376,16 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
   const double m2s10 = widen(-2.0f * S10);  // exact: scaling by -2
   const double q0 = widen(r0), q1 = widen(r1);
   const double det = fma(s00, s11, -(s10 * s10));
-  const long long db = __double_as_longlong(det);
-  const bool notpd = (db <= 0ll && (db & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) || S00 <= 0.0f;
+  const bool notpd = le0_64(det) || S00 <= 0.0f;
   const float det32 = fmaf(S00, S11, -(S10 * S10));
-  const double y0 = widen(__frcp_rn(det32));
+  const double y0 = widen(__fdividef(1.0f, det32));
   const double ey = fma(-det, y0, 1.0);
   const double inv = fma(y0, ey, y0);      // 1/det, one Newton step
   double qf = fma(m2s10, q1, s11 * q0);    // s11 r0 - 2 s10 r1
   qf = q0 * qf;
   qf = fma(s00 * q1, q1, qf);              // r^T adj(S) r
   chi2 = qf * inv;
-  const long long cb = __double_as_longlong(chi2);
-  acc = (cb <= gate_bits) && ((cb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll);
+  acc = le64(chi2, gate_hi, gate_lo);
   // ---- back to FP32 ----
   if (notpd) {
     acc = false;
@@ -414,9 +449,25 @@ __device__ __forceinline__ bool finite5(float a, float b, float c, float d, floa
 // ---------------------------------------------------------------------------
 // k_fit: persistent warps over the (sorted) track list.
 // ---------------------------------------------------------------------------
+// Validation of a cluster when the outward pass reaches it (before any
+// propagation towards it): row inside the geometry and above the previous
+// one, finite values, positive variances.
+__device__ __forceinline__ int check_cluster(int r, int rprev, int n_rows, float x, float y, float z, float vy,
+                                             float vz) {
+  if (r >= n_rows || r <= rprev) return ST_BAD_INPUT;
+  if (!finite5(x, y, z, vy, vz)) return ST_NONFINITE;
+  if (!(vy > 0.f) || !(vz > 0.f)) return ST_BAD_INPUT;
+  return ST_OK;
+}
+
+struct Clu {
+  float x, y, z, vy, vz;
+  int r;
+};
+
 // Issue the copies of chunk c (clusters a+4c .. a+4c+3, clipped to the track)
-// into buffer c&1 of this lane's staging columns; returns the chunk's rows
-// packed in one word (loaded now, used one chunk later).
+// into buffer c&1 of this lane's staging column; returns the chunk's rows
+// packed in one word (loaded now, used when the chunk becomes current).
 __device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, float *stg) {
   const int buf = c & 1;
   uint32_t rows = 0;
@@ -435,6 +486,20 @@ __device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int
   }
   cp_async_commit();
   return rows;
+}
+
+// Cluster lk of the track from the staged chunk lk/4 (which must be current).
+__device__ __forceinline__ Clu read_staged(const float *stg, int lk, uint32_t rows_cur) {
+  const int ch = lk / kChunk, slot = lk % kChunk;
+  const float *src = stg + (((ch & 1) * kStageArrays) * kChunk + slot) * kFitBlock;
+  Clu c;
+  c.x = src[0];
+  c.y = src[kChunk * kFitBlock];
+  c.z = src[2 * kChunk * kFitBlock];
+  c.vy = src[3 * kChunk * kFitBlock];
+  c.vz = src[4 * kChunk * kFitBlock];
+  c.r = (rows_cur >> (8 * slot)) & 0xffu;
+  return c;
 }
 
 __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
@@ -475,131 +540,138 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
     float xcur = xref;
 #pragma unroll
     for (int w = 0; w < kBitWords; ++w) bits[32 * w] = 0u;
-    int done = 0;     // clusters (from the outer end) whose accept byte is final
-    int out_done = 0; // clusters the outward pass updated with
-    int nacc_out = 0; // ... and accepted
+    int done = 0;      // clusters (from the outer end) whose accept byte is final
+    int out_done = 0;  // clusters the outward pass updated with
     if (st0 == ST_OK) {
-      const long long gate_bits = __double_as_longlong(A.chi2_max_d);
-      int rprev = -1;
-      // clusters staged through shared memory, two chunks of kChunk in flight
+      uint32_t gate_hi, gate_lo;
+      split64(A.chi2_max_d, gate_hi, gate_lo);
+      int nacc_out = 0;
+      // candidate: the next cluster to use, read from the lane's staged chunk;
+      // the following chunk is in flight (cp.async) while this one is used
       const int nch = (n + kChunk - 1) / kChunk;
+      int kc = 0;
       uint32_t rows_cur = stage_chunk(A, a, e, 0, stg), rows_next = 0;
       cp_async_wait_all();
       if (nch > 1) rows_next = stage_chunk(A, a, e, 1, stg);
-      for (int j = 0; j < 2 * n; ++j) {
-        const bool inward = j >= n;
-        const int lk = inward ? (2 * n - 1 - j) : j;
-        const int64_t k = a + lk;
-        const int ch = lk / kChunk, slot = lk % kChunk;
-        if (!inward) {
-          if (slot == 0 && j > 0) {  // entering chunk ch from ch-1
-            cp_async_wait_all();
-            rows_cur = rows_next;
-            if (ch + 1 < nch) rows_next = stage_chunk(A, a, e, ch + 1, stg);
-          }
-        } else if (j == n) {  // still in the last chunk; restage the one before it
-          if (nch > 1) rows_next = stage_chunk(A, a, e, nch - 2, stg);
-        } else if (slot == kChunk - 1) {  // entering chunk ch from ch+1
-          cp_async_wait_all();
-          rows_cur = rows_next;
-          if (ch > 0) rows_next = stage_chunk(A, a, e, ch - 1, stg);
-        }
-        const float *src = stg + (((ch & 1) * kStageArrays) * kChunk + slot) * kFitBlock;
-        const float xk = src[0], yk = src[kChunk * kFitBlock], zk = src[2 * kChunk * kFitBlock];
-        const float vyk = src[3 * kChunk * kFitBlock], vzk = src[4 * kChunk * kFitBlock];
-        const int rk = (rows_cur >> (8 * slot)) & 0xffu;
-        if (!inward) {  // validation when the outward pass reaches the cluster
-          if (rk >= A.n_rows || rk <= rprev) { st = ST_BAD_INPUT; break; }
-          if (!finite5(xk, yk, zk, vyk, vzk)) { st = ST_NONFINITE; break; }
-          if (!(vyk > 0.f) || !(vzk > 0.f)) { st = ST_BAD_INPUT; break; }
-        }
-        if (j == n) {
-          if (10 * nacc_out < 9 * n) {
-            // the outward pass accepted fewer than 90 % of the clusters: re-seed
-            // at the outermost cluster (circle through clusters n-1, n/2, 0 for
-            // motion towards cluster 0, reversed) with the seed covariance
-            float p[5];
-            const int64_t m = a + n / 2;
-            seed3(xk, yk, zk, A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
-            T.sp = -p[2];
-            T.spl = 0.f;
-            T.tl0 = -p[3];
-            T.dtl = 0.f;
-            T.w0 = -p[4];
-            T.dw = 0.f;
-            T.ya = yk;
-            T.za = zk;
-            T.dy = 0.f;
-            T.dz = 0.f;
-#pragma unroll
-            for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
-            T.c[0] = A.seed_cov[0];
-            T.c[2] = A.seed_cov[1];
-            T.c[5] = A.seed_cov[2];
-            T.c[9] = A.seed_cov[3];
-            T.c[14] = A.seed_cov[4];
-            T.c9l = 0.f;
-            T.c14l = 0.f;
-          } else {
-            // inward restart: diagonal, outward variances inflated, capped at the seed's
-            const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
-            const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
-            const float d2 = fminf(A.restart_scale * T.c[5], A.seed_cov[2]);
-            const float d3 = fminf(A.restart_scale * (T.c[9] + T.c9l), A.seed_cov[3]);
-            const float d4 = fminf(A.restart_scale * (T.c[14] + T.c14l), A.seed_cov[4]);
-#pragma unroll
-            for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
-            T.c[0] = d0;
-            T.c[2] = d1;
-            T.c[5] = d2;
-            T.c[9] = d3;
-            T.c[14] = d4;
-            T.c9l = 0.f;
-            T.c14l = 0.f;
-          }
-          if (A.restart_state) {
-            float *rs = A.restart_state + 5 * t;
-            rs[0] = T.ya + T.dy;
-            rs[1] = T.za + T.dz;
-            rs[2] = T.snp();
-            rs[3] = T.tl();
-            rs[4] = T.w();
-          }
-        } else if (j != 0) {
-          // crossed rows without a cluster (validated: rows strictly monotone)
-          const int dir = inward ? -1 : 1;
-          bool ok = true;
-          for (int r = rprev + dir; r != rk; r += dir) {
-            const float xr = s_rowx[r];
-            if (!propagate(T, xr - xcur, A.b, A.snp_max)) { ok = false; break; }
-            xcur = xr;
-            if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
-          }
-          if (!ok) { st = ST_SNP_LIMIT; break; }
-        }
-        if (!propagate(T, xk - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
-        xcur = xk;
-        rprev = rk;
-        bool acc;
-        double chi2;
-        const int ust = update(T, yk, zk, vyk, vzk, gate_bits, acc, chi2);
-        if (ust != ST_OK) { st = ust; break; }
-        if (!inward) {
-          if (acc) bits[32 * (lk >> 5)] |= 1u << (lk & 31);
-          if (A.chi2_out_c) A.chi2_out_c[k] = chi2;
+      Clu cand = read_staged(stg, 0, rows_cur);
+      int rprev = -1;
+      st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
+      // ---------------- outward pass: rows row[0] .. row[n-1] ----------------
+      for (int r = cand.r; st == ST_OK; ++r) {
+        const bool has = (cand.r == r);
+        const float xt = has ? cand.x : s_rowx[r];
+        if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
+        xcur = xt;
+        if (has) {
+          bool acc;
+          double chi2;
+          const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate_hi, gate_lo, acc, chi2);
+          if (ust != ST_OK) { st = ust; break; }
+          if (acc) bits[32 * (kc >> 5)] |= 1u << (kc & 31);
+          if (A.chi2_out_c) A.chi2_out_c[a + kc] = chi2;
           ++out_done;
           nacc_out += acc ? 1 : 0;
-        } else {
-          if (A.chi2_in_c) A.chi2_in_c[k] = chi2;
-          chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
-          nacc += acc ? 1 : 0;
-          const uint32_t ob = (bits[32 * (lk >> 5)] >> (lk & 31)) & 1u;
-          A.accept[k] = (uint8_t)(ob | (acc ? 2u : 0u));
-          ++done;
+          rprev = cand.r;
+          if (++kc < n) {
+            if (kc % kChunk == 0) {  // entering chunk kc/4
+              cp_async_wait_all();
+              rows_cur = rows_next;
+              if (kc / kChunk + 1 < nch) rows_next = stage_chunk(A, a, e, kc / kChunk + 1, stg);
+            }
+            cand = read_staged(stg, kc, rows_cur);
+            const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
+            if (vs != ST_OK) { st = vs; break; }
+          }
         }
         if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
+        if (kc == n) break;
       }
-      cp_async_wait_all();  // no copy may land in the columns after this track
+      // ---------------- restart ----------------
+      if (st == ST_OK) {
+        // cand holds the outermost cluster n-1
+        if (10 * nacc_out < 9 * n) {
+          // the outward pass accepted fewer than 90 % of the clusters: re-seed
+          // at the outermost cluster (circle through clusters n-1, n/2, 0 for
+          // motion towards cluster 0, reversed) with the seed covariance
+          float p[5];
+          const int64_t m = a + n / 2;
+          seed3(cand.x, cand.y, cand.z, A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
+          T.sp = -p[2];
+          T.spl = 0.f;
+          T.tl0 = -p[3];
+          T.dtl = 0.f;
+          T.w0 = -p[4];
+          T.dw = 0.f;
+          T.ya = cand.y;
+          T.za = cand.z;
+          T.dy = 0.f;
+          T.dz = 0.f;
+#pragma unroll
+          for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+          T.c[0] = A.seed_cov[0];
+          T.c[2] = A.seed_cov[1];
+          T.c[5] = A.seed_cov[2];
+          T.c[9] = A.seed_cov[3];
+          T.c[14] = A.seed_cov[4];
+        } else {
+          // inward restart: diagonal, outward variances inflated, capped at the seed's
+          const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
+          const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
+          const float d2 = fminf(A.restart_scale * T.c[5], A.seed_cov[2]);
+          const float d3 = fminf(A.restart_scale * (T.c[9] + T.c9l), A.seed_cov[3]);
+          const float d4 = fminf(A.restart_scale * (T.c[14] + T.c14l), A.seed_cov[4]);
+#pragma unroll
+          for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+          T.c[0] = d0;
+          T.c[2] = d1;
+          T.c[5] = d2;
+          T.c[9] = d3;
+          T.c[14] = d4;
+        }
+        T.c9l = 0.f;
+        T.c14l = 0.f;
+        if (A.restart_state) {
+          float *rs = A.restart_state + 5 * t;
+          rs[0] = T.ya + T.dy;
+          rs[1] = T.za + T.dz;
+          rs[2] = T.snp();
+          rs[3] = T.tl();
+          rs[4] = T.w();
+        }
+        // ---------------- inward pass: rows row[n-1] .. row[0] ----------------
+        kc = n - 1;
+        // the last chunk is current; restage the one below it into the other buffer
+        if (nch > 1) rows_next = stage_chunk(A, a, e, nch - 2, stg);
+        for (int r = cand.r;; --r) {
+          const bool has = (cand.r == r);
+          const float xt = has ? cand.x : s_rowx[r];
+          if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
+          xcur = xt;
+          if (has) {
+            bool acc;
+            double chi2;
+            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate_hi, gate_lo, acc, chi2);
+            if (ust != ST_OK) { st = ust; break; }
+            if (A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;
+            chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
+            nacc += acc ? 1 : 0;
+            const uint32_t ob = (bits[32 * (kc >> 5)] >> (kc & 31)) & 1u;
+            A.accept[a + kc] = (uint8_t)(ob | (acc ? 2u : 0u));
+            ++done;
+            if (--kc >= 0) {
+              if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above
+                cp_async_wait_all();
+                rows_cur = rows_next;
+                if (kc / kChunk > 0) rows_next = stage_chunk(A, a, e, kc / kChunk - 1, stg);
+              }
+              cand = read_staged(stg, kc, rows_cur);
+            }
+          }
+          if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
+          if (kc < 0) break;
+        }
+      }
+      cp_async_wait_all();  // no copy may land in the column after this track
       if (st == ST_OK) {
         bool fin = isfinite(T.dy) && isfinite(T.dz) && isfinite(T.snp()) && isfinite(T.tl()) && isfinite(T.w());
 #pragma unroll
@@ -634,7 +706,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   A.status[t] = st;
 }
 
-__global__ void __launch_bounds__(kFitBlock, 2) k_fit(FitArgs A) {
+__global__ void __launch_bounds__(kFitBlock, 3) k_fit(FitArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   float *s_rowx = reinterpret_cast<float *>(smem);
   uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + kSmemRowx);

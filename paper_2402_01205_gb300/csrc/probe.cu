@@ -2,8 +2,8 @@
 // peaks (declared in include/tpcfit_probe.h).
 #include <cuda_runtime.h>
 
-#include "../../include/tpcfit.h"
-#include "../../include/tpcfit_probe.h"
+#include "tpcfit.h"
+#include "tpcfit_probe.h"
 
 namespace {
 

@@ -21,8 +21,8 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/tpcfit.h"
-#include "../../include/tpcfit_noalloc.h"
+#include "tpcfit.h"
+#include "tpcfit_noalloc.h"
 #include "tpcfit_internal.h"
 
 using namespace tpcfit;

@@ -26,7 +26,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/tpcfit.h"
+#include "tpcfit.h"
 #include "tpcfit_internal.h"
 
 using namespace tpcfit;
