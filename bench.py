@@ -38,7 +38,11 @@ sys.path.insert(0, ROOT)
 import tpcgen  # noqa: E402
 
 WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT (mean 0.6 GeV/c), 36 sectors, "
-                       "x/X0 5e-4 per row, 5% dropout, 1% outliers, seed 0"}
+                       "x/X0 5e-4 per row, 5% dropout, 1% outliers, seed 0",
+             "events4096": "4,096 independent events, tracks per event log-normal (median 800, sigma_ln 1.0, "
+                           "10-20,000), tracks of 10-152 rows, pT log-uniform 0.2-10 GeV/c, 36 sectors, x/X0 5e-4 "
+                           "per row, 5% dropout, 1% outliers, seed 0; one graph-captured persistent launch sequence "
+                           "per step vs one plain launch sequence per event"}
 FP64_PER_CLUSTER = 21         # FP64 pipe instructions per cluster: 10 (outward update) + 11 (inward update + sum)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
@@ -157,7 +161,14 @@ def run_reference(args, ws, rank):
     import oracle
     oracle.build()
     n = args.ref_tracks
-    frame = tpcgen.generate(args.workload, n_tracks=n, seed=0)
+    if args.workload == "events4096":
+        # the first events of the same batch (sizes and tracks are drawn in index order)
+        sizes = tpcgen.lognormal_sizes(args.n_events, 800.0, 1.0, 10.0, 20000.0, seed=1000003)
+        k = max(1, int(np.searchsorted(np.cumsum(sizes), n, side="right")))
+        frame, _ = tpcgen.event_batch(n_events=k, seed=0)
+        n = frame.n_tracks
+    else:
+        frame = tpcgen.generate(args.workload, n_tracks=n, seed=0)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle.fit(frame.subset(0, min(n, 2000)), oracle.FitConfig(), threads=cores)
@@ -172,13 +183,191 @@ def run_reference(args, ws, rank):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                   "sample": f"first {n} tracks ({frame.n_clusters} clusters) of the frame per step"},
+                   "sample": f"first {n} tracks ({frame.n_clusters} clusters) of the workload per step"},
         "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {n} tracks ({frame.n_clusters} clusters) per step"},
         "e2e": {"value": value, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def gpu_index(local: int) -> int:
+    v = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    return int(v) if v.isdigit() else local
+
+
+def reduce_max(dist, torch, x: float) -> float:
+    if not dist:
+        return x
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(dist, torch, x: float) -> float:
+    if not dist:
+        return x
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+def run_events(args, ws, rank, local, T, torch, dist, probe):
+    """Batched uneven events: the autotuned batch graph vs one launch per event."""
+    from paper_2402_01205_gb300 import autotune
+    frame, ev = tpcgen.event_batch(n_events=args.n_events, seed=rank)
+    nt, nc = frame.n_tracks, frame.n_clusters
+    names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
+
+    class F:
+        pass
+
+    dev = F()
+    for k in names:
+        setattr(dev, k, torch.from_numpy(np.ascontiguousarray(getattr(frame, k))).cuda())
+    props = torch.cuda.get_device_properties(local)
+    table = autotune.load(args.tune_table) if args.tune_table else {}
+    entry = autotune.lookup(table, props.name, props.multi_processor_count, nt)
+    tuned_now = entry is None
+    if tuned_now:
+        entry = autotune.tune(T, dev, reps=3, device=local)
+        if args.tune_table and rank == 0:
+            autotune.save(args.tune_table, autotune.table_key(props.name, props.multi_processor_count, nt), entry)
+    cfg = autotune.config_for(entry)
+    fx = T.Fitter(device=local, **cfg)
+    stream = torch.cuda.Stream()
+    # batched arm: one captured launch sequence over all events per step
+    batch = T.Batch(fx, dev)
+    for _ in range(args.warmup):
+        batch.launch(stream)
+    batch.sync()
+    clocks = ClockSampler(gpu_index(local))
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    batch.sync()
+    ms = reduce_max(dist, torch, e0.elapsed_time(e1))
+    nc_all = reduce_sum(dist, torch, float(nc))
+    nt_all = reduce_sum(dist, torch, float(nt))
+    value = nc_all * args.steps / (ms * 1e-3)
+    res_b = {k: v.clone() for k, v in batch.res.items()}
+    # kernel split of the same launch sequence (event-timed plain fit of the whole batch frame)
+    res_t = T.alloc_result(nt, nc, device=torch.device("cuda", local))
+    fx.reset_timing()
+    for _ in range(3):
+        fx.fit_async(dev, res_t, stream=stream)
+    fx.sync()
+    tm = fx.timing()
+    # per-event arm: one plain launch sequence per event, in event order, on one stream
+    res_e = T.alloc_result(nt, nc, device=torch.device("cuda", local))
+    views = T.EventViews(dev, res_e, ev)
+    views.fit_async(fx, stream)
+    fx.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.perf_counter()
+    p0.record(stream)
+    for _ in range(args.per_event_steps):
+        views.fit_async(fx, stream)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    host_s = time.perf_counter() - h0
+    ms_pe = reduce_max(dist, torch, p0.elapsed_time(p1))
+    same = all(torch.equal(res_b[k], res_e[k]) or (k in ("state", "cov") and torch.equal(
+        torch.nan_to_num(res_b[k], nan=7.0), torch.nan_to_num(res_e[k], nan=7.0))) for k in res_b)
+    status = res_b["status"].cpu().numpy()
+    ok = status == 0
+    lens = np.diff(frame.offsets)
+    nc_fit = int(lens[ok].sum())
+    seq_s = tm["total_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
+    fit_s = tm["fit_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
+    peaks, peak_src = measured_peaks()
+    fp64_peak = probe["fp64_fma_per_s"]
+    achieved = FP64_PER_CLUSTER * nc_fit / fit_s
+    hbm_achieved = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
+    traffic, traffic_note = profiled_traffic(nc_fit)
+    roofline = {
+        "bound": "alu", "kernel": "k_fit", "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
+        "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "frac": achieved / fp64_peak,
+        "peak_source": "measured live: FP64 FMA chain probe in libtpcfit (tpcfit_probe_fma_rates)",
+        "traffic": traffic, "traffic_note": traffic_note, "fit_ms_avg": fit_s * 1e3,
+        "fp64_inst_per_cluster": FP64_PER_CLUSTER,
+        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
+                "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
+    }
+    e2e = None
+    if args.e2e_steps > 0:
+        host = F()
+        for k in names:
+            t = torch.empty(getattr(dev, k).shape, dtype=getattr(dev, k).dtype, pin_memory=True)
+            t.copy_(torch.from_numpy(np.ascontiguousarray(getattr(frame, k))))
+            setattr(host, k, t)
+        hres = T.alloc_result(nt, nc, pinned=True)
+        fx.fit(host, hres)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fx.fit(host, hres)
+            _ = float(hres["chi2"][0])
+        dt = reduce_max(dist, torch, time.perf_counter() - t0)
+        e2e = {"value": nc_all * args.e2e_steps / dt, "unit": "clusters/s",
+               "h2d_bytes_per_step": int(21 * nc + 8 * (nt + 1)), "d2h_bytes_per_step": int(100 * nt + nc),
+               "ms_per_step": dt / args.e2e_steps * 1e3,
+               "path": "tpcfit_fit of the concatenated events, TPCFIT_MEM_HOST pinned, chunked overlap"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(frame)
+    if rank == 0:
+        sizes = np.diff(ev)
+        line = {
+            "metric": "clusters/s fitted on 1 GB300, batched uneven events (FP32 fit, FP64 innovation inverse "
+                      "and chi2)",
+            "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "events4096", "description": WORKLOADS["events4096"], "n_events": len(sizes),
+                       "n_tracks": nt, "n_clusters": nc, "tracks_per_event_median": float(np.median(sizes)),
+                       "tracks_per_event_min": int(sizes.min()), "tracks_per_event_max": int(sizes.max()),
+                       "tracks_fitted_ok": int(ok.sum()), "l2": f"inputs {21 * nc / 1e9:.1f} GB > L2; no flush",
+                       "parallelism": f"replicas x{ws}", "launch": "tpcfit_batch graph replay",
+                       "autotuned": cfg, "autotune_ms": entry["ms"], "tuned_in_this_run": tuned_now,
+                       "autotune_candidates": entry.get("all")},
+            "tracks_per_s": nt_all * args.steps / (ms * 1e-3),
+            "per_event": {"value": nc_all * args.per_event_steps / (ms_pe * 1e-3), "unit": "clusters/s",
+                          "ms_per_step": ms_pe / args.per_event_steps, "steps": args.per_event_steps,
+                          "host_ms_per_step": host_s / args.per_event_steps * 1e3,
+                          "launch": "tpcfit_fit_async per event (memset + 4 kernels + 1 copy each), one stream",
+                          "speedup_of_batch": (ms_pe / args.per_event_steps) / (ms / args.steps),
+                          "results_identical_to_batch": bool(same)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(tm["kernel_launches"]) * args.steps,
+            "clocks": clk,
+            "kernel_ms": {"prepare": tm["prepare_ms_sum"] / tm["n_timed"], "sort": tm["sort_ms_sum"] / tm["n_timed"],
+                          "fit": tm["fit_ms_sum"] / tm["n_timed"], "sequence": seq_s * 1e3},
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    fx.close()
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -193,6 +382,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-tracks", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-events", type=int, default=4096, help="events4096: number of events (testing)")
+    ap.add_argument("--per-event-steps", type=int, default=3, help="events4096: timed steps of the per-event arm")
+    ap.add_argument("--tune-table", default=None, help="events4096: JSON tune table to read / extend")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -209,6 +401,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     probe = T.probe_fma_rates(local)
+    if args.workload == "events4096":
+        return run_events(args, ws, rank, local, T, torch, dist, probe)
     kw = {} if args.n_tracks is None else {"n_tracks": args.n_tracks}
     frame = tpcgen.generate(args.workload, seed=rank, **kw)
     nt, nc = frame.n_tracks, frame.n_clusters

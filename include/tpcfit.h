@@ -85,7 +85,7 @@ typedef struct tpcfit_config {
   uint64_t hbm_budget_bytes; /* serving: device bytes that resident frames may use (120 GB) */
   int32_t max_slots;      /* serving: frames resident at once (8) */
   int32_t device;         /* CUDA device ordinal (0) */
-  int32_t block_threads;  /* fit kernel block size, 0 = tuned default */
+  int32_t block_threads;  /* fit kernel block size: 128 or 256 (0 = 256) */
   int32_t blocks_per_sm;  /* fit kernel resident blocks per SM, 0 = occupancy maximum */
   int32_t sort_tracks;    /* 1: fit tracks longest-first (default); 0: in frame order */
   int32_t reserved[7];
@@ -157,6 +157,37 @@ int tpcfit_fit_async(tpcfit_handle *h, const tpcfit_frame *frame, tpcfit_result 
 /* Wait (bounded by timeout_s; < 0 = no bound) for the handle's enqueued work
  * and report a malformed-frame error seen since the last sync. */
 int tpcfit_sync(tpcfit_handle *h, double timeout_s);
+
+/* Batched events (Sec. 5: a frame holds many collisions; Sec. 4: a fixed
+ * pipeline replayed per input): the tracks of many events of uneven
+ * multiplicity are concatenated into one DEVICE frame, each event a
+ * contiguous range of tracks, and fitted by one launch sequence (offset
+ * check and seed, sort, persistent fit kernel) captured once into a CUDA
+ * graph; every tpcfit_batch_launch replays it with no host work per event.
+ * Results land in the DEVICE result buffers given at creation, track by
+ * track, so an event's results are the same index range.  The frame's and
+ * the results' buffers and the handle must outlive the batch; their contents
+ * may change between replays, their sizes may not.  The batch owns its
+ * scratch (not the handle's), so it may replay while the handle fits other
+ * frames on other streams.  Replays of one batch run one after another
+ * (CUDA orders launches of one graph), whatever streams they are given. */
+typedef struct tpcfit_batch tpcfit_batch;
+
+/* Capture the launch sequence of `frame` -> `res` into a graph.  Both must be
+ * device memory; the frame's offsets are checked on the device at every
+ * replay (a malformed frame is reported by tpcfit_batch_sync). */
+int tpcfit_batch_create(tpcfit_handle *h, const tpcfit_frame *frame, tpcfit_result *res, tpcfit_batch **out);
+
+/* Replay the captured graph on `stream` (a cudaStream_t as void*, NULL = the
+ * batch's own stream); returns without waiting. */
+int tpcfit_batch_launch(tpcfit_batch *b, void *stream);
+
+/* Wait for the batch's replays (bounded by timeout_s; < 0 = no bound) and
+ * report a malformed frame seen by the last replay. */
+int tpcfit_batch_sync(tpcfit_batch *b, double timeout_s);
+
+/* Release the graph and the batch's scratch (waits for replays first). */
+int tpcfit_batch_destroy(tpcfit_batch *b);
 
 /* Serving (Sec. 4 horizontal parallelism, Sec. 7 rate limiting by frames in
  * flight): copy a host frame into a library-owned resident slot when the HBM

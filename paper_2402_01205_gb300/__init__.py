@@ -23,7 +23,8 @@ from . import _build
 
 __all__ = ["TpcfitError", "Config", "default_config", "create", "destroy", "fit", "fit_async", "sync", "submit",
            "poll", "wait", "last_timing", "reset_timing", "probe_fma_rates", "strerror", "now", "Fitter",
-           "library_path", "alloc_result", "STATUS_NAMES"]
+           "library_path", "alloc_result", "STATUS_NAMES", "Batch", "EventViews", "batch_create", "batch_launch",
+           "batch_sync", "batch_destroy", "fit_noalloc"]
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_NOTFOUND, E_NODEV = 0, -1, -2, -3, -4, -5, -6, -7
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -107,9 +108,14 @@ def _load():
     lib.tpcfit_last_error_message.restype = ctypes.c_char_p
     lib.tpcfit_now.argtypes = []
     lib.tpcfit_now.restype = ctypes.c_double
+    lib.tpcfit_batch_create.argtypes = [H, ctypes.POINTER(_Frame), ctypes.POINTER(_Result), ctypes.POINTER(H)]
+    lib.tpcfit_batch_launch.argtypes = [H, ctypes.c_void_p]
+    lib.tpcfit_batch_sync.argtypes = [H, ctypes.c_double]
+    lib.tpcfit_batch_destroy.argtypes = [H]
     for fn in ("tpcfit_create", "tpcfit_fit", "tpcfit_fit_async", "tpcfit_sync", "tpcfit_submit", "tpcfit_poll",
                "tpcfit_wait", "tpcfit_last_timing", "tpcfit_reset_timing", "tpcfit_destroy",
-               "tpcfit_probe_fma_rates"):
+               "tpcfit_probe_fma_rates", "tpcfit_batch_create", "tpcfit_batch_launch", "tpcfit_batch_sync",
+               "tpcfit_batch_destroy"):
         getattr(lib, fn).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -311,6 +317,110 @@ def fit_noalloc(frame, res: dict, config: Optional[Config] = None, stream=None) 
     if rc < 0:
         raise TpcfitError(rc, strerror(rc))
     return res
+
+
+def batch_create(handle: int, frame, res: dict) -> int:
+    f, _, _, _ = _frame_struct(frame)
+    r, _ = _result_struct(res)
+    b = ctypes.c_void_p()
+    _check(_load().tpcfit_batch_create(handle, ctypes.byref(f), ctypes.byref(r), ctypes.byref(b)))
+    return b.value
+
+
+def batch_launch(batch: int, stream=None) -> None:
+    _check(_load().tpcfit_batch_launch(batch, getattr(stream, "cuda_stream", stream)))
+
+
+def batch_sync(batch: int, timeout_s: float = -1.0) -> None:
+    _check(_load().tpcfit_batch_sync(batch, timeout_s))
+
+
+def batch_destroy(batch: int) -> None:
+    _check(_load().tpcfit_batch_destroy(batch))
+
+
+class EventViews:
+    """Per-event frames and results inside one concatenated device frame.
+
+    For fitting the events of a batch one plain launch sequence per event:
+    event e's frame points into the concatenated cluster arrays and result
+    buffers, with its own offsets rebased to 0 (kept in one device tensor)."""
+
+    def __init__(self, frame, res: dict, event_offsets):
+        import torch
+        ev = np.asarray(event_offsets, dtype=np.int64)
+        off = frame.offsets.cpu().numpy() if _is_torch(frame.offsets) else np.asarray(frame.offsets)
+        ne = len(ev) - 1
+        reb = np.empty(int(ev[-1]) + ne, dtype=np.int64)
+        for e in range(ne):
+            t0, t1 = int(ev[e]), int(ev[e + 1])
+            reb[t0 + e:t1 + e + 1] = off[t0:t1 + 1] - off[t0]
+        self.rebased = torch.from_numpy(reb).to(frame.x.device)
+        self.frame, self.res = frame, res
+        fs, _, _, _ = _frame_struct(frame)
+        rs, _ = _result_struct(res)
+        if fs.mem != MEM_DEVICE or rs.mem != MEM_DEVICE:
+            raise ValueError("EventViews takes a device frame and device results")
+        self.frames, self.results = [], []
+        rb = self.rebased.data_ptr()
+        for e in range(ne):
+            t0, t1 = int(ev[e]), int(ev[e + 1])
+            c0, c1 = int(off[t0]), int(off[t1])
+            self.frames.append(_Frame(t1 - t0, c1 - c0, rb + 8 * (t0 + e), fs.x + 4 * c0, fs.y + 4 * c0,
+                                      fs.z + 4 * c0, fs.sy2 + 4 * c0, fs.sz2 + 4 * c0, fs.row + c0, 0, MEM_DEVICE))
+            self.results.append(_Result(rs.state + 20 * t0, rs.cov + 60 * t0, rs.x_ref + 4 * t0, rs.chi2 + 8 * t0,
+                                        rs.ndf + 4 * t0, rs.status + 4 * t0, rs.accept + c0, MEM_DEVICE, 0, 0, 0))
+
+    def __len__(self) -> int:
+        return len(self.frames)
+
+    def fit_async(self, fitter: "Fitter", stream=None) -> None:
+        """One plain launch sequence per event, enqueued in event order on `stream`."""
+        lib = _load()
+        s = getattr(stream, "cuda_stream", stream)
+        fn, h = lib.tpcfit_fit_async, fitter.handle
+        for f, r in zip(self.frames, self.results):
+            rc = fn(h, ctypes.byref(f), ctypes.byref(r), s)
+            if rc < 0:
+                _check(rc)
+
+
+class Batch:
+    """A captured launch sequence over one device frame of concatenated events.
+
+    Keeps the frame and result tensors alive for as long as the graph may
+    replay (the graph holds their device addresses)."""
+
+    def __init__(self, fitter: "Fitter", frame, res: Optional[dict] = None):
+        f, mem, nt, nc = _frame_struct(frame)
+        if res is None:
+            res = alloc_result(nt, nc, device=frame.x.device)
+        self.frame, self.res, self._fitter = frame, res, fitter
+        self.batch = batch_create(fitter.handle, frame, res)
+
+    def launch(self, stream=None) -> dict:
+        batch_launch(self.batch, stream)
+        return self.res
+
+    def sync(self, timeout_s: float = -1.0) -> None:
+        batch_sync(self.batch, timeout_s)
+
+    def close(self) -> None:
+        if self.batch:
+            batch_destroy(self.batch)
+            self.batch = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Fitter:

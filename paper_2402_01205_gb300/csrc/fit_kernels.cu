@@ -28,6 +28,8 @@
 // chi2 near the gate keeps FP64-level agreement with an FP64 fit.
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <math.h>
 #include <stdint.h>
 
@@ -37,16 +39,15 @@ namespace tpcfit {
 
 enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5 };
 
-constexpr int kFitBlock = 256;
-constexpr int kWarpsPerBlock = kFitBlock / 32;
+
 constexpr int kBitWords = kMaxRows / 32;  // outward accept bits of one track (<= 256 clusters)
 constexpr int kChunk = 4;                 // clusters per staged chunk (per lane)
 constexpr int kStageArrays = 5;           // x, y, z, sy2, sz2
 // dynamic shared memory of k_fit: row table, outward accept bits, staged clusters
 constexpr size_t kSmemRowx = kMaxRows * sizeof(float);
-constexpr size_t kSmemBits = (size_t)kWarpsPerBlock * kBitWords * 32 * sizeof(uint32_t);
-constexpr size_t kSmemStage = (size_t)2 * kStageArrays * kChunk * kFitBlock * sizeof(float);
-constexpr size_t kFitSmem = kSmemRowx + kSmemBits + kSmemStage;
+template <int BLOCK> __host__ __device__ constexpr size_t smem_bits() { return (size_t)(BLOCK / 32) * kBitWords * 32 * sizeof(uint32_t); }
+template <int BLOCK> __host__ __device__ constexpr size_t smem_stage() { return (size_t)2 * kStageArrays * kChunk * BLOCK * sizeof(float); }
+template <int BLOCK> __host__ __device__ constexpr size_t fit_smem() { return kSmemRowx + smem_bits<BLOCK>() + smem_stage<BLOCK>(); }
 
 // 4-byte asynchronous global->shared copy (zero-fill when !valid; the source
 // address is then still a valid element and is not read).
@@ -468,6 +469,7 @@ struct Clu {
 // Issue the copies of chunk c (clusters a+4c .. a+4c+3, clipped to the track)
 // into buffer c&1 of this lane's staging column; returns the chunk's rows
 // packed in one word (loaded now, used when the chunk becomes current).
+template <int BLOCK>
 __device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, float *stg) {
   const int buf = c & 1;
   uint32_t rows = 0;
@@ -476,12 +478,12 @@ __device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int
     const int64_t k = a + (int64_t)kChunk * c + s;
     const bool v = k < e;
     const int64_t kk = v ? k : e - 1;
-    float *dst = stg + ((buf * kStageArrays) * kChunk + s) * kFitBlock;
-    cp_async4(dst + 0 * kChunk * kFitBlock, A.x + kk, v);
-    cp_async4(dst + 1 * kChunk * kFitBlock, A.y + kk, v);
-    cp_async4(dst + 2 * kChunk * kFitBlock, A.z + kk, v);
-    cp_async4(dst + 3 * kChunk * kFitBlock, A.sy2 + kk, v);
-    cp_async4(dst + 4 * kChunk * kFitBlock, A.sz2 + kk, v);
+    float *dst = stg + ((buf * kStageArrays) * kChunk + s) * BLOCK;
+    cp_async4(dst + 0 * kChunk * BLOCK, A.x + kk, v);
+    cp_async4(dst + 1 * kChunk * BLOCK, A.y + kk, v);
+    cp_async4(dst + 2 * kChunk * BLOCK, A.z + kk, v);
+    cp_async4(dst + 3 * kChunk * BLOCK, A.sy2 + kk, v);
+    cp_async4(dst + 4 * kChunk * BLOCK, A.sz2 + kk, v);
     rows |= (v ? (uint32_t)A.row[kk] : 0u) << (8 * s);
   }
   cp_async_commit();
@@ -489,19 +491,21 @@ __device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int
 }
 
 // Cluster lk of the track from the staged chunk lk/4 (which must be current).
+template <int BLOCK>
 __device__ __forceinline__ Clu read_staged(const float *stg, int lk, uint32_t rows_cur) {
   const int ch = lk / kChunk, slot = lk % kChunk;
-  const float *src = stg + (((ch & 1) * kStageArrays) * kChunk + slot) * kFitBlock;
+  const float *src = stg + (((ch & 1) * kStageArrays) * kChunk + slot) * BLOCK;
   Clu c;
   c.x = src[0];
-  c.y = src[kChunk * kFitBlock];
-  c.z = src[2 * kChunk * kFitBlock];
-  c.vy = src[3 * kChunk * kFitBlock];
-  c.vz = src[4 * kChunk * kFitBlock];
+  c.y = src[kChunk * BLOCK];
+  c.z = src[2 * kChunk * BLOCK];
+  c.vy = src[3 * kChunk * BLOCK];
+  c.vz = src[4 * kChunk * BLOCK];
   c.r = (rows_cur >> (8 * slot)) & 0xffu;
   return c;
 }
 
+template <int BLOCK>
 __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
   const int st0 = A.status[t];
@@ -550,10 +554,10 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       // the following chunk is in flight (cp.async) while this one is used
       const int nch = (n + kChunk - 1) / kChunk;
       int kc = 0;
-      uint32_t rows_cur = stage_chunk(A, a, e, 0, stg), rows_next = 0;
+      uint32_t rows_cur = stage_chunk<BLOCK>(A, a, e, 0, stg), rows_next = 0;
       cp_async_wait_all();
-      if (nch > 1) rows_next = stage_chunk(A, a, e, 1, stg);
-      Clu cand = read_staged(stg, 0, rows_cur);
+      if (nch > 1) rows_next = stage_chunk<BLOCK>(A, a, e, 1, stg);
+      Clu cand = read_staged<BLOCK>(stg, 0, rows_cur);
       int rprev = -1;
       st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
       // ---------------- outward pass: rows row[0] .. row[n-1] ----------------
@@ -576,9 +580,9 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             if (kc % kChunk == 0) {  // entering chunk kc/4
               cp_async_wait_all();
               rows_cur = rows_next;
-              if (kc / kChunk + 1 < nch) rows_next = stage_chunk(A, a, e, kc / kChunk + 1, stg);
+              if (kc / kChunk + 1 < nch) rows_next = stage_chunk<BLOCK>(A, a, e, kc / kChunk + 1, stg);
             }
-            cand = read_staged(stg, kc, rows_cur);
+            cand = read_staged<BLOCK>(stg, kc, rows_cur);
             const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
             if (vs != ST_OK) { st = vs; break; }
           }
@@ -641,7 +645,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         // ---------------- inward pass: rows row[n-1] .. row[0] ----------------
         kc = n - 1;
         // the last chunk is current; restage the one below it into the other buffer
-        if (nch > 1) rows_next = stage_chunk(A, a, e, nch - 2, stg);
+        if (nch > 1) rows_next = stage_chunk<BLOCK>(A, a, e, nch - 2, stg);
         for (int r = cand.r;; --r) {
           const bool has = (cand.r == r);
           const float xt = has ? cand.x : s_rowx[r];
@@ -662,9 +666,9 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
               if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above
                 cp_async_wait_all();
                 rows_cur = rows_next;
-                if (kc / kChunk > 0) rows_next = stage_chunk(A, a, e, kc / kChunk - 1, stg);
+                if (kc / kChunk > 0) rows_next = stage_chunk<BLOCK>(A, a, e, kc / kChunk - 1, stg);
               }
-              cand = read_staged(stg, kc, rows_cur);
+              cand = read_staged<BLOCK>(stg, kc, rows_cur);
             }
           }
           if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
@@ -706,11 +710,12 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   A.status[t] = st;
 }
 
-__global__ void __launch_bounds__(kFitBlock, 3) k_fit(FitArgs A) {
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   float *s_rowx = reinterpret_cast<float *>(smem);
   uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + kSmemRowx);
-  float *s_stage = reinterpret_cast<float *>(smem + kSmemRowx + kSmemBits);
+  float *s_stage = reinterpret_cast<float *>(smem + kSmemRowx + smem_bits<BLOCK>());
   for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) s_rowx[i] = A.row_x[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -724,7 +729,7 @@ __global__ void __launch_bounds__(kFitBlock, 3) k_fit(FitArgs A) {
     const int64_t i = (int64_t)base + lane;
     if (i < A.n_tracks) {
       const int64_t t = A.perm ? (int64_t)A.perm[i] : i;
-      fit_track(A, t, bits, s_rowx, stg);
+      fit_track<BLOCK>(A, t, bits, s_rowx, stg);
     }
     __syncwarp();
   }
@@ -749,30 +754,50 @@ cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches) {
   return cudaGetLastError();
 }
 
+// Raise the dynamic shared memory limit of one k_fit instantiation, once per
+// device (the attribute belongs to the function in the current device's context).
+template <int BLOCK, int MINB> static cudaError_t set_fit_smem() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_fit<BLOCK, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem<BLOCK>());
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {
   if (a.n_tracks <= 0) return cudaSuccess;
-  (void)block;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFitSmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  cudaError_t e;
+  if (block == 128) {
+    if ((e = set_fit_smem<128, 6>()) != cudaSuccess) return e;
+    k_fit<128, 6><<<grid, 128, fit_smem<128>(), stream>>>(a);
+  } else {
+    if ((e = set_fit_smem<256, 3>()) != cudaSuccess) return e;
+    k_fit<256, 3><<<grid, 256, fit_smem<256>(), stream>>>(a);
   }
-  k_fit<<<grid, kFitBlock, kFitSmem, stream>>>(a);
   return cudaGetLastError();
 }
 
 int fit_blocks_per_sm(int block) {
-  (void)block;
   int n = 0;
-  cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFitSmem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit, kFitBlock, kFitSmem) != cudaSuccess) return 1;
+  cudaError_t e;
+  if (block == 128) {
+    set_fit_smem<128, 6>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<128, 6>, 128, fit_smem<128>());
+  } else {
+    set_fit_smem<256, 3>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<256, 3>, 256, fit_smem<256>());
+  }
+  if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 
 int fit_regs_per_thread() {
   cudaFuncAttributes at;
-  if (cudaFuncGetAttributes(&at, k_fit) != cudaSuccess) return -1;
+  if (cudaFuncGetAttributes(&at, k_fit<256, 3>) != cudaSuccess) return -1;
   return at.numRegs;
 }
 

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -258,7 +259,8 @@ static int check_config(const tpcfit_config &c) {
   if (c.n_rows < 1 || c.n_rows > kMaxRows) return fail(TPCFIT_E_INVAL, "n_rows must be in [1, %d]", kMaxRows);
   if (c.min_clusters < 0) return fail(TPCFIT_E_INVAL, "min_clusters < 0");
   if (c.max_slots < 1 || c.max_slots > 64) return fail(TPCFIT_E_INVAL, "max_slots must be in [1, 64]");
-  if (c.block_threads != 0 && c.block_threads != 256) return fail(TPCFIT_E_INVAL, "block_threads must be 0 or 256");
+  if (c.block_threads != 0 && c.block_threads != 128 && c.block_threads != 256)
+    return fail(TPCFIT_E_INVAL, "block_threads must be 0, 128 or 256");
   if (c.blocks_per_sm < 0) return fail(TPCFIT_E_INVAL, "blocks_per_sm < 0");
   return TPCFIT_OK;
 }
@@ -312,9 +314,9 @@ extern "C" int tpcfit_create(const tpcfit_config *cfg_in, tpcfit_handle **out) {
   if (cudaMalloc(&h->d_rowx, sizeof(rowx)) != cudaSuccess ||
       cudaMemcpy(h->d_rowx, rowx, sizeof(rowx), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(fail(TPCFIT_E_NOMEM, "row table allocation failed"));
-  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_blocks_per_sm(256);
+  h->fit_block = cfg.block_threads ? cfg.block_threads : 256;
+  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_blocks_per_sm(h->fit_block);
   h->fit_grid = h->sms * bps;
-  h->fit_block = 256;
   h->fit_regs = fit_regs_per_thread();
   h->chunk_clusters = cfg.host_chunk_clusters > 0 ? cfg.host_chunk_clusters : (int64_t)16 << 20;
   *out = h;
@@ -500,6 +502,116 @@ static int fit_device(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r,
   if (rc) return rc;
   CU(cudaMemcpyAsync(h->h_err, h->scratch.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   h->last_launches = launches;
+  return TPCFIT_OK;
+}
+
+// ----------------------------------------------------------------------------
+// batched events: one captured launch sequence, replayed
+// ----------------------------------------------------------------------------
+struct tpcfit_batch {
+  tpcfit_handle *h = nullptr;
+  int device = 0;
+  Scratch scratch;
+  cudaStream_t stream = nullptr;  // capture stream and default replay stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after the latest replay
+  int32_t *h_err = nullptr;    // pinned; the latest replay's frame-error word
+  int launches = 0;            // kernels per replay
+};
+
+static void batch_free(tpcfit_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  b->scratch.buf.release();
+  delete b;
+}
+
+extern "C" int tpcfit_batch_create(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, tpcfit_batch **out) {
+  if (!h || !out) return fail(TPCFIT_E_INVAL, "handle or out is NULL");
+  int rc = check_frame_shape(f, r);
+  if (rc) return rc;
+  if (f->mem != TPCFIT_MEM_DEVICE || r->mem != TPCFIT_MEM_DEVICE)
+    return fail(TPCFIT_E_INVAL, "a batch takes a device frame and device results");
+  CU(cudaSetDevice(h->device));
+  tpcfit_batch *b = new tpcfit_batch();
+  b->h = h;
+  b->device = h->device;
+  auto bail = [&](int code) {
+    if (b->stream) {
+      cudaStreamCaptureStatus cs;
+      if (cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(b->stream, &g);
+        if (g) cudaGraphDestroy(g);
+      }
+    }
+    cudaGetLastError();
+    batch_free(b);
+    return code;
+  };
+  if ((rc = b->scratch.ensure(std::max<int64_t>(f->n_tracks, 1)))) return bail(rc);
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&b->h_err, sizeof(int32_t)) != cudaSuccess)
+    return bail(fail(TPCFIT_E_CUDA, "batch stream, event or pinned word"));
+  *b->h_err = 0;
+  // set the kernel attributes before capture (no such calls inside it)
+  fit_blocks_per_sm(h->fit_block);
+  FitArgs a = make_args(h, f, r, b->scratch, 0);
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bail(fail(TPCFIT_E_CUDA, "begin capture: %s", cudaGetErrorString(e)));
+  int l = 0;
+  if ((e = cudaMemsetAsync(b->scratch.hist, 0, b->scratch.small_bytes, b->stream)) != cudaSuccess ||
+      (e = launch_prepare(a, b->stream)) != cudaSuccess || (e = launch_sort(a, b->stream, &l)) != cudaSuccess ||
+      (e = launch_fit(a, h->fit_grid, h->fit_block, b->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->h_err, b->scratch.err, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream)) !=
+          cudaSuccess)
+    return bail(fail(TPCFIT_E_CUDA, "capture: %s", cudaGetErrorString(e)));
+  if (f->n_tracks > 0) l += 2;  // prepare and fit
+  if ((e = cudaStreamEndCapture(b->stream, &b->graph)) != cudaSuccess)
+    return bail(fail(TPCFIT_E_CUDA, "end capture: %s", cudaGetErrorString(e)));
+  if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
+    return bail(fail(TPCFIT_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e)));
+  b->launches = l;
+  *out = b;
+  return TPCFIT_OK;
+}
+
+extern "C" int tpcfit_batch_launch(tpcfit_batch *b, void *stream) {
+  if (!b) return fail(TPCFIT_E_INVAL, "batch is NULL");
+  CU(cudaSetDevice(b->device));
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : b->stream;
+  CU(cudaGraphLaunch(b->exec, st));
+  CU(cudaEventRecord(b->done, st));
+  return TPCFIT_OK;
+}
+
+extern "C" int tpcfit_batch_sync(tpcfit_batch *b, double timeout_s) {
+  if (!b) return fail(TPCFIT_E_INVAL, "batch is NULL");
+  CU(cudaSetDevice(b->device));
+  const double t0 = tpcfit_now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return fail(TPCFIT_E_CUDA, "batch: %s", cudaGetErrorString(e));
+    if (timeout_s >= 0 && tpcfit_now() - t0 > timeout_s)
+      return fail(TPCFIT_E_TIMEOUT, "batch wait exceeded %.3f s", timeout_s);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  if (*b->h_err) return fail(TPCFIT_E_INVAL, "malformed track offsets in the batch frame");
+  return TPCFIT_OK;
+}
+
+extern "C" int tpcfit_batch_destroy(tpcfit_batch *b) {
+  if (!b) return fail(TPCFIT_E_INVAL, "batch is NULL");
+  cudaSetDevice(b->device);
+  cudaEventSynchronize(b->done);
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
   return TPCFIT_OK;
 }
 

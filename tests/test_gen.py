@@ -68,3 +68,18 @@ def test_lognormal_and_poisson():
     t = tpcgen.poisson_arrivals(20000, 50.0, seed=0)
     assert np.all(np.diff(t) > 0)
     assert abs(np.mean(np.diff(t)) - 0.02) < 0.001
+
+
+def test_event_batch_shapes_and_independence():
+    f, ev = tpcgen.event_batch(n_events=64, median=40, sigma_ln=1.0, lo=10, hi=400, seed=2)
+    sizes = np.diff(ev)
+    assert ev[0] == 0 and ev[-1] == f.n_tracks and sizes.min() >= 10 and sizes.max() <= 400
+    assert 15 < np.median(sizes) < 110
+    # an event equals the same tracks generated on their own (tracks keyed by index)
+    e = 7
+    t0, t1 = int(ev[e]), int(ev[e + 1])
+    alone = tpcgen.generate("detector50k", seed=2, n_tracks=t1 - t0, track_id_offset=t0)
+    sub = f.subset(t0, t1)
+    assert np.array_equal(alone.offsets, sub.offsets)
+    for k in ("x", "y", "z", "row"):
+        assert np.array_equal(getattr(alone, k), getattr(sub, k)), k

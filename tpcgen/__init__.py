@@ -184,6 +184,25 @@ def lognormal_sizes(n: int, median: float, sigma_ln: float, lo: float, hi: float
     return out
 
 
+def event_batch(n_events: int = 4096, median: float = 800.0, sigma_ln: float = 1.0, lo: float = 10.0,
+                hi: float = 20000.0, seed: int = 0, preset: str = "detector50k", threads: Optional[int] = None,
+                **overrides) -> tuple:
+    """Many independent events of uneven multiplicity in one frame.
+
+    Tracks per event are log-normal (median, log width, redrawn outside
+    [lo, hi]); the events' tracks are concatenated, event e holding tracks
+    [event_offsets[e], event_offsets[e+1]).  Tracks are generated
+    independently (keyed by seed and track index), so concatenating events
+    and generating one frame of the total size give the same tracks.
+    Returns (Frame, event_offsets int64[n_events+1])."""
+    sizes = lognormal_sizes(n_events, median, sigma_ln, lo, hi, seed=seed + 1000003)
+    ev = np.zeros(n_events + 1, dtype=np.int64)
+    np.cumsum(sizes, out=ev[1:])
+    f = generate(preset, seed=seed, threads=threads, n_tracks=int(ev[-1]), **overrides)
+    f.params["event_sizes"] = dict(n_events=n_events, median=median, sigma_ln=sigma_ln, lo=lo, hi=hi)
+    return f, ev
+
+
 def poisson_arrivals(n: int, rate_hz: float, seed: int = 0) -> np.ndarray:
     """Arrival times (s) of a Poisson process with the given rate."""
     out = np.empty(n, dtype=np.float64)
