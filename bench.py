@@ -42,7 +42,11 @@ WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT
              "events4096": "4,096 independent events, tracks per event log-normal (median 800, sigma_ln 1.0, "
                            "10-20,000), tracks of 10-152 rows, pT log-uniform 0.2-10 GeV/c, 36 sectors, x/X0 5e-4 "
                            "per row, 5% dropout, 1% outliers, seed 0; one graph-captured persistent launch sequence "
-                           "per step vs one plain launch sequence per event"}
+                           "per step vs one plain launch sequence per event",
+             "serving": "time frames arriving as a Poisson process at 50 frames/s, clusters per frame log-normal "
+                        "(median 20 M, sigma_ln 0.6, 1-120 M), tracks as in the 36-sector detector workload; a pool "
+                        "of 64 frames (windows of one pre-generated 1.1 M-track frame) replayed on a seeded "
+                        "arrival schedule; 120 GB HBM budget, 8 slots"}
 FP64_PER_CLUSTER = 21         # FP64 pipe instructions per cluster: 10 (outward update) + 11 (inward update + sum)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
@@ -167,6 +171,8 @@ def run_reference(args, ws, rank):
         k = max(1, int(np.searchsorted(np.cumsum(sizes), n, side="right")))
         frame, _ = tpcgen.event_batch(n_events=k, seed=0)
         n = frame.n_tracks
+    elif args.workload == "serving":
+        frame = tpcgen.generate("detector50k", n_tracks=n, seed=0)  # the first tracks of the frame pool
     else:
         frame = tpcgen.generate(args.workload, n_tracks=n, seed=0)
     cores = os.cpu_count() or 1
@@ -371,6 +377,200 @@ def run_events(args, ws, rank, local, T, torch, dist, probe):
     return 0
 
 
+SERVE_MEDIAN, SERVE_SIGMA, SERVE_LO, SERVE_HI = 20e6, 0.6, 1e6, 120e6
+
+
+def serving_pool(rank: int, n_frames: int, pool_tracks: int = 1_100_000, seed: int = 0):
+    """One pre-generated frame and n_frames windows of it whose cluster counts
+    follow the serving size law.  Returns (frame, [(t0, t1), ...])."""
+    big = tpcgen.generate("detector50k", n_tracks=pool_tracks, seed=rank)
+    want = tpcgen.lognormal_sizes(n_frames, SERVE_MEDIAN, SERVE_SIGMA, SERVE_LO, SERVE_HI, seed=seed + 77)
+    rng = np.random.default_rng(seed + 78)
+    off = big.offsets
+    wins = []
+    for c in want:
+        c = min(int(c), int(off[-1]) - 1)
+        # last start whose window of c clusters still fits
+        last = int(np.searchsorted(off, off[-1] - c, side="right")) - 1
+        t0 = int(rng.integers(0, max(last, 0) + 1))
+        t1 = int(np.searchsorted(off, off[t0] + c, side="left"))
+        wins.append((t0, max(t1, t0 + 1)))
+    return big, wins
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def run_serving(args, ws, rank, local, T, torch, dist, probe):
+    """Served frames (tpcfit_submit/poll) vs sequential plain fits (tpcfit_fit)."""
+    big, wins = serving_pool(rank, args.serve_pool)
+    names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
+
+    class F:
+        pass
+
+    pinned = {}
+    for k in names[1:]:
+        a = getattr(big, k)
+        t = torch.empty(a.shape, dtype=torch.from_numpy(a[:1]).dtype, pin_memory=True)
+        t.copy_(torch.from_numpy(a))
+        pinned[k] = t
+    frames = []
+    for t0, t1 in wins:
+        c0, c1 = int(big.offsets[t0]), int(big.offsets[t1])
+        f = F()
+        o = torch.empty(t1 - t0 + 1, dtype=torch.int64, pin_memory=True)
+        o.copy_(torch.from_numpy(big.offsets[t0:t1 + 1] - c0))
+        f.offsets = o
+        for k in names[1:]:
+            setattr(f, k, pinned[k][c0:c1])
+        f.n_tracks, f.n_clusters = t1 - t0, c1 - c0
+        frames.append(f)
+    max_nt = max(f.n_tracks for f in frames)
+    max_nc = max(f.n_clusters for f in frames)
+    ring = [T.alloc_result(max_nt, max_nc, pinned=True) for _ in range(16)]
+
+    def res_for(slot, f):
+        return {k: (v[:f.n_clusters] if k == "accept" else v[:f.n_tracks]) for k, v in ring[slot].items()}
+
+    n_req = max(1, int(round(args.serve_seconds * args.serve_rate)))
+    arrivals = tpcgen.poisson_arrivals(n_req, args.serve_rate, seed=rank + 79)
+    pick = np.random.default_rng(rank + 80).integers(0, len(frames), size=n_req)
+    budget = 120 << 30
+
+    def served(arr):
+        lat, t_done = [None] * len(arr), [0.0] * len(arr)
+        with T.Fitter(device=local, hbm_budget_bytes=budget, max_slots=8) as fx:
+            fx.wait(fx.submit(frames[0], res_for(0, frames[0])))  # warm-up: pool, streams, kernels
+            out = {}
+            t0 = T.now() + 0.05
+            for i, a in enumerate(arr):
+                slot = i % len(ring)
+                if slot in out:
+                    tk, j = out.pop(slot)
+                    st, td = fx.wait(tk)
+                    assert st == T.DONE, st
+                    lat[j], t_done[j] = td - (t0 + arr[j]), td
+                d = t0 + a - T.now()
+                if d > 0:
+                    time.sleep(d)
+                f = frames[pick[i]]
+                out[slot] = (fx.submit(f, res_for(slot, f)), i)
+            for tk, j in out.values():
+                st, td = fx.wait(tk)
+                assert st == T.DONE, st
+                lat[j], t_done[j] = td - (t0 + arr[j]), td
+        return lat, max(t_done) - (t0 + arr[0])
+
+    def sequential(arr):
+        lat, t_end = [None] * len(arr), 0.0
+        with T.Fitter(device=local) as fx:
+            fx.fit(frames[0], res_for(0, frames[0]))
+            t0 = T.now() + 0.05
+            for i, a in enumerate(arr):
+                d = t0 + a - T.now()
+                if d > 0:
+                    time.sleep(d)
+                f = frames[pick[i]]
+                fx.fit(f, res_for(i % len(ring), f))
+                t_end = T.now()
+                lat[i] = t_end - (t0 + a)
+        return lat, t_end - (t0 + arr[0])
+
+    ncl = np.array([frames[k].n_clusters for k in pick], dtype=np.float64)
+    ntr = np.array([frames[k].n_tracks for k in pick], dtype=np.float64)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(gpu_index(local))
+    clocks.start()
+    lat_s, span_s = served(arrivals)
+    clk = clocks.stop()
+    lat_q, span_q = sequential(arrivals)
+    # capacity: every frame of the schedule due at once
+    n_cap = min(n_req, 4 * len(frames))
+    zero = np.zeros(n_cap)
+    lat_cs, span_cs = served(zero)
+    lat_cq, span_cq = sequential(zero)
+    cap_cl = float(ncl[:n_cap].sum())
+    # device-only fit time of each pool frame, resident in HBM
+    dev_ms, fit_ms, fit_cl, fit_tr = [], 0.0, 0, 0
+    with T.Fitter(device=local) as fx:
+        for f in frames:
+            g = F()
+            for k in names:
+                setattr(g, k, getattr(f, k).cuda())
+            r = T.alloc_result(f.n_tracks, f.n_clusters, device=torch.device("cuda", local))
+            fx.fit_async(g, r)
+            fx.sync()
+            tm = fx.timing()
+            dev_ms.append(tm["total_ms"])
+            ok = (r["status"] == 0).cpu().numpy()
+            lens = np.diff(f.offsets.numpy())
+            fit_ms += tm["fit_ms"]
+            fit_cl += int(lens[ok].sum())
+            fit_tr += f.n_tracks
+            del g, r
+    nc_pool = sum(f.n_clusters for f in frames)
+    achieved = FP64_PER_CLUSTER * fit_cl / (fit_ms * 1e-3)
+    peaks, peak_src = measured_peaks()
+    hbm_achieved = (BYTES_PER_CLUSTER * nc_pool + BYTES_PER_TRACK * fit_tr) / (fit_ms * 1e-3) / 1e9
+    roofline = {
+        "bound": "alu", "kernel": "k_fit", "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
+        "achieved": achieved / 1e12, "peak": probe["fp64_fma_per_s"] / 1e12,
+        "frac": achieved / probe["fp64_fma_per_s"],
+        "peak_source": "measured live: FP64 FMA chain probe in libtpcfit (tpcfit_probe_fma_rates)",
+        "traffic": None, "traffic_note": "no ncu capture of the serving workload",
+        "fit_ms_avg": fit_ms / len(frames), "fp64_inst_per_cluster": FP64_PER_CLUSTER,
+        "over": f"one device-resident fit of each of the {len(frames)} pool frames",
+        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
+                "peak_source": peak_src},
+    }
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(big)
+    sustained = float(ncl.sum()) / span_s
+    value = reduce_sum(dist, torch, sustained)
+
+    def summary(lat, span, cl, tr):
+        ms = [x * 1e3 for x in lat]
+        return {"p50_ms": percentile(ms, 50), "p99_ms": percentile(ms, 99), "max_ms": max(ms),
+                "mean_ms": float(np.mean(ms)), "clusters_per_s": cl / span, "tracks_per_s": tr / span,
+                "frames": len(lat), "span_s": span}
+
+    if rank == 0:
+        line = {
+            "metric": "sustained clusters/s and p50/p99 frame latency (arrival to results in caller memory) of "
+                      "served time frames on 1 GB300",
+            "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": n_req, "warmup": 1,
+            "ms_per_step": span_s / n_req * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serving", "description": WORKLOADS["serving"], "rate_hz": args.serve_rate,
+                       "seconds": args.serve_seconds, "frames_submitted": n_req, "pool_frames": len(frames),
+                       "clusters_per_frame_median": float(np.median(ncl)), "clusters_per_frame_max": float(ncl.max()),
+                       "hbm_budget_bytes": budget, "max_slots": 8, "result_ring": len(ring),
+                       "l2": "frames of 1-120 M clusters, copied in per request; no flush",
+                       "parallelism": f"replicas x{ws}"},
+            "latency": {"served": summary(lat_s, span_s, ncl.sum(), ntr.sum()),
+                        "sequential_plain_fit": summary(lat_q, span_q, ncl.sum(), ntr.sum())},
+            "capacity": {"frames": n_cap,
+                         "served": summary(lat_cs, span_cs, cap_cl, float(ntr[:n_cap].sum())),
+                         "sequential_plain_fit": summary(lat_cq, span_cq, cap_cl, float(ntr[:n_cap].sum()))},
+            "device_only_fit_ms": {"p50": percentile(dev_ms, 50), "p99": percentile(dev_ms, 99),
+                                   "note": "one pool frame resident in HBM, launch sequence time"},
+            "e2e": {"value": sustained, "unit": "clusters/s", "h2d_bytes_per_step": int(21 * ncl.mean() + 8 * ntr.mean()),
+                    "d2h_bytes_per_step": int(100 * ntr.mean() + ncl.mean()),
+                    "path": "tpcfit_submit / tpcfit_wait, pinned host frames and results"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "gpu_launches": 4 * n_req,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,6 +585,9 @@ def main():
     ap.add_argument("--n-events", type=int, default=4096, help="events4096: number of events (testing)")
     ap.add_argument("--per-event-steps", type=int, default=3, help="events4096: timed steps of the per-event arm")
     ap.add_argument("--tune-table", default=None, help="events4096: JSON tune table to read / extend")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: length of the arrival schedule")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="serving: frames/s")
+    ap.add_argument("--serve-pool", type=int, default=64, help="serving: distinct frames in the replayed pool")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -403,6 +606,8 @@ def main():
     probe = T.probe_fma_rates(local)
     if args.workload == "events4096":
         return run_events(args, ws, rank, local, T, torch, dist, probe)
+    if args.workload == "serving":
+        return run_serving(args, ws, rank, local, T, torch, dist, probe)
     kw = {} if args.n_tracks is None else {"n_tracks": args.n_tracks}
     frame = tpcgen.generate(args.workload, seed=rank, **kw)
     nt, nc = frame.n_tracks, frame.n_clusters
