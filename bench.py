@@ -47,7 +47,7 @@ WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT
                         "(median 20 M, sigma_ln 0.6, 1-120 M), tracks as in the 36-sector detector workload; a pool "
                         "of 64 frames (windows of one pre-generated 1.1 M-track frame) replayed on a seeded "
                         "arrival schedule; 120 GB HBM budget, 8 slots"}
-FP64_PER_CLUSTER = 21         # FP64 pipe instructions per cluster: 10 (outward update) + 11 (inward update + sum)
+FP64_PER_CLUSTER = 19         # FP64 pipe instructions per cluster: 8 (outward update) + 11 (inward update + sum)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
 

@@ -86,12 +86,17 @@ typedef struct tpcfit_config {
   int32_t max_slots;      /* serving: frames resident at once (8) */
   int32_t device;         /* CUDA device ordinal (0) */
   int32_t block_threads;  /* fit kernel block size: 128 or 256 (0 = 256) */
-  int32_t blocks_per_sm;  /* fit kernel resident blocks per SM, 0 = occupancy maximum */
+  int32_t blocks_per_sm;  /* fit kernel resident blocks per SM; 0 = tuned default (512 threads per SM) */
   int32_t sort_tracks;    /* 1: fit tracks longest-first (default); 0: in frame order */
   int32_t reserved[7];
   int64_t host_chunk_clusters; /* host frames are copied and fitted in chunks of about this many clusters (16M) */
 } tpcfit_config;
 
+/* One time frame in SoA layout: the clusters of track t are
+ * [track_offsets[t], track_offsets[t+1]), rows strictly ascending.  Device
+ * arrays must come from a CUDA allocator (cudaMalloc, a memory pool, a
+ * framework's caching allocator): the fit reads each track's row bytes as the
+ * aligned 32-bit words that hold them, which lie inside such allocations. */
 typedef struct tpcfit_frame {
   int64_t n_tracks, n_clusters;
   const int64_t *track_offsets; /* n_tracks+1 */

@@ -19,9 +19,10 @@
 // chi2 = r^T S^-1 r, the gate decision and the chi2 sum are FP64.  GB300
 // executes FP64 at ~1/64 of the FP32 rate and a warp-wide FP64 instruction
 // costs the same with one active lane as with 32, so the FP64 island is kept
-// to 11 instructions per update, every FP32->FP64 widening is done exactly
-// with integer operations, and warps are filled with tracks of equal length
-// so that the FP64 instructions of a step serve (almost) every lane.
+// to 8 instructions per outward update (det, quadratic form, gate) and 11 per
+// inward update (plus reciprocal, chi2 and its sum), every FP32->FP64 widening
+// is done with integer operations, and warps are filled with tracks of equal
+// length so that the FP64 instructions of a step serve (almost) every lane.
 //
 // Track positions are carried as FP32 offsets (dy, dz) from the last
 // cluster's coordinates: residuals are then formed from small numbers and the
@@ -46,12 +47,15 @@ constexpr int kStageArrays = 5;           // x, y, z, sy2, sz2
 // dynamic shared memory of k_fit: row table, outward accept bits, staged clusters
 constexpr size_t kSmemRowx = kMaxRows * sizeof(float);
 template <int BLOCK> __host__ __device__ constexpr size_t smem_bits() { return (size_t)(BLOCK / 32) * kBitWords * 32 * sizeof(uint32_t); }
-template <int BLOCK> __host__ __device__ constexpr size_t smem_stage() { return (size_t)2 * kStageArrays * kChunk * BLOCK * sizeof(float); }
+// staged floats [buf][array][slot][lane], then staged row words [buf][word][lane]
+constexpr int kStageFloats = 2 * kStageArrays * kChunk;  // per lane
+constexpr int kStageRowWords = 2 * 2;                     // per lane: two aligned words per buffer
+template <int BLOCK> __host__ __device__ constexpr size_t smem_stage() { return (size_t)(kStageFloats + kStageRowWords) * BLOCK * sizeof(float); }
 template <int BLOCK> __host__ __device__ constexpr size_t fit_smem() { return kSmemRowx + smem_bits<BLOCK>() + smem_stage<BLOCK>(); }
 
 // 4-byte asynchronous global->shared copy (zero-fill when !valid; the source
 // address is then still a valid element and is not read).
-__device__ __forceinline__ void cp_async4(float *smem, const float *gmem, bool valid) {
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0)
                : "memory");
@@ -59,66 +63,51 @@ __device__ __forceinline__ void cp_async4(float *smem, const float *gmem, bool v
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 // ---------------------------------------------------------------------------
-// Exact binary32 -> binary64 widening with integer operations (IEEE 754: the
-// exponent is re-biased by 1023-127 = 896, the 23-bit fraction moves to the
-// top of the 52-bit fraction).  Zero and subnormal inputs give a signed zero;
-// Inf/NaN keep their class.
+// binary32 -> binary64 widening with integer operations (IEEE 754: the
+// exponent is re-biased by 1023-127 = 896 and the 23-bit fraction moves to the
+// top of the 52-bit fraction).  The FP64 pipe's own conversion costs as much
+// as an FP64 multiply, so the island widens its inputs on the integer pipe.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t mag = u & 0x7fffffffu;
-  const uint64_t sign = (uint64_t)(u >> 31) << 63;
-  const uint64_t bias = (mag >= 0x7f800000u) ? (1792ull << 23) : (896ull << 23);
-  uint64_t d = (((uint64_t)mag + bias) << 29) | sign;
-  d = (mag < 0x00800000u) ? sign : d;
-  return __longlong_as_double((long long)d);
+__device__ __forceinline__ double join64(uint32_t hi, uint32_t lo) {
+  double d;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(d) : "r"(lo), "r"(hi));
+  return d;
 }
-
-// The decisions and conversions below work on the two 32-bit halves of a
-// binary64 value.  The halves are taken with an opaque move so that the
-// compiler keeps integer operations and does not turn the tests back into
-// FP64-pipe instructions (which cost as much as the arithmetic they guard).
+// The two halves of a binary64 value, taken with an opaque move so that the
+// compiler keeps integer operations and does not turn the tests below back
+// into FP64-pipe instructions (which cost as much as the arithmetic they guard).
 __device__ __forceinline__ void split64(double x, uint32_t &hi, uint32_t &lo) {
   asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
 }
-__device__ __forceinline__ bool is_nan64(uint32_t hi, uint32_t lo) {
-  const uint32_t ha = hi & 0x7fffffffu;
-  return ha > 0x7ff00000u || (ha == 0x7ff00000u && lo != 0u);
+// Halves of the widened value of a finite binary32 f: exact for normal f; a
+// zero or subnormal f gives a value of the same sign and magnitude in
+// [2^-127, 2^-126), i.e. zero to within 2^-126 absolute.
+__device__ __forceinline__ void widen_halves(float f, uint32_t &hi, uint32_t &lo) {
+  const uint32_t u = __float_as_uint(f);
+  hi = (((u >> 3) & 0x0fffffffu) + (896u << 20)) | (u & 0x80000000u);
+  lo = u << 29;
 }
-// x <= g for a positive, finite g given as (ghi, glo); IEEE semantics for x.
-__device__ __forceinline__ bool le64(double x, uint32_t ghi, uint32_t glo) {
+__device__ __forceinline__ double widen(float f) {
+  uint32_t hi, lo;
+  widen_halves(f, hi, lo);
+  return join64(hi, lo);
+}
+// Exact widening of a positive normal binary32 value.
+__device__ __forceinline__ double widen_pos(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return join64((u >> 3) + (896u << 20), u << 29);
+}
+// x <= 0 for a finite x (-0 included).
+__device__ __forceinline__ bool le0_finite64(double x) {
   uint32_t hi, lo;
   split64(x, hi, lo);
-  if (is_nan64(hi, lo)) return false;
-  if (hi >> 31) return true;  // negative (or -0)
-  return hi < ghi || (hi == ghi && lo <= glo);
+  return (int32_t)hi < 0 || (hi | lo) == 0u;
 }
-// x <= 0 (NaN: false).
-__device__ __forceinline__ bool le0_64(double x) {
+// x <= g for a finite x and a positive finite g given as (ghi, glo).
+__device__ __forceinline__ bool le_finite64(double x, uint32_t ghi, uint32_t glo) {
   uint32_t hi, lo;
   split64(x, hi, lo);
-  if (is_nan64(hi, lo)) return false;
-  return (hi >> 31) || ((hi | lo) == 0u);
-}
-
-// Non-negative binary64 -> binary32, round to nearest even, with integer
-// operations only: values below the binary32 normal range flush to zero,
-// values above it give +Inf, NaN stays NaN.  (The inputs are reciprocals of
-// positive determinants.)
-__device__ __forceinline__ float narrow_pos(double v) {
-  uint32_t hi, lo;
-  split64(v, hi, lo);
-  hi &= 0x7fffffffu;
-  const uint32_t ex = hi >> 20;
-  // exponent and top 23 fraction bits; the bias change wraps correctly mod 2^32
-  uint32_t m = (hi << 3) | (lo >> 29);
-  const uint32_t rest = lo & 0x1fffffffu;
-  m += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
-  uint32_t f = m - (896u << 23);
-  f = (ex > 1150u) ? 0x7f800000u : f;
-  f = (ex < 897u) ? 0u : f;
-  f = is_nan64(hi, lo) ? 0x7fc00000u : f;
-  return __uint_as_float(f);
+  return (int32_t)hi < (int32_t)ghi || (hi == ghi && lo <= glo);
 }
 
 // Error-free sum of two binary32 numbers (Knuth's TwoSum): a + b = s + e exactly.
@@ -126,6 +115,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
+}
+// Dekker's Fast2Sum: the same when |a| >= |b| (a variance plus a smaller
+// increment, or minus a smaller decrement).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  e = b - (s - a);
 }
 
 // ---------------------------------------------------------------------------
@@ -358,41 +353,57 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   const float lg = fmaf(0.038f, __logf(eps * ib2), 1.0f);
   const float th2 = (0.0136f * 0.0136f) * pinv2 * ib2 * eps * lg * lg;
   T.c[5] = fmaf(th2, cs2 * tt, T.c[5]);
-  two_sum(T.c[9], fmaf(th2, tt * tt, T.c9l), T.c[9], T.c9l);
-  two_sum(T.c[14], fmaf(th2, w * w * t * t, T.c14l), T.c[14], T.c14l);
+  fast_two_sum(T.c[9], fmaf(th2, tt * tt, T.c9l), T.c[9], T.c9l);
+  fast_two_sum(T.c[14], fmaf(th2, w * w * t * t, T.c14l), T.c[14], T.c14l);
   T.c[13] = fmaf(th2, tt * w * t, T.c[13]);
 }
 
 // Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: det,
-// reciprocal (Newton step from an FP32 seed), quadratic form, chi2 product,
-// gate; the chi2 sum is done by the caller.  Returns the status (OK / NOT_PD).
-__device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, uint32_t gate_hi,
-                                      uint32_t gate_lo, bool &acc, double &chi2) {
+// quadratic form r^T adj(S) r and, where the chi2 value is needed (inward pass,
+// diagnostics), the reciprocal of det (Newton step from an FP32 seed) and the
+// chi2 product; otherwise the gate is decided as r^T adj(S) r - chi2_max det <= 0
+// with one fused multiply-add.  The chi2 sum is done by the caller.  Non-finite
+// innovation matrices give chi2 = NaN and a rejected cluster, as in FP64.
+// Returns the status (OK / NOT_PD).
+__device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, double gate, uint32_t gate_hi,
+                                      uint32_t gate_lo, bool want_chi2, bool &acc, double &chi2) {
   float *c = T.c;
   const float r0 = (yc - T.ya) - T.dy;
   const float r1 = (zc - T.za) - T.dz;
   const float S00 = c[0] + vy, S10 = c[1], S11 = c[2] + vz;
+  const bool fin = fabsf(S00 + S11 + S10) < INFINITY;
+  const float det32 = fmaf(S00, S11, -(S10 * S10));
+  const float i32 = __fdividef(1.0f, det32);  // FP32 seed of 1/det, and the gain's 1/det
   // ---- FP64 island ----
-  const double s00 = widen(S00), s10 = widen(S10), s11 = widen(S11);
-  const double m2s10 = widen(-2.0f * S10);  // exact: scaling by -2
+  const double s00 = widen_pos(S00), s11 = widen_pos(S11);
+  uint32_t h10, l10;
+  widen_halves(S10, h10, l10);
+  const double s10 = join64(h10, l10);
+  const double m2s10 = join64((h10 ^ 0x80000000u) + (1u << 20), l10);  // -2 s10, exactly
   const double q0 = widen(r0), q1 = widen(r1);
   const double det = fma(s00, s11, -(s10 * s10));
-  const bool notpd = le0_64(det) || S00 <= 0.0f;
-  const float det32 = fmaf(S00, S11, -(S10 * S10));
-  const double y0 = widen(__fdividef(1.0f, det32));
-  const double ey = fma(-det, y0, 1.0);
-  const double inv = fma(y0, ey, y0);      // 1/det, one Newton step
-  double qf = fma(m2s10, q1, s11 * q0);    // s11 r0 - 2 s10 r1
+  double qf = fma(m2s10, q1, s11 * q0);  // s11 r0 - 2 s10 r1
   qf = q0 * qf;
-  qf = fma(s00 * q1, q1, qf);              // r^T adj(S) r
-  chi2 = qf * inv;
-  acc = le64(chi2, gate_hi, gate_lo);
+  qf = fma(s00 * q1, q1, qf);            // r^T adj(S) r
+  if (want_chi2) {
+    const double y0 = widen_pos(i32);
+    const double ey = fma(-det, y0, 1.0);
+    const double inv = fma(y0, ey, y0);  // 1/det, one Newton step
+    chi2 = qf * inv;
+    acc = le_finite64(chi2, gate_hi, gate_lo);
+  } else {
+    acc = le0_finite64(fma(-gate, det, qf));
+  }
+  const bool notpd = fin && (le0_finite64(det) || !(S00 > 0.0f) || !(S11 > 0.0f));
   // ---- back to FP32 ----
+  if (!fin) {
+    acc = false;
+    chi2 = __longlong_as_double(0x7ff8000000000000ll);
+  }
   if (notpd) {
     acc = false;
     return ST_NOT_PD;
   }
-  const float i32 = narrow_pos(inv);
   const float Si00 = S11 * i32, Si10 = -S10 * i32, Si11 = S00 * i32;
   if (acc) {
     float K0[5], K1[5];
@@ -430,10 +441,10 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
     }
     c[5] = fmaf(-K0[2], h0[2], fmaf(-K1[2], h1[2], c[5]));
     c[8] = fmaf(-K0[3], h0[2], fmaf(-K1[3], h1[2], c[8]));
-    two_sum(c[9], T.c9l - fmaf(K0[3], h0[3], K1[3] * h1[3]), c[9], T.c9l);
+    fast_two_sum(c[9], T.c9l - fmaf(K0[3], h0[3], K1[3] * h1[3]), c[9], T.c9l);
     c[12] = fmaf(-K0[4], h0[2], fmaf(-K1[4], h1[2], c[12]));
     c[13] = fmaf(-K0[4], h0[3], fmaf(-K1[4], h1[3], c[13]));
-    two_sum(c[14], T.c14l - fmaf(K0[4], h0[4], K1[4] * h1[4]), c[14], T.c14l);
+    fast_two_sum(c[14], T.c14l - fmaf(K0[4], h0[4], K1[4] * h1[4]), c[14], T.c14l);
   } else {
     T.dy = -r0;
     T.dz = -r1;
@@ -467,12 +478,13 @@ struct Clu {
 };
 
 // Issue the copies of chunk c (clusters a+4c .. a+4c+3, clipped to the track)
-// into buffer c&1 of this lane's staging column; returns the chunk's rows
-// packed in one word (loaded now, used when the chunk becomes current).
+// into buffer c&1 of this lane's staging column.  The chunk's four row bytes
+// are copied as the two aligned 32-bit words that hold them (the second only
+// when it holds a byte of the track; an aligned word that holds a byte of an
+// allocation lies inside it, allocations being at least 4-byte granular).
 template <int BLOCK>
-__device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, float *stg) {
+__device__ __forceinline__ void stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, float *stg) {
   const int buf = c & 1;
-  uint32_t rows = 0;
 #pragma unroll
   for (int s = 0; s < kChunk; ++s) {
     const int64_t k = a + (int64_t)kChunk * c + s;
@@ -484,10 +496,22 @@ __device__ __forceinline__ uint32_t stage_chunk(const FitArgs &A, int64_t a, int
     cp_async4(dst + 2 * kChunk * BLOCK, A.z + kk, v);
     cp_async4(dst + 3 * kChunk * BLOCK, A.sy2 + kk, v);
     cp_async4(dst + 4 * kChunk * BLOCK, A.sz2 + kk, v);
-    rows |= (v ? (uint32_t)A.row[kk] : 0u) << (8 * s);
   }
+  const uint8_t *p0 = A.row + a + (int64_t)kChunk * c;
+  const uint32_t *w0 = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(p0) & ~(uintptr_t)3);
+  const bool v1 = reinterpret_cast<const uint8_t *>(w0 + 1) < A.row + e;
+  float *rdst = stg + (kStageFloats + 2 * buf) * BLOCK;
+  cp_async4(rdst, w0, true);
+  cp_async4(rdst + BLOCK, v1 ? w0 + 1 : w0, v1);
   cp_async_commit();
-  return rows;
+}
+
+// Rows of the staged chunk c (current), one byte per cluster; `rsh` is the
+// byte offset of the track's first row byte within its aligned word.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t staged_rows(const float *stg, int c, uint32_t rsh) {
+  const float *src = stg + (kStageFloats + 2 * (c & 1)) * BLOCK;
+  return __funnelshift_r(__float_as_uint(src[0]), __float_as_uint(src[BLOCK]), 8u * rsh);
 }
 
 // Cluster lk of the track from the staged chunk lk/4 (which must be current).
@@ -554,9 +578,11 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       // the following chunk is in flight (cp.async) while this one is used
       const int nch = (n + kChunk - 1) / kChunk;
       int kc = 0;
-      uint32_t rows_cur = stage_chunk<BLOCK>(A, a, e, 0, stg), rows_next = 0;
+      const uint32_t rsh = (uint32_t)(reinterpret_cast<uintptr_t>(A.row + a) & 3u);
+      stage_chunk<BLOCK>(A, a, e, 0, stg);
       cp_async_wait_all();
-      if (nch > 1) rows_next = stage_chunk<BLOCK>(A, a, e, 1, stg);
+      uint32_t rows_cur = staged_rows<BLOCK>(stg, 0, rsh);
+      if (nch > 1) stage_chunk<BLOCK>(A, a, e, 1, stg);
       Clu cand = read_staged<BLOCK>(stg, 0, rows_cur);
       int rprev = -1;
       st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
@@ -569,7 +595,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         if (has) {
           bool acc;
           double chi2;
-          const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate_hi, gate_lo, acc, chi2);
+          const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo,
+                                 A.chi2_out_c != nullptr, acc, chi2);
           if (ust != ST_OK) { st = ust; break; }
           if (acc) bits[32 * (kc >> 5)] |= 1u << (kc & 31);
           if (A.chi2_out_c) A.chi2_out_c[a + kc] = chi2;
@@ -579,8 +606,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           if (++kc < n) {
             if (kc % kChunk == 0) {  // entering chunk kc/4
               cp_async_wait_all();
-              rows_cur = rows_next;
-              if (kc / kChunk + 1 < nch) rows_next = stage_chunk<BLOCK>(A, a, e, kc / kChunk + 1, stg);
+              rows_cur = staged_rows<BLOCK>(stg, kc / kChunk, rsh);
+              if (kc / kChunk + 1 < nch) stage_chunk<BLOCK>(A, a, e, kc / kChunk + 1, stg);
             }
             cand = read_staged<BLOCK>(stg, kc, rows_cur);
             const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
@@ -645,7 +672,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         // ---------------- inward pass: rows row[n-1] .. row[0] ----------------
         kc = n - 1;
         // the last chunk is current; restage the one below it into the other buffer
-        if (nch > 1) rows_next = stage_chunk<BLOCK>(A, a, e, nch - 2, stg);
+        if (nch > 1) stage_chunk<BLOCK>(A, a, e, nch - 2, stg);
         for (int r = cand.r;; --r) {
           const bool has = (cand.r == r);
           const float xt = has ? cand.x : s_rowx[r];
@@ -654,7 +681,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           if (has) {
             bool acc;
             double chi2;
-            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate_hi, gate_lo, acc, chi2);
+            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc,
+                                   chi2);
             if (ust != ST_OK) { st = ust; break; }
             if (A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;
             chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
@@ -665,8 +693,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             if (--kc >= 0) {
               if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above
                 cp_async_wait_all();
-                rows_cur = rows_next;
-                if (kc / kChunk > 0) rows_next = stage_chunk<BLOCK>(A, a, e, kc / kChunk - 1, stg);
+                rows_cur = staged_rows<BLOCK>(stg, kc / kChunk, rsh);
+                if (kc / kChunk > 0) stage_chunk<BLOCK>(A, a, e, kc / kChunk - 1, stg);
               }
               cand = read_staged<BLOCK>(stg, kc, rows_cur);
             }
@@ -793,6 +821,17 @@ int fit_blocks_per_sm(int block) {
   }
   if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
+}
+
+// Resident blocks per SM when the caller leaves the choice to the library: the
+// occupancy maximum keeps 768 tracks per SM in flight, whose clusters do not
+// stay in L2 between the outward and the inward pass (DRAM reads of 170 B per
+// cluster against 60 B with 512 tracks per SM, measured on GB300); 512 tracks
+// per SM is the fastest residency there.
+int fit_default_blocks_per_sm(int block) {
+  const int occ = fit_blocks_per_sm(block);
+  const int want = 512 / (block == 128 ? 128 : 256);
+  return occ < want ? occ : want;
 }
 
 int fit_regs_per_thread() {

@@ -46,6 +46,8 @@ cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches);
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream);
 // Occupancy-derived resident blocks per SM for the fit kernel at `block` threads.
 int fit_blocks_per_sm(int block);
+// tuned default residency (blocks per SM) for a block size
+int fit_default_blocks_per_sm(int block);
 int fit_regs_per_thread();
 
 }  // namespace tpcfit

@@ -146,7 +146,7 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   if (cfg.row_x0_cm == 85.0f && cfg.row_pitch_cm == (float)(162.0 / 151.0)) pitch = 162.0 / 151.0;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device);
-  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_blocks_per_sm(256);
+  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(256);
   cudaError_t e;
   if ((e = cudaMemsetAsync(sc, 0, kZeroBytes, st)) != cudaSuccess) goto cuda_fail;
   k_noalloc_rowx<<<1, kMaxRows, 0, st>>>(reinterpret_cast<float *>(sc + kRowxOff), (double)cfg.row_x0_cm, pitch);
