@@ -121,9 +121,11 @@ def kernel_source_hash() -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def profiled_traffic(n_clusters_fitted: int):
-    """DRAM bytes per fit-kernel launch from the committed ncu summary, scaled to
-    this launch by clusters; None when the kernel changed since the capture."""
+def profiled_traffic(n_clusters: int, launch: tuple = (0, 0)):
+    """DRAM bytes (read + write) per fit-kernel launch from the committed ncu
+    record: the captured launch itself when this launch is the same frame and
+    launch shape, else scaled by clusters (traffic grows with the clusters
+    processed); None when the kernel source changed since the capture."""
     p = os.path.join(ROOT, "profiles", "fit_kernel_traffic.json")
     if not os.path.exists(p):
         return None, None
@@ -131,7 +133,12 @@ def profiled_traffic(n_clusters_fitted: int):
         d = json.load(fh)
     if d.get("kernel_sha256_16") != kernel_source_hash():
         return None, "kernel changed since the ncu capture"
-    return d["dram_bytes_per_cluster"] * n_clusters_fitted, d.get("capture")
+    if tuple(launch) != tuple(d.get("launch", (0, 0))):
+        return None, "no ncu capture of this launch shape (L2 reuse, hence traffic, depends on it)"
+    if n_clusters == d["n_clusters"]:
+        return d["dram_bytes_per_launch"], "ncu capture of this launch: " + d["capture"]
+    return d["dram_bytes_per_launch"] * n_clusters / d["n_clusters"], (
+        f"scaled by clusters from the ncu capture of {d['workload']}: " + d["capture"])
 
 
 def cpu_baseline(frame, seconds_target: float = 15.0):
@@ -306,7 +313,7 @@ def run_events(args, ws, rank, local, T, torch, dist, probe):
     fp64_peak = probe["fp64_fma_per_s"]
     achieved = FP64_PER_CLUSTER * nc_fit / fit_s
     hbm_achieved = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
-    traffic, traffic_note = profiled_traffic(nc_fit)
+    traffic, traffic_note = profiled_traffic(nc, (tm["fit_grid"], tm["fit_block"]))
     roofline = {
         "bound": "alu", "kernel": "k_fit", "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
         "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "frac": achieved / fp64_peak,
@@ -582,6 +589,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-tracks", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-threads", type=int, default=0, help="pbpb2m: fit kernel block size (0 = library default)")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="pbpb2m: resident fit blocks per SM (0 = default)")
     ap.add_argument("--n-events", type=int, default=4096, help="events4096: number of events (testing)")
     ap.add_argument("--per-event-steps", type=int, default=3, help="events4096: timed steps of the per-event arm")
     ap.add_argument("--tune-table", default=None, help="events4096: JSON tune table to read / extend")
@@ -619,7 +628,7 @@ def main():
     dev = F()
     for k in names:
         setattr(dev, k, torch.from_numpy(np.ascontiguousarray(getattr(frame, k))).cuda())
-    fx = T.Fitter(device=local)
+    fx = T.Fitter(device=local, block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm)
     res = T.alloc_result(nt, nc, device=torch.device("cuda", local))
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
@@ -662,7 +671,7 @@ def main():
     peaks, peak_src = measured_peaks()
     fp64_peak = probe["fp64_fma_per_s"]
     achieved = FP64_PER_CLUSTER * nc_fit / fit_s
-    traffic, traffic_note = profiled_traffic(nc_fit)
+    traffic, traffic_note = profiled_traffic(nc, (tm["fit_grid"], tm["fit_block"]))
     hbm_achieved = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
     roofline = {
         "bound": "alu", "kernel": "k_fit",
