@@ -47,7 +47,7 @@ WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT
                         "(median 20 M, sigma_ln 0.6, 1-120 M), tracks as in the 36-sector detector workload; a pool "
                         "of 64 frames (windows of one pre-generated 1.1 M-track frame) replayed on a seeded "
                         "arrival schedule; 120 GB HBM budget, 8 slots"}
-FP64_PER_CLUSTER = 19         # FP64 pipe instructions per cluster: 8 (outward update) + 11 (inward update + sum)
+FP64_PER_CLUSTER = 11         # FP64 lane-instructions per cluster: 4 (outward update) + 7 (inward update + sum)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
 
@@ -121,24 +121,71 @@ def kernel_source_hash() -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def profiled_traffic(n_clusters: int, launch: tuple = (0, 0)):
-    """DRAM bytes (read + write) per fit-kernel launch from the committed ncu
-    record: the captured launch itself when this launch is the same frame and
-    launch shape, else scaled by clusters (traffic grows with the clusters
-    processed); None when the kernel source changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "fit_kernel_traffic.json")
+ISSUE_PER_SM_CLK = 4          # warp instructions issued per SM per clock (4 schedulers, one each)
+
+
+def profiled_counters(n_clusters: int, launch: tuple):
+    """ncu counters of one fit-kernel launch from the committed record
+    (profiles/fit_kernel_counters.json): DRAM bytes and warp instructions,
+    for this frame when it is the captured one, else scaled by clusters for a
+    frame of the same launch shape; None for another shape or when the kernel
+    source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "fit_kernel_counters.json")
     if not os.path.exists(p):
-        return None, None
+        return None, "no ncu record"
     with open(p) as fh:
         d = json.load(fh)
     if d.get("kernel_sha256_16") != kernel_source_hash():
         return None, "kernel changed since the ncu capture"
     if tuple(launch) != tuple(d.get("launch", (0, 0))):
         return None, "no ncu capture of this launch shape (L2 reuse, hence traffic, depends on it)"
-    if n_clusters == d["n_clusters"]:
-        return d["dram_bytes_per_launch"], "ncu capture of this launch: " + d["capture"]
-    return d["dram_bytes_per_launch"] * n_clusters / d["n_clusters"], (
-        f"scaled by clusters from the ncu capture of {d['workload']}: " + d["capture"])
+    f = n_clusters / d["n_clusters"]
+    note = ("ncu capture of this launch: " if n_clusters == d["n_clusters"] else
+            f"scaled by clusters from the ncu capture of {d['workload']}: ") + d["capture"]
+    out = {"dram_bytes": d["dram_bytes_per_launch"] * f, "warp_inst": d["warp_inst_per_launch"] * f,
+           "thread_inst": d["thread_inst_per_launch"] * f}
+    if "fp32_flop_per_cluster" in d:
+        out["fp32_flop_per_cluster"] = d["fp32_flop_per_cluster"]
+    return out, note
+
+
+def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz):
+    """Roofline of the fit kernel.  Primary: instruction issue (the unit that
+    binds), achieved = ncu warp instructions per launch / mean launch time,
+    peak = 4 per SM per clock at the sampled SM clock.  Beside it the
+    algorithmic roofs: FP64 lane-instructions (11 per cluster) against the
+    live FP64 FMA probe, FP32 flops against 2x the FP32 FMA probe, HBM bytes
+    (22 per cluster + 108 per track) against the measured copy bandwidth."""
+    peaks, peak_src = measured_peaks()
+    c, note = profiled_counters(nc, launch)
+    fp64 = FP64_PER_CLUSTER * nc_fit / fit_s
+    hbm = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
+    sub = {
+        "fp64": {"achieved_tinst_s": fp64 / 1e12, "peak_tinst_s": probe["fp64_fma_per_s"] / 1e12,
+                 "frac": fp64 / probe["fp64_fma_per_s"], "lane_inst_per_cluster": FP64_PER_CLUSTER,
+                 "peak_source": "measured live: FP64 FMA chain probe (tpcfit_probe_fma_rates)"},
+        "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks["hbm_gbs"], "frac": hbm * 1e9 / (peaks["hbm_gbs"] * 1e9),
+                "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
+    }
+    if c and "fp32_flop_per_cluster" in c:
+        f32 = c["fp32_flop_per_cluster"] * nc_fit / fit_s
+        sub["fp32"] = {"achieved_tflops": f32 / 1e12, "peak_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
+                       "frac": f32 / (2 * probe["fp32_fma_per_s"]), "flop_per_cluster": c["fp32_flop_per_cluster"],
+                       "peak_source": "2 x measured live FP32 FMA chain probe"}
+    issue_peak = ISSUE_PER_SM_CLK * sms * (sm_mhz or 2070.0) * 1e6
+    if c:
+        ach = c["warp_inst"] / fit_s
+        roof = {"bound": "alu", "kernel": "k_fit", "unit": "G warp-inst/s (instruction issue)",
+                "achieved": ach / 1e9, "peak": issue_peak / 1e9, "frac": ach / issue_peak,
+                "peak_source": f"{ISSUE_PER_SM_CLK} issue slots per SM per clock x {sms} SMs x sampled SM clock",
+                "traffic": c["dram_bytes"], "traffic_note": note,
+                "warp_inst_per_cluster": c["warp_inst"] / nc, "active_lanes_per_inst": c["thread_inst"] / c["warp_inst"]}
+    else:
+        roof = {"bound": "alu", "kernel": "k_fit", "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
+                "achieved": fp64 / 1e12, "peak": probe["fp64_fma_per_s"] / 1e12,
+                "frac": fp64 / probe["fp64_fma_per_s"], "traffic": None, "traffic_note": note}
+    roof.update({"fit_ms_avg": fit_s * 1e3, "algorithmic": sub})
+    return roof
 
 
 def cpu_baseline(frame, seconds_target: float = 15.0):
@@ -309,20 +356,8 @@ def run_events(args, ws, rank, local, T, torch, dist, probe):
     nc_fit = int(lens[ok].sum())
     seq_s = tm["total_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
     fit_s = tm["fit_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
-    peaks, peak_src = measured_peaks()
-    fp64_peak = probe["fp64_fma_per_s"]
-    achieved = FP64_PER_CLUSTER * nc_fit / fit_s
-    hbm_achieved = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
-    traffic, traffic_note = profiled_traffic(nc, (tm["fit_grid"], tm["fit_block"]))
-    roofline = {
-        "bound": "alu", "kernel": "k_fit", "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
-        "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "frac": achieved / fp64_peak,
-        "peak_source": "measured live: FP64 FMA chain probe in libtpcfit (tpcfit_probe_fma_rates)",
-        "traffic": traffic, "traffic_note": traffic_note, "fit_ms_avg": fit_s * 1e3,
-        "fp64_inst_per_cluster": FP64_PER_CLUSTER,
-        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
-                "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
-    }
+    roofline = fit_roofline(nc, nt, nc_fit, fit_s, (tm["fit_grid"], tm["fit_block"]), probe,
+                            props.multi_processor_count, clk.get("sm_mhz"))
     e2e = None
     if args.e2e_steps > 0:
         host = F()
@@ -519,20 +554,10 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe):
             fit_tr += f.n_tracks
             del g, r
     nc_pool = sum(f.n_clusters for f in frames)
-    achieved = FP64_PER_CLUSTER * fit_cl / (fit_ms * 1e-3)
-    peaks, peak_src = measured_peaks()
-    hbm_achieved = (BYTES_PER_CLUSTER * nc_pool + BYTES_PER_TRACK * fit_tr) / (fit_ms * 1e-3) / 1e9
-    roofline = {
-        "bound": "alu", "kernel": "k_fit", "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
-        "achieved": achieved / 1e12, "peak": probe["fp64_fma_per_s"] / 1e12,
-        "frac": achieved / probe["fp64_fma_per_s"],
-        "peak_source": "measured live: FP64 FMA chain probe in libtpcfit (tpcfit_probe_fma_rates)",
-        "traffic": None, "traffic_note": "no ncu capture of the serving workload",
-        "fit_ms_avg": fit_ms / len(frames), "fp64_inst_per_cluster": FP64_PER_CLUSTER,
-        "over": f"one device-resident fit of each of the {len(frames)} pool frames",
-        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
-                "peak_source": peak_src},
-    }
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline = fit_roofline(nc_pool, fit_tr, fit_cl, fit_ms * 1e-3, (tm["fit_grid"], tm["fit_block"]), probe, sms,
+                            clk.get("sm_mhz"))
+    roofline["over"] = f"one device-resident fit of each of the {len(frames)} pool frames"
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(big)
@@ -668,22 +693,9 @@ def main():
     lens = np.diff(frame.offsets)
     nc_fit = int(lens[ok].sum())
     fit_s = tm["fit_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
-    peaks, peak_src = measured_peaks()
-    fp64_peak = probe["fp64_fma_per_s"]
-    achieved = FP64_PER_CLUSTER * nc_fit / fit_s
-    traffic, traffic_note = profiled_traffic(nc, (tm["fit_grid"], tm["fit_block"]))
-    hbm_achieved = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
-    roofline = {
-        "bound": "alu", "kernel": "k_fit",
-        "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
-        "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "frac": achieved / fp64_peak,
-        "peak_source": "measured live: FP64 FMA chain probe in libtpcfit (tpcfit_probe_fma_rates)",
-        "traffic": traffic, "traffic_note": traffic_note,
-        "fit_ms_avg": fit_s * 1e3, "fp64_inst_per_cluster": FP64_PER_CLUSTER,
-        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_achieved / peaks["hbm_gbs"],
-                "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
-        "fp32_fma_peak_per_s": probe["fp32_fma_per_s"],
-    }
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline = fit_roofline(nc, nt, nc_fit, fit_s, (tm["fit_grid"], tm["fit_block"]), probe, sms, clk.get("sm_mhz"))
+    roofline["fp32_fma_peak_per_s"] = probe["fp32_fma_per_s"]
     # end to end through the C-ABI: pinned host frame in, pinned host results out
     e2e = None
     if args.e2e_steps > 0:

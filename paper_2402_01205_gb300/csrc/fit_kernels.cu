@@ -19,8 +19,9 @@
 // chi2 = r^T S^-1 r, the gate decision and the chi2 sum are FP64.  GB300
 // executes FP64 at ~1/64 of the FP32 rate and a warp-wide FP64 instruction
 // costs the same with one active lane as with 32, so the FP64 island is kept
-// to 8 instructions per outward update (det, quadratic form, gate) and 11 per
-// inward update (plus reciprocal, chi2 and its sum), every FP32->FP64 widening
+// to 4 instructions per outward update (det, gate) and 7 per inward update
+// (det, reciprocal, chi2, sum); the quadratic form of the residual is formed
+// in twice the binary32 precision on the FP32 pipe, every FP32->FP64 widening
 // is done with integer operations, and warps are filled with tracks of equal
 // length so that the FP64 instructions of a step serve (almost) every lane.
 //
@@ -110,17 +111,20 @@ __device__ __forceinline__ bool le_finite64(double x, uint32_t ghi, uint32_t glo
   return (int32_t)hi < (int32_t)ghi || (hi == ghi && lo <= glo);
 }
 
-// Error-free sum of two binary32 numbers (Knuth's TwoSum): a + b = s + e exactly.
+// Error-free sum of two binary32 numbers (Knuth's TwoSum): a + b = s + e
+// exactly.  The error-free transformations use the _rn intrinsics, which the
+// compiler never contracts into a fused multiply-add: the proofs need each
+// sum and product rounded on its own.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 // Dekker's Fast2Sum: the same when |a| >= |b| (a variance plus a smaller
 // increment, or minus a smaller decrement).
 __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  e = b - (s - a);
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
 // ---------------------------------------------------------------------------
@@ -358,12 +362,42 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   T.c[13] = fmaf(th2, tt * w * t, T.c[13]);
 }
 
-// Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: det,
-// quadratic form r^T adj(S) r and, where the chi2 value is needed (inward pass,
-// diagnostics), the reciprocal of det (Newton step from an FP32 seed) and the
-// chi2 product; otherwise the gate is decided as r^T adj(S) r - chi2_max det <= 0
-// with one fused multiply-add.  The chi2 sum is done by the caller.  Non-finite
-// innovation matrices give chi2 = NaN and a rejected cluster, as in FP64.
+// Error-free product of two binary32 numbers: a * b = p + e exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+
+// The quadratic form r^T adj(S) r = S11 r0^2 - 2 S10 r0 r1 + S00 r1^2 as an
+// unevaluated sum qh + ql of two binary32 numbers, from error-free products
+// and sums (the compensated dot product of Ogita, Rump and Oishi, 2005, in
+// nested form r0 (S11 r0 - 2 S10 r1) + S00 r1 r1): relative error of order
+// 2^-46 of the sum of the magnitudes of the three terms, which for a positive
+// definite S bounds it by a small multiple of the form itself.  On GB300 these
+// 31 binary32 operations cost less than the 5 binary64 ones they replace.
+__device__ __forceinline__ void quad_form2(float S00, float S10, float S11, float r0, float r1, float &qh,
+                                           float &ql) {
+  float p1, e1, p2, e2, uh, ul, vh, t, tl, wh;
+  two_prod(S11, r0, p1, e1);
+  two_prod(-2.0f * S10, r1, p2, e2);  // -2 S10 exact
+  two_sum(p1, p2, uh, ul);
+  ul += e1 + e2;                       // u = S11 r0 - 2 S10 r1 = uh + ul
+  vh = __fmul_rn(r0, uh);
+  const float vl = fmaf(r0, ul, fmaf(r0, uh, -vh));  // r0 u = vh + vl
+  two_prod(r1, r1, t, tl);
+  wh = __fmul_rn(S00, t);
+  const float wl = fmaf(S00, tl, fmaf(S00, t, -wh));  // S00 r1^2 = wh + wl
+  two_sum(vh, wh, qh, ql);
+  ql += vl + wl;
+}
+
+// Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: the
+// determinant of S, and where the chi2 value is needed (inward pass,
+// diagnostics) the reciprocal of det (Newton step from an FP32 seed), chi2 =
+// q / det and (by the caller) the chi2 sum; otherwise the gate is decided in
+// FP64 as q - chi2_max det <= 0.  The quadratic form q = r^T adj(S) r enters
+// as the exact binary64 sum of its two binary32 parts.  Non-finite innovation
+// matrices or residuals give chi2 = NaN and a rejected cluster, as in FP64.
 // Returns the status (OK / NOT_PD).
 __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, double gate, uint32_t gate_hi,
                                       uint32_t gate_lo, bool want_chi2, bool &acc, double &chi2) {
@@ -371,28 +405,23 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
   const float r0 = (yc - T.ya) - T.dy;
   const float r1 = (zc - T.za) - T.dz;
   const float S00 = c[0] + vy, S10 = c[1], S11 = c[2] + vz;
-  const bool fin = fabsf(S00 + S11 + S10) < INFINITY;
+  float qh, ql;
+  quad_form2(S00, S10, S11, r0, r1, qh, ql);
+  const bool fin = fabsf((S00 + S11) + (S10 + qh)) < INFINITY;
   const float det32 = fmaf(S00, S11, -(S10 * S10));
   const float i32 = __fdividef(1.0f, det32);  // FP32 seed of 1/det, and the gain's 1/det
   // ---- FP64 island ----
-  const double s00 = widen_pos(S00), s11 = widen_pos(S11);
-  uint32_t h10, l10;
-  widen_halves(S10, h10, l10);
-  const double s10 = join64(h10, l10);
-  const double m2s10 = join64((h10 ^ 0x80000000u) + (1u << 20), l10);  // -2 s10, exactly
-  const double q0 = widen(r0), q1 = widen(r1);
+  const double s00 = widen_pos(S00), s11 = widen_pos(S11), s10 = widen(S10);
   const double det = fma(s00, s11, -(s10 * s10));
-  double qf = fma(m2s10, q1, s11 * q0);  // s11 r0 - 2 s10 r1
-  qf = q0 * qf;
-  qf = fma(s00 * q1, q1, qf);            // r^T adj(S) r
+  const double qhd = widen(qh), qld = widen(ql);
   if (want_chi2) {
     const double y0 = widen_pos(i32);
     const double ey = fma(-det, y0, 1.0);
     const double inv = fma(y0, ey, y0);  // 1/det, one Newton step
-    chi2 = qf * inv;
+    chi2 = fma(qhd, inv, qld * inv);
     acc = le_finite64(chi2, gate_hi, gate_lo);
   } else {
-    acc = le0_finite64(fma(-gate, det, qf));
+    acc = le0_finite64(fma(-gate, det, qhd) + qld);
   }
   const bool notpd = fin && (le0_finite64(det) || !(S00 > 0.0f) || !(S11 > 0.0f));
   // ---- back to FP32 ----
@@ -485,19 +514,29 @@ struct Clu {
 template <int BLOCK>
 __device__ __forceinline__ void stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, float *stg) {
   const int buf = c & 1;
+  const int64_t k0 = a + (int64_t)kChunk * c;
+  float *dst0 = stg + (buf * kStageArrays) * kChunk * BLOCK;
+  if (k0 + kChunk <= e) {  // full chunk: four consecutive clusters of each array
+    const float *src[kStageArrays] = {A.x + k0, A.y + k0, A.z + k0, A.sy2 + k0, A.sz2 + k0};
 #pragma unroll
-  for (int s = 0; s < kChunk; ++s) {
-    const int64_t k = a + (int64_t)kChunk * c + s;
-    const bool v = k < e;
-    const int64_t kk = v ? k : e - 1;
-    float *dst = stg + ((buf * kStageArrays) * kChunk + s) * BLOCK;
-    cp_async4(dst + 0 * kChunk * BLOCK, A.x + kk, v);
-    cp_async4(dst + 1 * kChunk * BLOCK, A.y + kk, v);
-    cp_async4(dst + 2 * kChunk * BLOCK, A.z + kk, v);
-    cp_async4(dst + 3 * kChunk * BLOCK, A.sy2 + kk, v);
-    cp_async4(dst + 4 * kChunk * BLOCK, A.sz2 + kk, v);
+    for (int j = 0; j < kStageArrays; ++j)
+#pragma unroll
+      for (int s = 0; s < kChunk; ++s) cp_async4(dst0 + (j * kChunk + s) * BLOCK, src[j] + s, true);
+  } else {  // the track's last chunk: slots past the end are zero-filled from an in-range address
+#pragma unroll
+    for (int s = 0; s < kChunk; ++s) {
+      const int64_t k = k0 + s;
+      const bool v = k < e;
+      const int64_t kk = v ? k : e - 1;
+      float *dst = dst0 + s * BLOCK;
+      cp_async4(dst + 0 * kChunk * BLOCK, A.x + kk, v);
+      cp_async4(dst + 1 * kChunk * BLOCK, A.y + kk, v);
+      cp_async4(dst + 2 * kChunk * BLOCK, A.z + kk, v);
+      cp_async4(dst + 3 * kChunk * BLOCK, A.sy2 + kk, v);
+      cp_async4(dst + 4 * kChunk * BLOCK, A.sz2 + kk, v);
+    }
   }
-  const uint8_t *p0 = A.row + a + (int64_t)kChunk * c;
+  const uint8_t *p0 = A.row + k0;
   const uint32_t *w0 = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(p0) & ~(uintptr_t)3);
   const bool v1 = reinterpret_cast<const uint8_t *>(w0 + 1) < A.row + e;
   float *rdst = stg + (kStageFloats + 2 * buf) * BLOCK;
@@ -568,6 +607,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
     float xcur = xref;
 #pragma unroll
     for (int w = 0; w < kBitWords; ++w) bits[32 * w] = 0u;
+    uint8_t *const acc_t = A.accept + a;  // this track's accept bytes
     int done = 0;      // clusters (from the outer end) whose accept byte is final
     int out_done = 0;  // clusters the outward pass updated with
     if (st0 == ST_OK) {
@@ -688,7 +728,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
             nacc += acc ? 1 : 0;
             const uint32_t ob = (bits[32 * (kc >> 5)] >> (kc & 31)) & 1u;
-            A.accept[a + kc] = (uint8_t)(ob | (acc ? 2u : 0u));
+            acc_t[kc] = (uint8_t)(ob | (acc ? 2u : 0u));
             ++done;
             if (--kc >= 0) {
               if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above
@@ -800,11 +840,11 @@ cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t strea
   if (a.n_tracks <= 0) return cudaSuccess;
   cudaError_t e;
   if (block == 128) {
-    if ((e = set_fit_smem<128, 6>()) != cudaSuccess) return e;
-    k_fit<128, 6><<<grid, 128, fit_smem<128>(), stream>>>(a);
+    if ((e = set_fit_smem<128, 4>()) != cudaSuccess) return e;
+    k_fit<128, 4><<<grid, 128, fit_smem<128>(), stream>>>(a);
   } else {
-    if ((e = set_fit_smem<256, 3>()) != cudaSuccess) return e;
-    k_fit<256, 3><<<grid, 256, fit_smem<256>(), stream>>>(a);
+    if ((e = set_fit_smem<256, 2>()) != cudaSuccess) return e;
+    k_fit<256, 2><<<grid, 256, fit_smem<256>(), stream>>>(a);
   }
   return cudaGetLastError();
 }
@@ -813,21 +853,21 @@ int fit_blocks_per_sm(int block) {
   int n = 0;
   cudaError_t e;
   if (block == 128) {
-    set_fit_smem<128, 6>();
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<128, 6>, 128, fit_smem<128>());
+    set_fit_smem<128, 4>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<128, 4>, 128, fit_smem<128>());
   } else {
-    set_fit_smem<256, 3>();
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<256, 3>, 256, fit_smem<256>());
+    set_fit_smem<256, 2>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<256, 2>, 256, fit_smem<256>());
   }
   if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 
-// Resident blocks per SM when the caller leaves the choice to the library: the
-// occupancy maximum keeps 768 tracks per SM in flight, whose clusters do not
+// Resident blocks per SM when the caller leaves the choice to the library:
+// 512 tracks per SM.  With 768 tracks per SM in flight their clusters do not
 // stay in L2 between the outward and the inward pass (DRAM reads of 170 B per
-// cluster against 60 B with 512 tracks per SM, measured on GB300); 512 tracks
-// per SM is the fastest residency there.
+// cluster against 60 B with 512, measured on GB300), so the instantiations are
+// compiled for 512 threads per SM (up to 128 registers per thread).
 int fit_default_blocks_per_sm(int block) {
   const int occ = fit_blocks_per_sm(block);
   const int want = 512 / (block == 128 ? 128 : 256);
@@ -836,7 +876,7 @@ int fit_default_blocks_per_sm(int block) {
 
 int fit_regs_per_thread() {
   cudaFuncAttributes at;
-  if (cudaFuncGetAttributes(&at, k_fit<256, 3>) != cudaSuccess) return -1;
+  if (cudaFuncGetAttributes(&at, k_fit<256, 2>) != cudaSuccess) return -1;
   return at.numRegs;
 }
 

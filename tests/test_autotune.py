@@ -9,12 +9,13 @@ from paper_2402_01205_gb300 import autotune as A
 def test_candidates_cover_every_shape_once():
     c = A.candidates()
     keys = {tuple(sorted(d.items())) for d in c}
-    assert len(keys) == len(c) == 2 * (6 + 3)
+    assert len(keys) == len(c) == 2 * (5 + 2)
     assert all(1 <= d["blocks_per_sm"] <= A.MAX_BLOCKS_PER_SM[d["block_threads"]] for d in c)
 
 
 def test_tune_picks_fastest_and_ties_go_first():
     cands = A.candidates(block_threads=(256,), sort_tracks=(1,))
+    cands = cands + [{"block_threads": 256, "blocks_per_sm": 3, "sort_tracks": 1}]
     ms = {1: 30.0, 2: 12.5, 3: 12.5}
     e = A.tune(None, None, cands=cands, timer=lambda c: ms[c["blocks_per_sm"]])
     assert e["choice"] == {"block_threads": 256, "blocks_per_sm": 2, "sort_tracks": 1}
