@@ -520,6 +520,30 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe):
                 lat[i] = t_end - (t0 + a)
         return lat, t_end - (t0 + arr[0])
 
+    def unloaded(f, reps=3):
+        """Latency of one frame with nothing else in flight: served, and plain fit."""
+        out = {}
+        with T.Fitter(device=local, hbm_budget_bytes=budget, max_slots=8) as fx:
+            fx.wait(fx.submit(f, res_for(0, f)))
+            ts = []
+            for _ in range(reps):
+                t0 = T.now()
+                ts.append(fx.wait(fx.submit(f, res_for(0, f)))[1] - t0)
+            out["served_ms"] = 1e3 * min(ts)
+        with T.Fitter(device=local) as fx:
+            fx.fit(f, res_for(0, f))
+            ts = []
+            for _ in range(reps):
+                t0 = T.now()
+                fx.fit(f, res_for(0, f))
+                ts.append(T.now() - t0)
+            out["plain_fit_ms"] = 1e3 * min(ts)
+        out["n_clusters"] = f.n_clusters
+        out["h2d_floor_ms"] = 1e3 * (21 * f.n_clusters + 8 * f.n_tracks) / 211e9
+        return out
+
+    by_size = sorted(range(len(frames)), key=lambda k: frames[k].n_clusters)
+    unloaded_lat = {"largest": unloaded(frames[by_size[-1]]), "median": unloaded(frames[by_size[len(by_size) // 2]])}
     ncl = np.array([frames[k].n_clusters for k in pick], dtype=np.float64)
     ntr = np.array([frames[k].n_tracks for k in pick], dtype=np.float64)
     if dist:
@@ -566,7 +590,8 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe):
 
     def summary(lat, span, cl, tr):
         ms = [x * 1e3 for x in lat]
-        return {"p50_ms": percentile(ms, 50), "p99_ms": percentile(ms, 99), "max_ms": max(ms),
+        return {"p50_ms": percentile(ms, 50), "p90_ms": percentile(ms, 90), "p99_ms": percentile(ms, 99),
+                "p999_ms": percentile(ms, 99.9), "max_ms": max(ms),
                 "mean_ms": float(np.mean(ms)), "clusters_per_s": cl / span, "tracks_per_s": tr / span,
                 "frames": len(lat), "span_s": span}
 
@@ -588,6 +613,7 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe):
             "capacity": {"frames": n_cap,
                          "served": summary(lat_cs, span_cs, cap_cl, float(ntr[:n_cap].sum())),
                          "sequential_plain_fit": summary(lat_cq, span_cq, cap_cl, float(ntr[:n_cap].sum()))},
+            "unloaded_latency": unloaded_lat,
             "device_only_fit_ms": {"p50": percentile(dev_ms, 50), "p99": percentile(dev_ms, 99),
                                    "note": "one pool frame resident in HBM, launch sequence time"},
             "e2e": {"value": sustained, "unit": "clusters/s", "h2d_bytes_per_step": int(21 * ncl.mean() + 8 * ntr.mean()),

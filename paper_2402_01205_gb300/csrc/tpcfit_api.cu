@@ -210,9 +210,10 @@ struct tpcfit_handle {
 FitArgs make_args(tpcfit_handle *h, const tpcfit_frame *f, const tpcfit_result *r, Scratch &s, int64_t off_base);
 int run_sequence(tpcfit_handle *h, const FitArgs &a, cudaStream_t st, Scratch &s, bool timed, int *launches);
 cudaStream_t handle_stream(tpcfit_handle *h) { return h->stream; }
+int64_t handle_chunk_clusters(tpcfit_handle *h) { return h->chunk_clusters; }
 size_t serve_scratch_bytes(int64_t n_tracks) { return Scratch::bytes_for(n_tracks); }
 int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
-                       cudaStream_t st, const int32_t **err_dev);
+                       int64_t off_base, cudaStream_t st, const int32_t **err_dev);
 int handle_device(tpcfit_handle *h) { return h->device; }
 const tpcfit_config &handle_config(tpcfit_handle *h) { return h->cfg; }
 ServeState *&handle_serve(tpcfit_handle *h) { return h->serve; }
@@ -446,14 +447,14 @@ int run_sequence(tpcfit_handle *h, const FitArgs &a, cudaStream_t st, Scratch &s
   return TPCFIT_OK;
 }
 
-// Fit of one resident serving frame on a slot stream; scratch lives in the
-// slot's allocation.
+// Fit of one resident serving frame (or part of a frame, whose offsets start
+// at off_base) on a slot stream; scratch lives in the slot's allocation.
 int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
-                       cudaStream_t st, const int32_t **err_dev) {
+                       int64_t off_base, cudaStream_t st, const int32_t **err_dev) {
   Scratch s;
   s.layout((char *)scratch_base, f->n_tracks);
   CU(cudaMemsetAsync(s.hist, 0, s.small_bytes, st));
-  FitArgs a = make_args(h, f, r, s, 0);
+  FitArgs a = make_args(h, f, r, s, off_base);
   int rc = run_sequence(h, a, st, s, false, nullptr);
   if (rc) return rc;
   *err_dev = s.err;
@@ -628,11 +629,13 @@ static int validate_host_offsets(const tpcfit_frame *f) {
 static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
   if (r->chi2_out_cluster || r->chi2_in_cluster || r->restart_state)
     return fail(TPCFIT_E_INVAL, "diagnostic outputs need a device frame and device results");
-  int rc = validate_host_offsets(f);
-  if (rc) return rc;
   const int64_t *off = f->track_offsets;
   const int64_t nt = f->n_tracks;
-  // chunk boundaries
+  int rc = TPCFIT_OK;
+  if (off[0] != 0 || off[nt] != f->n_clusters) return fail(TPCFIT_E_INVAL, "offsets do not span [0, n_clusters]");
+  // chunk boundaries by binary search on the offsets; the cut points are
+  // checked here, the offsets inside each chunk just before its copies are
+  // enqueued (so the check of chunk i overlaps the copies of chunk i-1)
   std::vector<int64_t> cuts{0};
   while (cuts.back() < nt) {
     int64_t t0 = cuts.back();
@@ -643,6 +646,8 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
       if (off[mid] >= target) hi = mid;
       else lo = mid + 1;
     }
+    if (off[lo] < off[t0] || off[lo] > f->n_clusters)
+      return fail(TPCFIT_E_INVAL, "offsets decrease or leave [0, n_clusters] before track %lld", (long long)lo);
     cuts.push_back(lo);
   }
   int64_t max_nt = 0, max_nc = 0;
@@ -662,6 +667,14 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     const int64_t t0 = cuts[ci], t1 = cuts[ci + 1];
     const int64_t c0 = off[t0], c1 = off[t1];
     const int64_t cnt = t1 - t0, ncl = c1 - c0;
+    for (int64_t t = t0; t < t1; ++t)
+      if (off[t + 1] < off[t]) {
+        // nothing of this chunk is enqueued; let the chunks in flight finish
+        wait_stream(h->h2d, -1);
+        wait_stream(h->stream, -1);
+        wait_stream(h->d2h, -1);
+        return fail(TPCFIT_E_INVAL, "offsets decrease at track %lld", (long long)t);
+      }
     // inputs: wait until this stage's previous results have been copied out
     CU(cudaStreamWaitEvent(h->h2d, S.free_ev, 0));
     CU(cudaMemcpyAsync(S.off, off + t0, (size_t)(cnt + 1) * 8, cudaMemcpyHostToDevice, h->h2d));

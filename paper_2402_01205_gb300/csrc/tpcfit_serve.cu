@@ -1,7 +1,11 @@
 // Serving runtime: time frames submitted from the host are admitted into
 // resident device slots as slots and HBM budget free up, fitted on one stream
 // per slot (so the copies and kernels of different frames overlap on the
-// device), and their results copied back into the caller's buffers.
+// device), and their results copied back into the caller's buffers.  A frame
+// is split into parts of about host_chunk_clusters clusters (tracks are
+// independent), each admitted to a slot of its own, so that the copies of one
+// part overlap the fit of the previous part of the same frame; a ticket is
+// done when all its parts are.
 //
 // The paper's asynchronous reconstruction limits the number of time frames in
 // flight and throttles their injection (Sec. 7) and processes several time
@@ -39,7 +43,8 @@ int handle_device(tpcfit_handle *h);
 const tpcfit_config &handle_config(tpcfit_handle *h);
 ServeState *&handle_serve(tpcfit_handle *h);
 int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *dev_frame, tpcfit_result *dev_res, void *scratch_base,
-                       cudaStream_t st, const int32_t **err_dev);
+                       int64_t off_base, cudaStream_t st, const int32_t **err_dev);
+int64_t handle_chunk_clusters(tpcfit_handle *h);
 size_t serve_scratch_bytes(int64_t n_tracks);
 void serve_stop(tpcfit_handle *h);
 
@@ -64,15 +69,23 @@ size_t frame_bytes(int64_t nt, int64_t nc) {
 struct Request {
   tpcfit_frame frame;
   tpcfit_result res;
-  size_t bytes = 0;
+  size_t bytes = 0;  // the whole frame resident at once (admission limit)
   int state = TPCFIT_PENDING;
   double t_submit = 0, t_done = 0;
-  int slot = -1;
+  int parts_left = 0;
+  bool failed = false;
+};
+
+// Tracks [t0, t1) of a request, fitted as one resident frame.
+struct Part {
+  uint64_t ticket = 0;
+  int64_t t0 = 0, t1 = 0;
+  size_t bytes = 0;
 };
 
 struct Slot {
   bool busy = false;
-  uint64_t ticket = 0;
+  Part part;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   void *mem = nullptr;
@@ -88,7 +101,7 @@ struct ServeState {
   std::thread worker;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<uint64_t> queue;
+  std::deque<Part> queue;
   std::map<uint64_t, Request> reqs;
   std::vector<Slot> slots;
   size_t used = 0, budget = 0;
@@ -130,60 +143,70 @@ static void carve(void *mem, int64_t nt, int64_t nc, tpcfit_frame *df, tpcfit_re
   *scratch = p;
 }
 
-// Enqueue copy-in, fit and copy-out of request `tk` on slot `si` (lock held).
-static bool launch(ServeState *S, uint64_t tk, int si) {
-  Request &R = S->reqs[tk];
+// Enqueue copy-in, fit and copy-out of part P on slot `si` (lock held).
+static bool launch(ServeState *S, const Part &P, int si) {
+  Request &R = S->reqs[P.ticket];
   Slot &L = S->slots[si];
-  const int64_t nt = R.frame.n_tracks, nc = R.frame.n_clusters;
-  if (cudaError_t e = cudaMallocFromPoolAsync(&L.mem, R.bytes, S->pool, L.stream); e != cudaSuccess) {
+  const tpcfit_frame &F = R.frame;
+  const int64_t c0 = F.track_offsets[P.t0], c1 = F.track_offsets[P.t1];
+  const int64_t nt = P.t1 - P.t0, nc = c1 - c0;
+  if (cudaError_t e = cudaMallocFromPoolAsync(&L.mem, P.bytes, S->pool, L.stream); e != cudaSuccess) {
     cudaGetLastError();
     if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: pool allocation of %zu bytes failed: %s\n",
-                                 (unsigned long long)tk, R.bytes, cudaGetErrorString(e));
+                                 (unsigned long long)P.ticket, P.bytes, cudaGetErrorString(e));
     return false;
   }
-  L.bytes = R.bytes;
+  L.bytes = P.bytes;
   L.busy = true;
-  L.ticket = tk;
+  L.part = P;
   L.failed = false;
-  R.slot = si;
-  S->used += R.bytes;
+  S->used += P.bytes;
   tpcfit_frame df;
   tpcfit_result dr;
   void *scratch = nullptr;
   carve(L.mem, nt, nc, &df, &dr, &scratch);
-  const tpcfit_frame &F = R.frame;
   bool ok = true;
   auto cp = [&](const void *dst, const void *src, size_t b, cudaMemcpyKind k) {
     if (!b || !ok) return;
     if (cudaError_t e = cudaMemcpyAsync((void *)dst, src, b, k, L.stream); e != cudaSuccess) {
       ok = false;
       if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: copy of %zu bytes failed: %s\n",
-                                   (unsigned long long)tk, b, cudaGetErrorString(e));
+                                   (unsigned long long)P.ticket, b, cudaGetErrorString(e));
     }
   };
-  cp(df.track_offsets, F.track_offsets, (size_t)(nt + 1) * 8, cudaMemcpyHostToDevice);
-  cp(df.x, F.x, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.y, F.y, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.z, F.z, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.sy2, F.sy2, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.sz2, F.sz2, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.row, F.row, (size_t)nc, cudaMemcpyHostToDevice);
+  cp(df.track_offsets, F.track_offsets + P.t0, (size_t)(nt + 1) * 8, cudaMemcpyHostToDevice);
+  cp(df.x, F.x + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.y, F.y + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.z, F.z + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.sy2, F.sy2 + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.sz2, F.sz2 + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
+  cp(df.row, F.row + c0, (size_t)nc, cudaMemcpyHostToDevice);
   const int32_t *err_dev = nullptr;
-  if (ok && serve_launch_frame(S->h, &df, &dr, scratch, L.stream, &err_dev) != TPCFIT_OK) ok = false;
+  if (ok && serve_launch_frame(S->h, &df, &dr, scratch, c0, L.stream, &err_dev) != TPCFIT_OK) ok = false;
   if (ok) cp(L.h_err, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost);
   const tpcfit_result &O = R.res;
-  cp(O.state, dr.state, (size_t)nt * 20, cudaMemcpyDeviceToHost);
-  cp(O.cov, dr.cov, (size_t)nt * 60, cudaMemcpyDeviceToHost);
-  cp(O.x_ref, dr.x_ref, (size_t)nt * 4, cudaMemcpyDeviceToHost);
-  cp(O.chi2, dr.chi2, (size_t)nt * 8, cudaMemcpyDeviceToHost);
-  cp(O.ndf, dr.ndf, (size_t)nt * 4, cudaMemcpyDeviceToHost);
-  cp(O.status, dr.status, (size_t)nt * 4, cudaMemcpyDeviceToHost);
-  cp(O.accept, dr.accept, (size_t)nc, cudaMemcpyDeviceToHost);
+  cp(O.state + 5 * P.t0, dr.state, (size_t)nt * 20, cudaMemcpyDeviceToHost);
+  cp(O.cov + 15 * P.t0, dr.cov, (size_t)nt * 60, cudaMemcpyDeviceToHost);
+  cp(O.x_ref + P.t0, dr.x_ref, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+  cp(O.chi2 + P.t0, dr.chi2, (size_t)nt * 8, cudaMemcpyDeviceToHost);
+  cp(O.ndf + P.t0, dr.ndf, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+  cp(O.status + P.t0, dr.status, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+  cp(O.accept + c0, dr.accept, (size_t)nc, cudaMemcpyDeviceToHost);
   if (!ok) cudaGetLastError();
   L.failed = !ok;
   cudaFreeAsync(L.mem, L.stream);  // released in stream order after the copies
   cudaEventRecord(L.done, L.stream);
   return true;
+}
+
+// One part of a request has finished (lock held).
+static void part_done(ServeState *S, uint64_t tk, bool failed) {
+  Request &R = S->reqs[tk];
+  R.failed |= failed;
+  if (--R.parts_left == 0) {
+    R.t_done = tpcfit_now();
+    R.state = R.failed ? TPCFIT_FAILED : TPCFIT_DONE;
+  }
 }
 
 static void worker_loop(ServeState *S) {
@@ -197,12 +220,11 @@ static void worker_loop(ServeState *S) {
       if (!L.busy) continue;
       cudaError_t q = cudaEventQuery(L.done);
       if (q == cudaErrorNotReady) continue;
-      Request &R = S->reqs[L.ticket];
-      R.t_done = tpcfit_now();
-      R.state = (q == cudaSuccess && !L.failed && *L.h_err == 0) ? TPCFIT_DONE : TPCFIT_FAILED;
-      if (R.state == TPCFIT_FAILED && debug_on())
+      const bool failed = !(q == cudaSuccess && !L.failed && *L.h_err == 0);
+      if (failed && debug_on())
         std::fprintf(stderr, "tpcfit serve: ticket %llu failed: event %s, enqueue %s, frame error word %d\n",
-                     (unsigned long long)L.ticket, cudaGetErrorString(q), L.failed ? "failed" : "ok", *L.h_err);
+                     (unsigned long long)L.part.ticket, cudaGetErrorString(q), L.failed ? "failed" : "ok", *L.h_err);
+      part_done(S, L.part.ticket, failed);
       if (q != cudaSuccess) cudaGetLastError();
       S->used -= L.bytes;
       L.busy = false;
@@ -220,12 +242,11 @@ static void worker_loop(ServeState *S) {
           break;
         }
       if (free_slot < 0) break;
-      Request &R = S->reqs[*it];
+      const Part P = *it;
       const bool is_head = (it == S->queue.begin());
-      if (S->used + R.bytes <= S->budget) {
-        if (!launch(S, *it, free_slot)) {
-          R.state = TPCFIT_FAILED;
-          R.t_done = tpcfit_now();
+      if (S->used + P.bytes <= S->budget) {
+        if (!launch(S, P, free_slot)) {
+          part_done(S, P.ticket, true);
           S->cv_done.notify_all();
         }
         if (is_head) S->head_blocked_since = -1.0;
@@ -312,6 +333,24 @@ int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint
   ServeState *S = handle_serve(h);
   const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters);
   if (bytes > S->budget) return TPCFIT_E_NOMEM;
+  // parts of about host_chunk_clusters clusters (offsets were checked by the caller)
+  const int64_t *off = f->track_offsets;
+  const int64_t target = handle_chunk_clusters(h);
+  std::vector<Part> parts;
+  for (int64_t t0 = 0; t0 < f->n_tracks;) {
+    int64_t lo = t0 + 1, hi = f->n_tracks;  // first t1 with off[t1] >= off[t0] + target, or nt
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (off[mid] >= off[t0] + target) hi = mid;
+      else lo = mid + 1;
+    }
+    Part P;
+    P.t0 = t0;
+    P.t1 = lo;
+    P.bytes = frame_bytes(lo - t0, off[lo] - off[t0]);
+    parts.push_back(P);
+    t0 = lo;
+  }
   std::lock_guard<std::mutex> lk(S->mu);
   const uint64_t tk = S->next_ticket++;
   Request &R = S->reqs[tk];
@@ -319,11 +358,14 @@ int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint
   R.res = *r;
   R.bytes = bytes;
   R.t_submit = tpcfit_now();
-  if (f->n_tracks == 0) {
+  R.parts_left = (int)parts.size();
+  if (parts.empty()) {
     R.state = TPCFIT_DONE;
     R.t_done = R.t_submit;
-  } else {
-    S->queue.push_back(tk);
+  }
+  for (Part &P : parts) {
+    P.ticket = tk;
+    S->queue.push_back(P);
   }
   *ticket = tk;
   S->cv_work.notify_one();

@@ -114,3 +114,18 @@ def test_poll_pending_then_done_and_wait_timeout(T):
             st, t_done = fx.poll(tk)
             time.sleep(0.001)
         assert st == T.DONE
+
+
+def test_frame_split_into_parts_equals_plain_fit(T):
+    """A served frame larger than host_chunk_clusters is fitted as several
+    parts on several slots; the results are those of one plain fit."""
+    f = tpcgen.generate("detector50k", n_tracks=20_000, seed=6)
+    ref = alone(T, f)
+    with T.Fitter(host_chunk_clusters=250_000, max_slots=3) as fx:  # about 9 parts, 3 slots
+        res = [T.alloc_result(f.n_tracks, f.n_clusters, pinned=True) for _ in range(2)]
+        tickets = [fx.submit(pinned_frame(f), r) for r in res]
+        for t in tickets:
+            assert fx.wait(t, 60)[0] == T.DONE
+    for r in res:
+        for k in ref:
+            assert np.array_equal(ref[k], r[k].numpy(), equal_nan=k in ("state", "cov")), k
