@@ -722,6 +722,26 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roofline = fit_roofline(nc, nt, nc_fit, fit_s, (tm["fit_grid"], tm["fit_block"]), probe, sms, clk.get("sm_mhz"))
     roofline["fp32_fma_peak_per_s"] = probe["fp32_fma_per_s"]
+    # the same steps with the track-model compression residual codes written (4 B per cluster more)
+    res_r = T.alloc_result(nt, nc, device=torch.device("cuda", local), residuals=True)
+    for _ in range(2):
+        fx.fit_async(dev, res_r, stream=stream)
+    fx.sync()
+    fx.reset_timing()
+    n_res = max(3, min(args.steps, 20))
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(n_res):
+        fx.fit_async(dev, res_r, stream=stream)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    ms_res = reduce_max(dist, torch, r0.elapsed_time(r1))
+    tm_res = fx.timing()
+    with_residuals = {"value": nc_all * n_res / (ms_res * 1e-3), "unit": "clusters/s", "steps": n_res,
+                      "ms_per_step": ms_res / n_res, "fit_ms": tm_res["fit_ms_sum"] / max(tm_res["n_timed"], 1),
+                      "extra_bytes_per_cluster": 4,
+                      "what": "int16 residual codes of every cluster against the fitted helix (y and z)"}
+    del res_r
     # end to end through the C-ABI: pinned host frame in, pinned host results out
     e2e = None
     if args.e2e_steps > 0:
@@ -761,6 +781,7 @@ def main():
                        "fit_regs": tm["fit_regs"]},
             "tracks_per_s": nt * ws * args.steps / (ms * 1e-3),
             "roofline": roofline,
+            "with_residuals": with_residuals,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(tm["kernel_launches"]) * args.steps,

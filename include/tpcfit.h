@@ -88,7 +88,9 @@ typedef struct tpcfit_config {
   int32_t block_threads;  /* fit kernel block size: 128 or 256 (0 = 256) */
   int32_t blocks_per_sm;  /* fit kernel resident blocks per SM; 0 = tuned default (512 threads per SM) */
   int32_t sort_tracks;    /* 1: fit tracks longest-first (default); 0: in frame order */
-  int32_t reserved[7];
+  float res_step_y_cm;    /* residual code step in y (0.01 cm), see tpcfit_result.res_y */
+  float res_step_z_cm;    /* residual code step in z (0.01 cm) */
+  int32_t reserved[5];
   int64_t host_chunk_clusters; /* host frames are copied and fitted in chunks of about this many clusters (16M) */
 } tpcfit_config;
 
@@ -124,6 +126,18 @@ typedef struct tpcfit_result {
   /* optional: state (y, z, sinphi, tanlambda, q/pT) the inward pass restarted
    * from, at the outermost cluster; NULL = not written (same rules as above) */
   float *restart_state;     /* n_tracks*5 */
+  /* optional track-model compression residuals (Sec. 5: the TPC data are
+   * stored as cluster-to-track residuals instead of absolute coordinates):
+   * for the clusters of a track with status OK, round-half-even((y_c - y_t) /
+   * res_step_y_cm) and likewise in z, where (y_t, z_t) is the fitted helix
+   * (state at x_ref, no scattering) evaluated at the cluster's x; clipped to
+   * +-32767.  -32768 marks a cluster that is not encoded (track not OK, or a
+   * helix that does not reach the cluster).  A decoder holding the fitted
+   * state, x_ref and the clusters' x restores y, z to within half a step.
+   * NULL = not written.  Written by tpcfit_fit (device and host frames),
+   * tpcfit_fit_async, batches and serving; not by tpcfit_fit_noalloc. */
+  int16_t *res_y;           /* n_clusters */
+  int16_t *res_z;           /* n_clusters */
 } tpcfit_result;
 
 /* Kernel timings of the last completed fit on a handle (CUDA events on the

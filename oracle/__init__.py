@@ -70,6 +70,8 @@ def _load():
         lib.orc_update.restype = ctypes.c_int
         lib.orc_ms_noise.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double]
         lib.orc_seed.argtypes = [_D, _D, _D, ctypes.c_double, _D]
+        lib.oracle_residuals.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64] * 2 + [ctypes.c_void_p] * 11
+        lib.oracle_residuals.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -120,6 +122,26 @@ def fit(frame, cfg: Optional[FitConfig] = None, threads: Optional[int] = None, d
     if rc != 0:
         raise ValueError("oracle_fit: malformed track offsets")
     out["threads"] = min(th, max(nt, 1))
+    return out
+
+
+def residuals(frame, fitted: dict, step=(0.01, 0.01), bz: float = 0.5) -> dict:
+    """Track-model compression residual codes of ``frame`` against the oracle's
+    own fit ``fitted`` (the output of ``fit``): int16 codes ``res_y``,
+    ``res_z`` and the unquantised residuals in code units ``raw_y``, ``raw_z``."""
+    lib = _load()
+    off = np.ascontiguousarray(frame.offsets, dtype=np.int64)
+    x, y, z = (np.ascontiguousarray(getattr(frame, k), dtype=np.float32) for k in ("x", "y", "z"))
+    nt, nc = off.shape[0] - 1, int(x.shape[0])
+    st = np.ascontiguousarray(fitted["state"], dtype=np.float64)
+    xr = np.ascontiguousarray(fitted["x_ref"], dtype=np.float64)
+    status = np.ascontiguousarray(fitted["status"], dtype=np.int32)
+    out = dict(res_y=np.zeros(nc, np.int16), res_z=np.zeros(nc, np.int16), raw_y=np.zeros(nc), raw_z=np.zeros(nc))
+    rc = lib.oracle_residuals(bz, step[0], step[1], nt, nc, off.ctypes.data, x.ctypes.data, y.ctypes.data,
+                              z.ctypes.data, st.ctypes.data, xr.ctypes.data, status.ctypes.data,
+                              *[out[k].ctypes.data for k in ("res_y", "res_z", "raw_y", "raw_z")])
+    if rc != 0:
+        raise ValueError("oracle_residuals: malformed track offsets")
     return out
 
 

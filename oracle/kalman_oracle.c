@@ -407,3 +407,47 @@ int oracle_fit(const orc_config *c, int64_t nt, int64_t nc, const int64_t *off, 
   if (nth > 1) for (int i = 0; i < nth; ++i) pthread_join(th[i], NULL);
   return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Track-model compression residuals.  The paper's TPC compression stores
+ * cluster-to-track residuals instead of absolute coordinates (Sec. 5) and
+ * gives no formula.  Reading: for a track with status OK, the residual of
+ * cluster k is its (y, z) minus the fitted helix -- the fit's output state at
+ * x_ref, transported without scattering in one exact-helix step to the
+ * cluster's x; its code is round-half-even(residual / step), clipped to
+ * +-32767.  Clusters of other tracks, and clusters the helix does not reach,
+ * get -32768.  raw_y / raw_z (may be NULL) receive residual / step in FP64.
+ * Returns 0, or -1 on malformed offsets.
+ * ------------------------------------------------------------------------- */
+static int16_t orc_code(double q) {
+  if (isnan(q)) return (int16_t)-32768;
+  if (!(fabs(q) < 32767.5)) return q > 0 ? (int16_t)32767 : (int16_t)-32767;
+  return (int16_t)nearbyint(q); /* default rounding mode: half to even */
+}
+
+int oracle_residuals(double bz, double step_y, double step_z, int64_t nt, int64_t nc, const int64_t *off,
+                     const float *x, const float *y, const float *z, const double *state, const double *x_ref,
+                     const int32_t *status, int16_t *res_y, int16_t *res_z, double *raw_y, double *raw_z) {
+  if (nt < 0 || nc < 0 || !off || off[0] != 0 || off[nt] != nc) return -1;
+  for (int64_t t = 0; t < nt; ++t)
+    if (off[t + 1] < off[t]) return -1;
+  for (int64_t t = 0; t < nt; ++t) {
+    for (int64_t k = off[t]; k < off[t + 1]; ++k) {
+      double qy = NAN, qz = NAN;
+      if (status[t] == ST_OK) {
+        double pn[5], F[25];
+        /* no |sinphi| limit short of 1: a reachable plane is always encoded */
+        if (orc_propagate(state + 5 * t, x_ref[t], (double)x[k], bz, 1.0, pn, F) == ST_OK) {
+          qy = ((double)y[k] - pn[0]) / step_y;
+          qz = ((double)z[k] - pn[1]) / step_z;
+        }
+      }
+      res_y[k] = orc_code(qy);
+      res_z[k] = orc_code(qz);
+      if (raw_y) raw_y[k] = qy;
+      if (raw_z) raw_z[k] = qz;
+    }
+  }
+  return 0;
+}
+

@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
         ("restart_scale", ctypes.c_float), ("min_clusters", ctypes.c_int32), ("n_rows", ctypes.c_int32),
         ("row_x0_cm", ctypes.c_float), ("row_pitch_cm", ctypes.c_float), ("hbm_budget_bytes", ctypes.c_uint64),
         ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-        ("blocks_per_sm", ctypes.c_int32), ("sort_tracks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("blocks_per_sm", ctypes.c_int32), ("sort_tracks", ctypes.c_int32), ("res_step_y_cm", ctypes.c_float),
+        ("res_step_z_cm", ctypes.c_float), ("reserved", ctypes.c_int32 * 5),
         ("host_chunk_clusters", ctypes.c_int64),
     ]
 
@@ -61,7 +62,8 @@ class _Result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("x_ref", ctypes.c_void_p),
                 ("chi2", ctypes.c_void_p), ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p),
                 ("accept", ctypes.c_void_p), ("mem", ctypes.c_int32), ("chi2_out_cluster", ctypes.c_void_p),
-                ("chi2_in_cluster", ctypes.c_void_p), ("restart_state", ctypes.c_void_p)]
+                ("chi2_in_cluster", ctypes.c_void_p), ("restart_state", ctypes.c_void_p), ("res_y", ctypes.c_void_p),
+                ("res_z", ctypes.c_void_p)]
 
 
 class _Timing(ctypes.Structure):
@@ -199,33 +201,40 @@ def _frame_struct(frame) -> tuple:
     return f, mem, nt, nc
 
 
-def alloc_result(n_tracks: int, n_clusters: int, device=None, pinned: bool = False) -> dict:
-    """Result buffers: torch tensors on ``device`` (CUDA) or numpy arrays on the host."""
-    if device is not None:
+def alloc_result(n_tracks: int, n_clusters: int, device=None, pinned: bool = False, residuals: bool = False) -> dict:
+    """Result buffers: torch tensors on ``device`` (CUDA) or numpy arrays on the
+    host (pinned torch tensors with ``pinned``).  ``residuals`` adds the int16
+    track-model compression residual codes ``res_y``, ``res_z``."""
+    if device is not None or pinned:
         import torch
-        mk = lambda shape, dt: torch.empty(shape, dtype=dt, device=device)  # noqa: E731
-        return dict(state=mk((n_tracks, 5), torch.float32), cov=mk((n_tracks, 15), torch.float32),
-                    x_ref=mk((n_tracks,), torch.float32), chi2=mk((n_tracks,), torch.float64),
-                    ndf=mk((n_tracks,), torch.int32), status=mk((n_tracks,), torch.int32),
-                    accept=mk((n_clusters,), torch.uint8))
-    if pinned:
-        import torch
-        mk = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True)  # noqa: E731
-        return dict(state=mk((n_tracks, 5), torch.float32), cov=mk((n_tracks, 15), torch.float32),
-                    x_ref=mk((n_tracks,), torch.float32), chi2=mk((n_tracks,), torch.float64),
-                    ndf=mk((n_tracks,), torch.int32), status=mk((n_tracks,), torch.int32),
-                    accept=mk((n_clusters,), torch.uint8))
-    return dict(state=np.empty((n_tracks, 5), np.float32), cov=np.empty((n_tracks, 15), np.float32),
-                x_ref=np.empty(n_tracks, np.float32), chi2=np.empty(n_tracks, np.float64),
-                ndf=np.empty(n_tracks, np.int32), status=np.empty(n_tracks, np.int32),
-                accept=np.empty(n_clusters, np.uint8))
+        kw = dict(device=device) if device is not None else dict(pin_memory=True)
+        mk = lambda shape, dt: torch.empty(shape, dtype=dt, **kw)  # noqa: E731
+        out = dict(state=mk((n_tracks, 5), torch.float32), cov=mk((n_tracks, 15), torch.float32),
+                   x_ref=mk((n_tracks,), torch.float32), chi2=mk((n_tracks,), torch.float64),
+                   ndf=mk((n_tracks,), torch.int32), status=mk((n_tracks,), torch.int32),
+                   accept=mk((n_clusters,), torch.uint8))
+        if residuals:
+            out.update(res_y=mk((n_clusters,), torch.int16), res_z=mk((n_clusters,), torch.int16))
+        return out
+    out = dict(state=np.empty((n_tracks, 5), np.float32), cov=np.empty((n_tracks, 15), np.float32),
+               x_ref=np.empty(n_tracks, np.float32), chi2=np.empty(n_tracks, np.float64),
+               ndf=np.empty(n_tracks, np.int32), status=np.empty(n_tracks, np.int32),
+               accept=np.empty(n_clusters, np.uint8))
+    if residuals:
+        out.update(res_y=np.empty(n_clusters, np.int16), res_z=np.empty(n_clusters, np.int16))
+    return out
 
 
 def _result_struct(res: dict) -> tuple:
     names = ("state", "cov", "x_ref", "chi2", "ndf", "status", "accept")
     arrs = [res[k] for k in names]
     mem = _mem_of(arrs)
-    extra = [_ptr(res.get(k)) for k in ("chi2_out_cluster", "chi2_in_cluster", "restart_state")]
+    extra = [_ptr(res.get(k)) for k in ("chi2_out_cluster", "chi2_in_cluster", "restart_state", "res_y", "res_z")]
+    for k in ("res_y", "res_z"):
+        if res.get(k) is not None:
+            dt = str(res[k].dtype).replace("torch.", "")
+            if dt != "int16":
+                raise TypeError(f"{k} must be int16, got {dt}")
     return _Result(*[_ptr(a) for a in arrs], mem, *extra), mem
 
 
@@ -369,7 +378,8 @@ class EventViews:
             self.frames.append(_Frame(t1 - t0, c1 - c0, rb + 8 * (t0 + e), fs.x + 4 * c0, fs.y + 4 * c0,
                                       fs.z + 4 * c0, fs.sy2 + 4 * c0, fs.sz2 + 4 * c0, fs.row + c0, 0, MEM_DEVICE))
             self.results.append(_Result(rs.state + 20 * t0, rs.cov + 60 * t0, rs.x_ref + 4 * t0, rs.chi2 + 8 * t0,
-                                        rs.ndf + 4 * t0, rs.status + 4 * t0, rs.accept + c0, MEM_DEVICE, 0, 0, 0))
+                                        rs.ndf + 4 * t0, rs.status + 4 * t0, rs.accept + c0, MEM_DEVICE, 0, 0, 0,
+                                        rs.res_y + 2 * c0 if rs.res_y else 0, rs.res_z + 2 * c0 if rs.res_z else 0))
 
     def __len__(self) -> int:
         return len(self.frames)

@@ -568,6 +568,59 @@ __device__ __forceinline__ Clu read_staged(const float *stg, int lk, uint32_t ro
   return c;
 }
 
+// ---------------------------------------------------------------------------
+// Track-model compression residuals (Sec. 5: TPC clusters are stored as
+// residuals to their track instead of absolute coordinates).  The fitted
+// helix (state at x0, no scattering) is evaluated at each cluster's x in one
+// exact step of the chord form; the residual is quantised to an int16 code.
+// ---------------------------------------------------------------------------
+// (y, z) of the helix through (y0, z0) at x0 with sinphi s0, tanlambda tl and
+// curvature C, at x0 + dx; false if the helix does not reach that plane.
+// Correctly rounded division and square roots: this pass is off the hot loop.
+__device__ __forceinline__ bool helix_at(float y0, float z0, float s0, float tl, float C, float dx, float &y,
+                                         float &z) {
+  const float s2 = fmaf(C, dx, s0);
+  if (!(fabsf(s0) < 1.0f) || !(fabsf(s2) < 1.0f)) return false;
+  const float c1 = sqrtf(fmaf(-s0, s0, 1.0f)), c2 = sqrtf(fmaf(-s2, s2, 1.0f));
+  const float Tn = (s0 + s2) / (c1 + c2);  // tangent of the chord direction
+  const float L = dx * sqrtf(fmaf(Tn, Tn, 1.0f));
+  const float u = 0.5f * C * L;            // sine of half the turning angle
+  float g;                                 // arc / chord = asin(u) / u
+  if (fabsf(u) < 0.1f) {
+    const float u2 = u * u;
+    g = 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
+  } else {
+    g = asinf(u) / u;
+  }
+  y = fmaf(dx, Tn, y0);
+  z = fmaf(tl, L * g, z0);
+  return isfinite(y) && isfinite(z);
+}
+
+// Residual in code units -> int16 code: round half to even, clipped to
+// +-32767; -32768 (not encoded) for a non-finite residual.
+__device__ __forceinline__ int16_t res_code(float r, float inv_step) {
+  const float q = r * inv_step;
+  if (isnan(q)) return (int16_t)-32768;
+  if (!(fabsf(q) < 32767.5f)) return q > 0.0f ? (int16_t)32767 : (int16_t)-32767;
+  return (int16_t)__float2int_rn(q);
+}
+
+__device__ void residual_codes(const FitArgs &A, int64_t a, int64_t e, bool ok, float y0, float z0, float s0,
+                               float tl, float w, float x0) {
+  const float C = A.b * w;
+  for (int64_t k = a; k < e; ++k) {
+    int16_t cy = -32768, cz = -32768;
+    float yt, zt;
+    if (ok && helix_at(y0, z0, s0, tl, C, A.x[k] - x0, yt, zt)) {
+      cy = res_code(A.y[k] - yt, A.res_inv_step_y);
+      cz = res_code(A.z[k] - zt, A.res_inv_step_z);
+    }
+    if (A.res_y) A.res_y[k] = cy;
+    if (A.res_z) A.res_z[k] = cz;
+  }
+}
+
 template <int BLOCK>
 __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
@@ -760,6 +813,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       for (int64_t k = a; k < e - done; ++k) A.chi2_in_c[k] = __longlong_as_double(0x7ff8000000000000ll);
     if (A.chi2_out_c)
       for (int64_t k = a + out_done; k < e; ++k) A.chi2_out_c[k] = __longlong_as_double(0x7ff8000000000000ll);
+    if (A.res_y || A.res_z)
+      residual_codes(A, a, e, st == ST_OK, T.ya + T.dy, T.za + T.dz, T.snp(), T.tl(), T.w(), xref);
   }
   A.x_ref[t] = xref;
   float *ps = A.state + 5 * t;

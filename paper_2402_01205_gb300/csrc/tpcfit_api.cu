@@ -139,6 +139,7 @@ struct Stage {
   double *chi2 = nullptr;
   int32_t *ndf = nullptr, *status = nullptr;
   uint8_t *accept = nullptr;
+  int16_t *res_y = nullptr, *res_z = nullptr;
   cudaEvent_t free_ev = nullptr;  // recorded after the results left this stage
   int ensure(int64_t nt, int64_t nc) {
     size_t o = 0;
@@ -156,6 +157,8 @@ struct Stage {
     size_t nd_o = o; o += align256((size_t)nt * 4);
     size_t ss_o = o; o += align256((size_t)nt * 4);
     size_t ac_o = o; o += align256((size_t)nc);
+    size_t ry_o = o; o += align256((size_t)nc * 2);
+    size_t rz_o = o; o += align256((size_t)nc * 2);
     int rc = buf.ensure(o);
     if (rc) return rc;
     off = buf.as<int64_t>(off_o);
@@ -164,6 +167,8 @@ struct Stage {
     state = buf.as<float>(st_o); cov = buf.as<float>(cv_o); xref = buf.as<float>(xr_o);
     chi2 = buf.as<double>(c2_o); ndf = buf.as<int32_t>(nd_o); status = buf.as<int32_t>(ss_o);
     accept = buf.as<uint8_t>(ac_o);
+    res_y = buf.as<int16_t>(ry_o);
+    res_z = buf.as<int16_t>(rz_o);
     return TPCFIT_OK;
   }
 };
@@ -248,6 +253,8 @@ extern "C" void tpcfit_default_config(tpcfit_config *c) {
   c->block_threads = 0;
   c->blocks_per_sm = 0;
   c->sort_tracks = 1;
+  c->res_step_y_cm = 0.01f;
+  c->res_step_z_cm = 0.01f;
   c->host_chunk_clusters = (int64_t)16 << 20;
 }
 
@@ -263,6 +270,7 @@ static int check_config(const tpcfit_config &c) {
   if (c.block_threads != 0 && c.block_threads != 128 && c.block_threads != 256)
     return fail(TPCFIT_E_INVAL, "block_threads must be 0, 128 or 256");
   if (c.blocks_per_sm < 0) return fail(TPCFIT_E_INVAL, "blocks_per_sm < 0");
+  if (!(c.res_step_y_cm > 0.0f) || !(c.res_step_z_cm > 0.0f)) return fail(TPCFIT_E_INVAL, "residual steps must be > 0");
   return TPCFIT_OK;
 }
 
@@ -369,6 +377,10 @@ FitArgs make_args(tpcfit_handle *h, const tpcfit_frame *f, const tpcfit_result *
   a.chi2_out_c = r->chi2_out_cluster;
   a.chi2_in_c = r->chi2_in_cluster;
   a.restart_state = r->restart_state;
+  a.res_y = r->res_y;
+  a.res_z = r->res_z;
+  a.res_inv_step_y = 1.0f / c.res_step_y_cm;
+  a.res_inv_step_z = 1.0f / c.res_step_z_cm;
   a.seed = s.seed;
   a.perm = c.sort_tracks ? s.perm : nullptr;
   a.hist = s.hist;
@@ -700,6 +712,8 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     cr.restart_state = nullptr;
     cr.state = S.state; cr.cov = S.cov; cr.x_ref = S.xref; cr.chi2 = S.chi2; cr.ndf = S.ndf;
     cr.status = S.status; cr.accept = S.accept;
+    cr.res_y = r->res_y ? S.res_y : nullptr;
+    cr.res_z = r->res_z ? S.res_z : nullptr;
     FitArgs a = make_args(h, &cf, &cr, h->scratch, c0);
     if ((rc = run_sequence(h, a, h->stream, h->scratch, nchunks == 1, &launches))) return rc;
     CU(cudaEventRecord(h->ev_fit[ci & 1], h->stream));
@@ -712,6 +726,8 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     CU(cudaMemcpyAsync(r->ndf + t0, S.ndf, (size_t)cnt * 4, dk, h->d2h));
     CU(cudaMemcpyAsync(r->status + t0, S.status, (size_t)cnt * 4, dk, h->d2h));
     if (ncl > 0) CU(cudaMemcpyAsync(r->accept + c0, S.accept, (size_t)ncl, dk, h->d2h));
+    if (ncl > 0 && r->res_y) CU(cudaMemcpyAsync(r->res_y + c0, S.res_y, (size_t)ncl * 2, dk, h->d2h));
+    if (ncl > 0 && r->res_z) CU(cudaMemcpyAsync(r->res_z + c0, S.res_z, (size_t)ncl * 2, dk, h->d2h));
     CU(cudaEventRecord(S.free_ev, h->d2h));
   }
   CU(cudaMemcpyAsync(h->h_err, h->scratch.err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));

@@ -23,6 +23,8 @@ struct FitArgs {
   uint8_t *accept;
   double *chi2_out_c, *chi2_in_c;  // optional per-cluster chi2 (nullptr: not written)
   float *restart_state;            // optional inward restart state (nullptr: not written)
+  int16_t *res_y, *res_z;          // optional residual codes (nullptr: not written)
+  float res_inv_step_y, res_inv_step_z;
   // scratch (device)
   float *seed;                   // n_tracks*5
   int32_t *perm;                 // n_tracks (sorted order), or nullptr for frame order

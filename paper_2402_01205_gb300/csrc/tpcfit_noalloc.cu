@@ -124,6 +124,7 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   a.chi2_out_c = r->chi2_out_cluster;
   a.chi2_in_c = r->chi2_in_cluster;
   a.restart_state = r->restart_state;
+  a.res_y = a.res_z = nullptr;  // residuals are not written by this entry point
   a.hist = reinterpret_cast<uint32_t *>(sc + kHistOff);
   a.work = reinterpret_cast<unsigned long long *>(sc + kWorkOff);
   a.frame_error = reinterpret_cast<int32_t *>(sc + kErrOff);

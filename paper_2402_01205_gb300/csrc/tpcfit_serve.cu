@@ -63,7 +63,7 @@ size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t frame_bytes(int64_t nt, int64_t nc) {
   return a256((size_t)(nt + 1) * 8) + 5 * a256((size_t)nc * 4) + 2 * a256((size_t)nc) + a256((size_t)nt * 20) +
          a256((size_t)nt * 60) + a256((size_t)nt * 4) + a256((size_t)nt * 8) + 2 * a256((size_t)nt * 4) +
-         serve_scratch_bytes(nt);
+         2 * a256((size_t)nc * 2) + serve_scratch_bytes(nt);
 }
 
 struct Request {
@@ -112,7 +112,8 @@ struct ServeState {
 };
 
 // Carve one allocation into the frame and result arrays of a resident frame.
-static void carve(void *mem, int64_t nt, int64_t nc, tpcfit_frame *df, tpcfit_result *dr, void **scratch) {
+static void carve(void *mem, int64_t nt, int64_t nc, bool want_ry, bool want_rz, tpcfit_frame *df,
+                  tpcfit_result *dr, void **scratch) {
   char *p = (char *)mem;
   auto take = [&](size_t b) {
     char *q = p;
@@ -137,6 +138,9 @@ static void carve(void *mem, int64_t nt, int64_t nc, tpcfit_frame *df, tpcfit_re
   dr->ndf = (int32_t *)take((size_t)nt * 4);
   dr->status = (int32_t *)take((size_t)nt * 4);
   dr->accept = (uint8_t *)take((size_t)nc);
+  int16_t *ry = (int16_t *)take((size_t)nc * 2), *rz = (int16_t *)take((size_t)nc * 2);
+  dr->res_y = want_ry ? ry : nullptr;
+  dr->res_z = want_rz ? rz : nullptr;
   dr->mem = TPCFIT_MEM_DEVICE;
   dr->chi2_out_cluster = dr->chi2_in_cluster = nullptr;
   dr->restart_state = nullptr;
@@ -164,7 +168,7 @@ static bool launch(ServeState *S, const Part &P, int si) {
   tpcfit_frame df;
   tpcfit_result dr;
   void *scratch = nullptr;
-  carve(L.mem, nt, nc, &df, &dr, &scratch);
+  carve(L.mem, nt, nc, R.res.res_y != nullptr, R.res.res_z != nullptr, &df, &dr, &scratch);
   bool ok = true;
   auto cp = [&](const void *dst, const void *src, size_t b, cudaMemcpyKind k) {
     if (!b || !ok) return;
@@ -192,6 +196,8 @@ static bool launch(ServeState *S, const Part &P, int si) {
   cp(O.ndf + P.t0, dr.ndf, (size_t)nt * 4, cudaMemcpyDeviceToHost);
   cp(O.status + P.t0, dr.status, (size_t)nt * 4, cudaMemcpyDeviceToHost);
   cp(O.accept + c0, dr.accept, (size_t)nc, cudaMemcpyDeviceToHost);
+  if (dr.res_y) cp(O.res_y + c0, dr.res_y, (size_t)nc * 2, cudaMemcpyDeviceToHost);
+  if (dr.res_z) cp(O.res_z + c0, dr.res_z, (size_t)nc * 2, cudaMemcpyDeviceToHost);
   if (!ok) cudaGetLastError();
   L.failed = !ok;
   cudaFreeAsync(L.mem, L.stream);  // released in stream order after the copies

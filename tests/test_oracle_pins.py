@@ -343,3 +343,60 @@ def test_empty_frame_and_thread_invariance():
     b = oracle.fit(f, _cfg(), threads=7)
     for k in ("state", "cov", "chi2", "ndf", "status", "accept"):
         assert np.array_equal(a[k], b[k])
+
+
+# ---------------------------------------------------------------------------
+# Track-model compression residuals (Sec. 5 reading: cluster minus the fitted
+# helix at the cluster's x, quantised to int16 codes of a fixed step)
+# ---------------------------------------------------------------------------
+def test_residual_codes_decode_within_half_a_step():
+    """Decoding with an independent helix (the angle-form transport of the LSQ
+    fitter) restores every encoded cluster to within half a step."""
+    f = tpcgen.generate("detector50k", n_tracks=300, seed=11)
+    r = oracle.fit(f)
+    step = (0.01, 0.02)
+    q = oracle.residuals(f, r, step=step)
+    n_checked = 0
+    for t in range(f.n_tracks):
+        a, b = f.offsets[t], f.offsets[t + 1]
+        if r["status"][t] != 0:
+            assert np.all(q["res_y"][a:b] == -32768) and np.all(q["res_z"][a:b] == -32768)
+            continue
+        for k in range(a, b):
+            p = lsq.transport(r["state"][t], r["x_ref"][t], float(f.x[k]), 0.5)
+            dy = float(f.y[k]) - (p[0] + q["res_y"][k] * step[0])
+            dz = float(f.z[k]) - (p[1] + q["res_z"][k] * step[1])
+            assert abs(dy) <= 0.5 * step[0] + 1e-9 and abs(dz) <= 0.5 * step[1] + 1e-9, (t, k, dy, dz)
+            assert abs(q["raw_y"][k] - (float(f.y[k]) - p[0]) / step[0]) < 1e-6
+            n_checked += 1
+    assert n_checked > 20_000
+
+
+def test_residuals_vanish_on_noise_free_helices():
+    """No noise, no scattering: the fitted helix is the true one, every code is 0."""
+    f = tpcgen.generate("sector1k", n_tracks=200, sigma_y=0.0, sigma_z=0.0, seed=2)
+    r = oracle.fit(f, oracle.FitConfig(xx0=0.0))
+    assert np.all(r["status"] == 0)
+    q = oracle.residuals(f, r)
+    assert np.all(q["res_y"] == 0) and np.all(q["res_z"] == 0)
+    assert np.abs(q["raw_y"]).max() < 1e-3 and np.abs(q["raw_z"]).max() < 1e-3
+
+
+def test_residual_codes_clip_and_round_half_even():
+    f = tpcgen.generate("detector50k", n_tracks=50, seed=12)
+    r = oracle.fit(f)
+    q = oracle.residuals(f, r, step=(1e-6, 1e-6))  # residuals of ~0.1 cm are far beyond 32767 steps
+    ok = np.repeat(r["status"] == 0, np.diff(f.offsets))
+    big = ok & (np.abs(q["raw_y"]) >= 32767.5)
+    assert big.sum() > 100 and np.all(np.abs(q["res_y"][big]) == 32767)
+    assert np.all(np.sign(q["res_y"][big]) == np.sign(q["raw_y"][big]))
+    # half-way residuals: at the track's first cluster (x = x_ref, no transport)
+    # the prediction is the state itself; place it 2.5 and -3.5 binary steps off
+    t = int(np.nonzero(r["status"] == 0)[0][0])
+    k = int(f.offsets[t])
+    step = 2.0 ** -6
+    for want, code_y in ((2.5, 2), (-3.5, -4), (0.5, 0), (-0.5, 0), (1.5, 2)):
+        rr = {kk: (v.copy() if isinstance(v, np.ndarray) else v) for kk, v in r.items()}
+        rr["state"][t, 0] = float(f.y[k]) - want * step  # exact in binary64
+        qq = oracle.residuals(f, rr, step=(step, step))
+        assert qq["raw_y"][k] == want and qq["res_y"][k] == code_y, (want, qq["raw_y"][k], qq["res_y"][k])
