@@ -1,0 +1,91 @@
+"""Pins of the rANS reference coder (oracle/rans.py) against what the
+mathematics fixes: a hand-derived example, exact round trips, the size the
+model's cross-entropy predicts, the normalisation's invariants, and that a
+damaged stream does not decode to its input."""
+import os
+import struct
+
+import numpy as np
+import pytest
+
+from oracle import rans
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rans_hand_example.txt")
+
+
+def test_hand_derived_example():
+    want = {}
+    for ln in open(GOLDEN):
+        if ln.strip() and not ln.startswith("#"):
+            k, *v = ln.split()
+            want.setdefault(k, []).append([int(t) for t in v])
+    p = rans.parse(rans.encode(np.array([0, 0, 1], np.int16)))
+    for s, fq in want["freq"]:
+        assert p["f"][s] == fq
+    assert p["f"].sum() == rans.M and np.count_nonzero(p["f"]) == 2
+    states = struct.unpack_from("<32I", p["payload"], 0)
+    for lane, x in want["state"]:
+        assert states[lane] == x
+    assert all(x == rans.L for x in states[3:])
+    assert len(p["payload"]) == 128 + 2 * want["words"][0][0] and len(p["esc"]) == want["escapes"][0][0]
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 127, 128, 129, 1000])
+def test_round_trip_partial_segments(n):
+    rng = np.random.default_rng(n)
+    c = np.round(rng.normal(0, 20, n)).astype(np.int16)
+    c[rng.random(n) < 0.02] = -32768
+    blob = rans.encode(c, seg=128)
+    assert np.array_equal(rans.decode(blob), c)
+
+
+def test_round_trip_escapes_extremes_and_one_symbol():
+    c = np.array([32767, -32767, -32768, 255, -255, 256, -256, 0] * 50, np.int16)
+    assert np.array_equal(rans.decode(rans.encode(c, seg=64)), c)
+    p = rans.parse(rans.encode(c, seg=64))
+    assert len(p["esc"]) == 5 * 50 and set(p["esc"]) == {32767, -32767, -32768, 256, -256}
+    one = np.full(5000, 7, np.int16)  # a single symbol: f = M, no words at all
+    p1 = rans.parse(rans.encode(one, seg=1024))
+    assert p1["f"][7 + 255] == rans.M and len(p1["payload"]) == 128 * 5
+    assert np.array_equal(rans.decode(rans.encode(one, seg=1024)), one)
+
+
+def test_size_matches_cross_entropy():
+    rng = np.random.default_rng(3)
+    c = np.round(rng.laplace(0, 6, 60_000)).astype(np.int16)
+    blob = rans.encode(c, seg=4096)
+    p = rans.parse(blob)
+    bits = 0.0
+    lanes = 0
+    for j in range(p["n_seg"]):
+        base, end = int(p["seg_off"][j]), int(p["seg_off"][j + 1])
+        st = struct.unpack_from("<32I", p["payload"], base)
+        active = min(32, p["n"] - j * p["seg"])
+        bits += 16 * (end - base - 128) / 2 + sum(np.log2(x) for x in st[:active]) - 16 * active
+        lanes += active
+    h = rans.cross_entropy_bits(c)
+    # rANS codes each symbol at log2(M/f) up to a relative error of order M/L per step
+    assert abs(bits - h) < 0.01 * len(c) + lanes, (bits, h)
+
+
+def test_normalisation_invariants():
+    for counts in (np.ones(512, np.int64), np.r_[10**6, np.ones(511, np.int64)], np.r_[3, 0, 0, 5, np.zeros(508)]):
+        f = rans.normalise(counts)
+        assert f.sum() == rans.M and np.all((f > 0) == (counts > 0))
+    assert np.all(rans.normalise(np.r_[np.ones(4), np.zeros(508)]) [:4] == 1024)
+    assert np.all(rans.normalise(np.ones(512)) == 8)
+    assert rans.normalise(np.zeros(512)).sum() == 0
+
+
+def test_damaged_stream_does_not_decode_to_the_input():
+    rng = np.random.default_rng(5)
+    c = np.round(rng.normal(0, 10, 4000)).astype(np.int16)
+    blob = bytearray(rans.encode(c, seg=1024))
+    p = rans.parse(bytes(blob))
+    off = len(blob) - 2 * len(p["esc"]) - len(p["payload"]) + 128 + 40  # a word of segment 0
+    blob[off] ^= 0x5A
+    try:
+        out = rans.decode(bytes(blob))
+    except ValueError:
+        return
+    assert not np.array_equal(out, c)
