@@ -640,6 +640,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-tracks", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rans-steps", type=int, default=5, help="pbpb2m: timed rANS encode/decode calls per stream")
     ap.add_argument("--block-threads", type=int, default=0, help="pbpb2m: fit kernel block size (0 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="pbpb2m: resident fit blocks per SM (0 = default)")
     ap.add_argument("--n-events", type=int, default=4096, help="events4096: number of events (testing)")
@@ -741,6 +742,39 @@ def main():
                       "ms_per_step": ms_res / n_res, "fit_ms": tm_res["fit_ms_sum"] / max(tm_res["n_timed"], 1),
                       "extra_bytes_per_cluster": 4,
                       "what": "int16 residual codes of every cluster against the fitted helix (y and z)"}
+    # rANS entropy coding of the residual codes (both streams), blocking calls timed whole
+    codec = None
+    if args.rans_steps > 0:
+        peaks, _ = measured_peaks()
+        enc_s, dec_s, sizes = [], [], []
+        outs = {}
+        for k in ("res_y", "res_z"):
+            outs[k] = fx.rans_encode(res_r[k], stream=stream)
+            fx.rans_decode(outs[k][0], outs[k][1], nc, stream=stream)
+        dec = torch.empty(nc, dtype=torch.int16, device=torch.device("cuda", local))
+        for _ in range(args.rans_steps):
+            for k in ("res_y", "res_z"):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                o, sz = fx.rans_encode(res_r[k], out=outs[k][0], stream=stream)
+                enc_s.append(time.perf_counter() - t0)
+                t0 = time.perf_counter()
+                fx.rans_decode(o, sz, nc, out=dec, stream=stream)
+                dec_s.append(time.perf_counter() - t0)
+                sizes.append(sz)
+        ok_rt = bool(torch.equal(dec, res_r["res_z"]))
+        e_ms, d_ms = 1e3 * statistics.median(enc_s), 1e3 * statistics.median(dec_s)
+        mean_size = float(np.mean(sizes))
+        dec_bytes = mean_size + 2 * nc  # container read + codes written
+        codec = {"encode_gcodes_s": nc / (e_ms * 1e-3) / 1e9, "decode_gcodes_s": nc / (d_ms * 1e-3) / 1e9,
+                 "encode_ms": e_ms, "decode_ms": d_ms, "codes_per_stream": nc, "streams": 2,
+                 "bits_per_code": 8 * mean_size / nc, "raw_bits_per_code": 16,
+                 "decode_hbm": {"achieved_gbs": dec_bytes / (d_ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                                "frac": dec_bytes / (d_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                "bytes": "container read + 2 B per code written"},
+                 "round_trip_identical": ok_rt, "calls": "tpcfit_rans_encode / tpcfit_rans_decode, blocking, "
+                 "median of %d calls per stream" % args.rans_steps}
+        del outs, dec
     del res_r
     # end to end through the C-ABI: pinned host frame in, pinned host results out
     e2e = None
@@ -782,6 +816,7 @@ def main():
             "tracks_per_s": nt * ws * args.steps / (ms * 1e-3),
             "roofline": roofline,
             "with_residuals": with_residuals,
+            "rans": codec,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(tm["kernel_launches"]) * args.steps,

@@ -24,7 +24,7 @@ from . import _build
 __all__ = ["TpcfitError", "Config", "default_config", "create", "destroy", "fit", "fit_async", "sync", "submit",
            "poll", "wait", "last_timing", "reset_timing", "probe_fma_rates", "strerror", "now", "Fitter",
            "library_path", "alloc_result", "STATUS_NAMES", "Batch", "EventViews", "batch_create", "batch_launch",
-           "batch_sync", "batch_destroy", "fit_noalloc"]
+           "batch_sync", "batch_destroy", "fit_noalloc", "rans_bound", "rans_encode", "rans_decode"]
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_NOTFOUND, E_NODEV = 0, -1, -2, -3, -4, -5, -6, -7
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -110,6 +110,15 @@ def _load():
     lib.tpcfit_last_error_message.restype = ctypes.c_char_p
     lib.tpcfit_now.argtypes = []
     lib.tpcfit_now.restype = ctypes.c_double
+    lib.tpcfit_rans_bound.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    lib.tpcfit_rans_bound.restype = ctypes.c_int64
+    lib.tpcfit_rans_encode.argtypes = [H, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    lib.tpcfit_rans_decode.argtypes = [H, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_void_p]
+    lib.tpcfit_fit_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_Frame), ctypes.POINTER(_Result),
+                                       ctypes.c_void_p]
+    lib.tpcfit_fit_noalloc.restype = ctypes.c_int
     lib.tpcfit_batch_create.argtypes = [H, ctypes.POINTER(_Frame), ctypes.POINTER(_Result), ctypes.POINTER(H)]
     lib.tpcfit_batch_launch.argtypes = [H, ctypes.c_void_p]
     lib.tpcfit_batch_sync.argtypes = [H, ctypes.c_double]
@@ -117,7 +126,7 @@ def _load():
     for fn in ("tpcfit_create", "tpcfit_fit", "tpcfit_fit_async", "tpcfit_sync", "tpcfit_submit", "tpcfit_poll",
                "tpcfit_wait", "tpcfit_last_timing", "tpcfit_reset_timing", "tpcfit_destroy",
                "tpcfit_probe_fma_rates", "tpcfit_batch_create", "tpcfit_batch_launch", "tpcfit_batch_sync",
-               "tpcfit_batch_destroy"):
+               "tpcfit_batch_destroy", "tpcfit_rans_encode", "tpcfit_rans_decode"):
         getattr(lib, fn).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -348,6 +357,38 @@ def batch_destroy(batch: int) -> None:
     _check(_load().tpcfit_batch_destroy(batch))
 
 
+def rans_bound(n: int, segment_symbols: int = 0) -> int:
+    """Largest rANS container size (bytes) for n codes."""
+    b = _load().tpcfit_rans_bound(n, segment_symbols)
+    if b < 0:
+        raise TpcfitError(E_INVAL, "bad rANS sizes")
+    return b
+
+
+def rans_encode(handle: int, codes, segment_symbols: int = 0, out=None, stream=None):
+    """Entropy-code a CUDA int16 tensor; returns (uint8 CUDA tensor, container bytes)."""
+    import torch
+    if not (_is_torch(codes) and codes.is_cuda and codes.dtype == torch.int16 and codes.is_contiguous()):
+        raise TypeError("codes must be a contiguous CUDA int16 tensor")
+    n = int(codes.numel())
+    if out is None:
+        out = torch.empty(rans_bound(n, segment_symbols), dtype=torch.uint8, device=codes.device)
+    size = ctypes.c_int64()
+    _check(_load().tpcfit_rans_encode(handle, codes.data_ptr() if n else None, n, segment_symbols, out.data_ptr(),
+                                      out.numel(), ctypes.byref(size), getattr(stream, "cuda_stream", stream)))
+    return out, size.value
+
+
+def rans_decode(handle: int, blob, size: int, n: int, out=None, stream=None):
+    """Decode a container held in a CUDA uint8 tensor into n int16 codes (CUDA tensor)."""
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.int16, device=blob.device)
+    _check(_load().tpcfit_rans_decode(handle, blob.data_ptr(), size, out.data_ptr() if n else None, n,
+                                      getattr(stream, "cuda_stream", stream)))
+    return out
+
+
 class EventViews:
     """Per-event frames and results inside one concatenated device frame.
 
@@ -474,6 +515,12 @@ class Fitter:
 
     def timing(self) -> dict:
         return last_timing(self.handle)
+
+    def rans_encode(self, codes, segment_symbols: int = 0, out=None, stream=None):
+        return rans_encode(self.handle, codes, segment_symbols, out, stream)
+
+    def rans_decode(self, blob, size: int, n: int, out=None, stream=None):
+        return rans_decode(self.handle, blob, size, n, out, stream)
 
     def reset_timing(self) -> None:
         reset_timing(self.handle)

@@ -191,6 +191,7 @@ struct tpcfit_handle {
   float *d_rowx = nullptr;
   Scratch scratch;
   Stage stage[2];
+  DevBuf rans_buf;           // rANS codec scratch
   int32_t *h_err = nullptr;  // pinned
   // ring of event quadruples around prepare / sort / fit of timed calls
   static constexpr int kRing = 64;
@@ -220,6 +221,15 @@ size_t serve_scratch_bytes(int64_t n_tracks) { return Scratch::bytes_for(n_track
 int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
                        int64_t off_base, cudaStream_t st, const int32_t **err_dev);
 int handle_device(tpcfit_handle *h) { return h->device; }
+// exposed to the rANS codec (tpcfit_rans.cu)
+int handle_rans_scratch(tpcfit_handle *h, size_t bytes, void **p) {
+  int rc = h->rans_buf.ensure(bytes);
+  if (rc) return rc;
+  *p = h->rans_buf.p;
+  return TPCFIT_OK;
+}
+int32_t *handle_pinned_word(tpcfit_handle *h) { return h->h_err; }
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
 const tpcfit_config &handle_config(tpcfit_handle *h) { return h->cfg; }
 ServeState *&handle_serve(tpcfit_handle *h) { return h->serve; }
 std::mutex &handle_mutex(tpcfit_handle *h) { return h->mu; }
@@ -340,6 +350,7 @@ extern "C" int tpcfit_destroy(tpcfit_handle *h) {
   if (h->h2d) cudaStreamSynchronize(h->h2d);
   if (h->d2h) cudaStreamSynchronize(h->d2h);
   h->scratch.buf.release();
+  h->rans_buf.release();
   for (auto &s : h->stage) {
     s.buf.release();
     if (s.free_ev) cudaEventDestroy(s.free_ev);

@@ -77,3 +77,14 @@ def test_struct_layout_matches_header(lib, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_binding_declares_the_signature_of_every_entry_point():
+    """ctypes passes undeclared arguments as C int: a pointer or an int64_t
+    would be truncated.  The binding must declare every entry point it can call."""
+    import paper_2402_01205_gb300 as T
+    lib = T._load()
+    missing = [n for n in sorted(_declared()) if getattr(lib, n).argtypes is None]
+    assert not missing, missing
+    for n in ("tpcfit_rans_bound", "tpcfit_now"):
+        assert getattr(lib, n).restype in (ctypes.c_int64, ctypes.c_double), n
