@@ -606,21 +606,6 @@ __device__ __forceinline__ int16_t res_code(float r, float inv_step) {
   return (int16_t)__float2int_rn(q);
 }
 
-__device__ void residual_codes(const FitArgs &A, int64_t a, int64_t e, bool ok, float y0, float z0, float s0,
-                               float tl, float w, float x0) {
-  const float C = A.b * w;
-  for (int64_t k = a; k < e; ++k) {
-    int16_t cy = -32768, cz = -32768;
-    float yt, zt;
-    if (ok && helix_at(y0, z0, s0, tl, C, A.x[k] - x0, yt, zt)) {
-      cy = res_code(A.y[k] - yt, A.res_inv_step_y);
-      cz = res_code(A.z[k] - zt, A.res_inv_step_z);
-    }
-    if (A.res_y) A.res_y[k] = cy;
-    if (A.res_z) A.res_z[k] = cz;
-  }
-}
-
 template <int BLOCK>
 __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
@@ -813,8 +798,6 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       for (int64_t k = a; k < e - done; ++k) A.chi2_in_c[k] = __longlong_as_double(0x7ff8000000000000ll);
     if (A.chi2_out_c)
       for (int64_t k = a + out_done; k < e; ++k) A.chi2_out_c[k] = __longlong_as_double(0x7ff8000000000000ll);
-    if (A.res_y || A.res_z)
-      residual_codes(A, a, e, st == ST_OK, T.ya + T.dy, T.za + T.dz, T.snp(), T.tl(), T.w(), xref);
   }
   A.x_ref[t] = xref;
   float *ps = A.state + 5 * t;
@@ -859,6 +842,59 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// k_residuals: track-model compression residual codes, after k_fit.  One warp
+// per track (grid-stride); the lanes take the track's clusters 32 at a time,
+// so the loads of x, y, z and the stores of the codes are coalesced.  Input:
+// the fitted state and x_ref that k_fit wrote.
+// ---------------------------------------------------------------------------
+constexpr int kResChunks = 5;  // 160 clusters: a whole track of 152 pad rows in one sweep
+
+__global__ void __launch_bounds__(256) k_residuals(FitArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < A.n_tracks; t += warps) {
+    const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
+    if (a < 0 || e < a || e > A.n_clusters) continue;  // malformed offsets: k_prepare reported the frame
+    const bool ok = A.status[t] == ST_OK;
+    float y0 = 0.f, z0 = 0.f, s0 = 0.f, tl = 0.f, w = 0.f, x0 = 0.f;
+    if (ok) {
+      const float *p = A.state + 5 * t;
+      y0 = p[0]; z0 = p[1]; s0 = p[2]; tl = p[3]; w = p[4];
+      x0 = A.x_ref[t];
+    }
+    const float C = A.b * w;
+    // up to 32 * kResChunks clusters per sweep: every load of the sweep is
+    // issued before the first residual is formed (one memory latency per track)
+    for (int64_t base = a; base < e; base += 32 * kResChunks) {
+      float xs[kResChunks], ys[kResChunks], zs[kResChunks];
+#pragma unroll
+      for (int q = 0; q < kResChunks; ++q) {
+        const int64_t k = base + q * 32 + lane;
+        xs[q] = ys[q] = zs[q] = 0.f;
+        if (k < e) {
+          xs[q] = A.x[k];
+          ys[q] = A.y[k];
+          zs[q] = A.z[k];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kResChunks; ++q) {
+        const int64_t k = base + q * 32 + lane;
+        if (k >= e) break;
+        int16_t cy = -32768, cz = -32768;
+        float yt, zt;
+        if (ok && helix_at(y0, z0, s0, tl, C, xs[q] - x0, yt, zt)) {
+          cy = res_code(ys[q] - yt, A.res_inv_step_y);
+          cz = res_code(zs[q] - zt, A.res_inv_step_z);
+        }
+        if (A.res_y) A.res_y[k] = cy;
+        if (A.res_z) A.res_z[k] = cz;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream) {
@@ -889,6 +925,17 @@ template <int BLOCK, int MINB> static cudaError_t set_fit_smem() {
   e = cudaFuncSetAttribute(k_fit<BLOCK, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem<BLOCK>());
   if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
+}
+
+cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream) {
+  if (a.n_tracks <= 0 || (!a.res_y && !a.res_z)) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (a.n_tracks + 7) / 8;  // 8 warps (tracks) per block in flight
+  const int64_t cap = (int64_t)sms * 8;
+  k_residuals<<<(unsigned)(want < cap ? want : cap), 256, 0, stream>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {

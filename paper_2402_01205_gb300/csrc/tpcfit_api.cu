@@ -461,6 +461,10 @@ int run_sequence(tpcfit_handle *h, const FitArgs &a, cudaStream_t st, Scratch &s
   if (timed) CU(cudaEventRecord(h->ring[slot].ev[2], st));
   CU(launch_fit(a, h->fit_grid, h->fit_block, st));
   l += 1;
+  if (a.res_y || a.res_z) {
+    CU(launch_residuals(a, st));
+    l += 1;
+  }
   if (timed) {
     CU(cudaEventRecord(h->ring[slot].ev[3], st));
     h->ring[slot].pending = true;
@@ -592,10 +596,11 @@ extern "C" int tpcfit_batch_create(tpcfit_handle *h, const tpcfit_frame *f, tpcf
   if ((e = cudaMemsetAsync(b->scratch.hist, 0, b->scratch.small_bytes, b->stream)) != cudaSuccess ||
       (e = launch_prepare(a, b->stream)) != cudaSuccess || (e = launch_sort(a, b->stream, &l)) != cudaSuccess ||
       (e = launch_fit(a, h->fit_grid, h->fit_block, b->stream)) != cudaSuccess ||
+      (e = launch_residuals(a, b->stream)) != cudaSuccess ||
       (e = cudaMemcpyAsync(b->h_err, b->scratch.err, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream)) !=
           cudaSuccess)
     return bail(fail(TPCFIT_E_CUDA, "capture: %s", cudaGetErrorString(e)));
-  if (f->n_tracks > 0) l += 2;  // prepare and fit
+  if (f->n_tracks > 0) l += 2 + ((r->res_y || r->res_z) ? 1 : 0);  // prepare, fit, residuals
   if ((e = cudaStreamEndCapture(b->stream, &b->graph)) != cudaSuccess)
     return bail(fail(TPCFIT_E_CUDA, "end capture: %s", cudaGetErrorString(e)));
   if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
@@ -832,8 +837,10 @@ extern "C" int tpcfit_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_res
   if (f->mem != TPCFIT_MEM_HOST || r->mem != TPCFIT_MEM_HOST)
     return fail(TPCFIT_E_INVAL, "tpcfit_submit takes host frames and host results");
   if ((rc = validate_host_offsets(f))) return rc;
-  if (!h->serve && (rc = serve_start(h))) return rc;
-  return serve_submit(h, f, r, ticket);
+  if (!h->serve && (rc = serve_start(h))) return fail(rc, "serving start-up failed");
+  rc = serve_submit(h, f, r, ticket);
+  if (rc == TPCFIT_E_NOMEM) return fail(rc, "frame larger than the whole HBM budget");
+  return rc;
 }
 
 extern "C" int tpcfit_poll(tpcfit_handle *h, uint64_t ticket, int *state, double *t_done_s) {

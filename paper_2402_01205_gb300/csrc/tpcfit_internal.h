@@ -46,6 +46,8 @@ struct FitArgs {
 cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream);
 cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches);
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream);
+// track-model compression residual codes (nothing when a.res_y and a.res_z are null)
+cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream);
 // Occupancy-derived resident blocks per SM for the fit kernel at `block` threads.
 int fit_blocks_per_sm(int block);
 // tuned default residency (blocks per SM) for a block size

@@ -59,11 +59,12 @@ constexpr double kBackfillWindow = 0.050;  // seconds a blocked queue head may b
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Device bytes one resident frame occupies: inputs, results, fit scratch.
-size_t frame_bytes(int64_t nt, int64_t nc) {
+// Device bytes one resident frame occupies: inputs, results (with `n_res`
+// residual code arrays), fit scratch.
+size_t frame_bytes(int64_t nt, int64_t nc, int n_res) {
   return a256((size_t)(nt + 1) * 8) + 5 * a256((size_t)nc * 4) + 2 * a256((size_t)nc) + a256((size_t)nt * 20) +
          a256((size_t)nt * 60) + a256((size_t)nt * 4) + a256((size_t)nt * 8) + 2 * a256((size_t)nt * 4) +
-         2 * a256((size_t)nc * 2) + serve_scratch_bytes(nt);
+         (size_t)n_res * a256((size_t)nc * 2) + serve_scratch_bytes(nt);
 }
 
 struct Request {
@@ -138,9 +139,8 @@ static void carve(void *mem, int64_t nt, int64_t nc, bool want_ry, bool want_rz,
   dr->ndf = (int32_t *)take((size_t)nt * 4);
   dr->status = (int32_t *)take((size_t)nt * 4);
   dr->accept = (uint8_t *)take((size_t)nc);
-  int16_t *ry = (int16_t *)take((size_t)nc * 2), *rz = (int16_t *)take((size_t)nc * 2);
-  dr->res_y = want_ry ? ry : nullptr;
-  dr->res_z = want_rz ? rz : nullptr;
+  dr->res_y = want_ry ? (int16_t *)take((size_t)nc * 2) : nullptr;
+  dr->res_z = want_rz ? (int16_t *)take((size_t)nc * 2) : nullptr;
   dr->mem = TPCFIT_MEM_DEVICE;
   dr->chi2_out_cluster = dr->chi2_in_cluster = nullptr;
   dr->restart_state = nullptr;
@@ -337,7 +337,8 @@ void serve_stop(tpcfit_handle *h) {
 
 int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint64_t *ticket) {
   ServeState *S = handle_serve(h);
-  const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters);
+  const int n_res = (r->res_y ? 1 : 0) + (r->res_z ? 1 : 0);
+  const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters, n_res);
   if (bytes > S->budget) return TPCFIT_E_NOMEM;
   // parts of about host_chunk_clusters clusters (offsets were checked by the caller)
   const int64_t *off = f->track_offsets;
@@ -353,7 +354,7 @@ int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint
     Part P;
     P.t0 = t0;
     P.t1 = lo;
-    P.bytes = frame_bytes(lo - t0, off[lo] - off[t0]);
+    P.bytes = frame_bytes(lo - t0, off[lo] - off[t0], n_res);
     parts.push_back(P);
     t0 = lo;
   }
