@@ -52,6 +52,11 @@ class _Res(ctypes.Structure):
                  "state_out_t", "restart_t")]
 
 
+class _FollowCfg(ctypes.Structure):
+    _fields_ = [("window_sigma", ctypes.c_double), ("nominal_v", ctypes.c_double), ("max_miss", ctypes.c_int32),
+                ("tan_edge", ctypes.c_double), ("z_max", ctypes.c_double)]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 
 
@@ -71,6 +76,9 @@ def _load():
         lib.orc_ms_noise.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double]
         lib.orc_seed.argtypes = [_D, _D, _D, ctypes.c_double, _D]
         lib.oracle_residuals.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64] * 2 + [ctypes.c_void_p] * 11
+        lib.oracle_follow.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_FollowCfg), ctypes.c_int64] + \
+            [ctypes.c_void_p] * 6 + [ctypes.c_int64] + [ctypes.c_void_p] * 10 + [ctypes.c_int]
+        lib.oracle_follow.restype = ctypes.c_int
         lib.oracle_residuals.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -142,6 +150,54 @@ def residuals(frame, fitted: dict, step=(0.01, 0.01), bz: float = 0.5) -> dict:
                               *[out[k].ctypes.data for k in ("res_y", "res_z", "raw_y", "raw_z")])
     if rc != 0:
         raise ValueError("oracle_residuals: malformed track offsets")
+    return out
+
+
+@dataclass
+class FollowConfig:
+    """Track-following readings (the paper describes no algorithm)."""
+    window_sigma: float = 4.0      # search window half-width in sigma
+    nominal_v: float = 0.01        # cluster variance used for the window (cm^2)
+    max_miss: int = 4              # consecutive rows without a cluster that end the track
+    tan_edge: float = float(np.tan(np.radians(10.0)))  # sector edge
+    z_max: float = 250.0
+    seed_cov: tuple = (0.01, 0.01, 1e-4, 1e-4, 0.01)
+
+
+def cluster_sectors(frame) -> np.ndarray:
+    """Sector of every cluster (the frames store one sector per track)."""
+    return np.repeat(np.asarray(frame.sector, dtype=np.uint8), np.diff(frame.offsets)).astype(np.uint8)
+
+
+def follow(hits, seeds: dict, cfg: Optional[FitConfig] = None, fcfg: Optional[FollowConfig] = None,
+           threads: Optional[int] = None) -> dict:
+    """Follow ``seeds`` (dict: state float64[ns,5], row uint8[ns], sector uint8[ns]) through the
+    clusters of ``hits`` (y, z, sy2, sz2, row arrays and ``sectors`` per cluster)."""
+    lib = _load()
+    cfg = cfg or FitConfig()
+    fcfg = fcfg or FollowConfig()
+    y, z, sy2, sz2 = (np.ascontiguousarray(getattr(hits, k), dtype=np.float32) for k in ("y", "z", "sy2", "sz2"))
+    row = np.ascontiguousarray(hits.row, dtype=np.uint8)
+    sec = np.ascontiguousarray(hits.sectors, dtype=np.uint8)
+    st = np.ascontiguousarray(seeds["state"], dtype=np.float64)
+    srow = np.ascontiguousarray(seeds["row"], dtype=np.uint8)
+    ssec = np.ascontiguousarray(seeds["sector"], dtype=np.uint8)
+    scov = np.ascontiguousarray(fcfg.seed_cov, dtype=np.float64)
+    ns, nc, nr = st.shape[0], y.shape[0], cfg.n_rows
+    rx = cfg.row_x()
+    c = _Cfg(cfg.bz, cfg.chi2_max, cfg.xx0, cfg.mass, cfg.snp_max, (ctypes.c_double * 5)(*cfg.seed_cov),
+             cfg.min_clusters, cfg.n_rows, rx.ctypes.data, cfg.restart_scale)
+    fc = _FollowCfg(fcfg.window_sigma, fcfg.nominal_v, fcfg.max_miss, fcfg.tan_edge, fcfg.z_max)
+    out = dict(att=np.zeros((ns, nr), np.int32), n_att=np.zeros(ns, np.int32), status=np.zeros(ns, np.int32),
+               state=np.zeros((ns, 5)), best2=np.zeros((ns, nr, 2)), edge=np.zeros((ns, nr)))
+    th = threads if threads else (os.cpu_count() or 1)
+    rc = lib.oracle_follow(ctypes.byref(c), ctypes.byref(fc), nc, y.ctypes.data, z.ctypes.data, sy2.ctypes.data,
+                           sz2.ctypes.data, row.ctypes.data, sec.ctypes.data, ns, st.ctypes.data, srow.ctypes.data,
+                           ssec.ctypes.data, scov.ctypes.data, *[out[k].ctypes.data for k in
+                                                                ("att", "n_att", "status", "state", "best2", "edge")],
+                           th)
+    if rc != 0:
+        raise ValueError("oracle_follow: bad arguments")
     return out
 
 

@@ -451,3 +451,175 @@ int oracle_residuals(double bz, double step_y, double step_z, int64_t nt, int64_
   return 0;
 }
 
+
+/* ---------------------------------------------------------------------------
+ * Track following: the tracking step in front of the fit (the paper runs the
+ * full TPC tracking on the GPU, Sec. 5 and Sec. 6, and describes no
+ * algorithm).  Reading: a seed (state at the plane of pad row r0, sector s,
+ * diagonal covariance) is carried row by row with the fit's own propagation,
+ * update and scattering; at each row the candidate clusters are those of its
+ * sector and row with |y_c - y| <= k sqrt(C_yy + v) and |z_c - z| <= k
+ * sqrt(C_zz + v) (k = window_sigma, v = nominal_v); the candidate with the
+ * smallest chi2 (its own variances; ties: lowest cluster index) is attached
+ * if its chi2 passes the gate.  MS noise after the (possible) update at every
+ * row.  Following ends at the last row, at the sector edge (|y| > x tan_edge),
+ * at |z| > z_max (status END), after max_miss consecutive rows without a
+ * cluster (MISSES), or on a numerical failure (SNP_LIMIT, NOT_PD).
+ * Diagnostics per (seed, row), for the comparison with other arithmetic:
+ * the best and second-best candidate chi2 and the smallest relative distance
+ * of any cluster of the row to the window edge.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double window_sigma;
+  double nominal_v;
+  int32_t max_miss;
+  double tan_edge;
+  double z_max;
+} orc_follow_cfg;
+
+enum { FL_END = 0, FL_MISSES = 1 };
+
+static const float *g_sort_y; /* qsort comparator context (set per call under a lock) */
+static int cmp_y_idx(const void *a, const void *b) {
+  const int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+  if (g_sort_y[i] < g_sort_y[j]) return -1;
+  if (g_sort_y[i] > g_sort_y[j]) return 1;
+  return (i > j) - (i < j);
+}
+static pthread_mutex_t g_sort_mu = PTHREAD_MUTEX_INITIALIZER;
+
+typedef struct {
+  const orc_config *c;
+  const orc_follow_cfg *fc;
+  const float *y, *z, *sy2, *sz2;
+  const int64_t *bstart; /* n_buckets + 1 */
+  const int64_t *bidx;   /* cluster indices, bucket by bucket, by y */
+  int64_t ns;
+  const double *seed_state, *seed_cov;
+  const uint8_t *seed_row, *seed_sector;
+  int32_t *att, *n_att, *status;
+  double *state_out, *best2, *edge;
+  int tid, nth;
+} follow_job;
+
+static void follow_seed(const follow_job *J, int64_t s) {
+  const orc_config *c = J->c;
+  const orc_follow_cfg *fc = J->fc;
+  const int nr = c->n_rows;
+  double p[5], C[25], pn[5], F[25];
+  for (int i = 0; i < 5; ++i) p[i] = J->seed_state[5 * s + i];
+  memset(C, 0, sizeof(C));
+  for (int i = 0; i < 5; ++i) C[i * 5 + i] = J->seed_cov[i];
+  for (int r = 0; r < nr; ++r) {
+    J->att[s * nr + r] = -1;
+    if (J->best2) J->best2[(s * nr + r) * 2] = J->best2[(s * nr + r) * 2 + 1] = NAN;
+    if (J->edge) J->edge[s * nr + r] = NAN;
+  }
+  int status = FL_END, misses = 0, n = 0;
+  const int r0 = J->seed_row[s], sec = J->seed_sector[s];
+  double xcur = c->row_x[r0 < nr ? r0 : 0];
+  for (int r = r0; r < nr; ++r) {
+    const double xr = c->row_x[r];
+    if (r > r0) {
+      if ((status = orc_propagate(p, xcur, xr, c->bz, c->snp_max, pn, F)) != ST_OK) break;
+      memcpy(p, pn, sizeof(pn));
+      cov_transport(C, F);
+      xcur = xr;
+    }
+    if (fabs(p[0]) > xr * fc->tan_edge || fabs(p[1]) > fc->z_max) { status = FL_END; break; }
+    const double wy = fc->window_sigma * sqrt(C[0] + fc->nominal_v);
+    const double wz = fc->window_sigma * sqrt(C[6] + fc->nominal_v);
+    const int64_t b = (int64_t)sec * nr + r;
+    const int64_t lo0 = J->bstart[b], hi0 = J->bstart[b + 1];
+    /* first cluster with y >= p0 - 1.01 wy (binary search over the bucket sorted by y) */
+    int64_t lo = lo0, hi = hi0;
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if ((double)J->y[J->bidx[mid]] < p[0] - 1.01 * wy) lo = mid + 1;
+      else hi = mid;
+    }
+    int64_t best = -1;
+    double c1 = INFINITY, c2 = INFINITY, edge = INFINITY;
+    for (int64_t q = lo; q < hi0; ++q) {
+      const int64_t k = J->bidx[q];
+      const double dy = (double)J->y[k] - p[0], dz = (double)J->z[k] - p[1];
+      if (dy > 1.01 * wy) break;
+      if (fabs(dz) > 1.01 * wz) continue;
+      const double ey = fabs(fabs(dy) - wy) / wy, ez = fabs(fabs(dz) - wz) / wz;
+      edge = fmin(edge, fmin(ey, ez));
+      if (fabs(dy) > wy || fabs(dz) > wz) continue;
+      const double S00 = C[0] + J->sy2[k], S01 = C[1], S11 = C[6] + J->sz2[k];
+      const double det = S00 * S11 - S01 * S01;
+      const double chi2 = (dy * (S11 * dy - S01 * dz) + dz * (S00 * dz - S01 * dy)) / det;
+      if (chi2 < c1 || (chi2 == c1 && k < best)) { c2 = c1; c1 = chi2; best = k; }
+      else if (chi2 < c2) c2 = chi2;
+    }
+    if (J->best2) { J->best2[(s * nr + r) * 2] = c1; J->best2[(s * nr + r) * 2 + 1] = c2; }
+    if (J->edge) J->edge[s * nr + r] = edge;
+    int acc = 0;
+    if (best >= 0) {
+      double chi2;
+      if ((status = orc_update(p, C, J->y[best], J->z[best], J->sy2[best], J->sz2[best], c->chi2_max, &chi2, &acc)) !=
+          ST_OK)
+        break;
+    }
+    if (acc) { J->att[s * nr + r] = (int32_t)best; ++n; misses = 0; }
+    else if (++misses > fc->max_miss) { status = FL_MISSES; break; }
+    orc_ms_noise(p, C, c->xx0, c->mass);
+  }
+  J->n_att[s] = n;
+  J->status[s] = status;
+  if (J->state_out) for (int i = 0; i < 5; ++i) J->state_out[5 * s + i] = p[i];
+}
+
+static void *follow_worker(void *arg) {
+  follow_job *j = (follow_job *)arg;
+  for (int64_t s = j->tid; s < j->ns; s += j->nth) follow_seed(j, s);
+  return NULL;
+}
+
+/* Follow ns seeds through the clusters (x is the row plane; rows and sectors
+ * per cluster).  att: ns*n_rows cluster indices by row (-1: none).  Returns 0,
+ * or -1 on bad arguments. */
+int oracle_follow(const orc_config *c, const orc_follow_cfg *fc, int64_t nc, const float *y, const float *z,
+                  const float *sy2, const float *sz2, const uint8_t *row, const uint8_t *sector, int64_t ns,
+                  const double *seed_state, const uint8_t *seed_row, const uint8_t *seed_sector, const double *seed_cov,
+                  int32_t *att, int32_t *n_att, int32_t *status, double *state_out, double *best2, double *edge,
+                  int n_threads) {
+  if (nc < 0 || ns < 0 || c->n_rows < 1 || c->n_rows > 256) return -1;
+  const int64_t nb = 256 * (int64_t)c->n_rows;
+  int64_t *bstart = calloc((size_t)nb + 1, sizeof(int64_t));
+  int64_t *bidx = malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int64_t));
+  int64_t *cur = calloc((size_t)nb + 1, sizeof(int64_t));
+  if (!bstart || !bidx || !cur) { free(bstart); free(bidx); free(cur); return -1; }
+  for (int64_t k = 0; k < nc; ++k) {
+    if (row[k] >= c->n_rows) continue;
+    ++bstart[(int64_t)sector[k] * c->n_rows + row[k] + 1];
+  }
+  for (int64_t b = 0; b < nb; ++b) bstart[b + 1] += bstart[b];
+  memcpy(cur, bstart, (size_t)nb * sizeof(int64_t));
+  for (int64_t k = 0; k < nc; ++k) {
+    if (row[k] >= c->n_rows) continue;
+    bidx[cur[(int64_t)sector[k] * c->n_rows + row[k]]++] = k;
+  }
+  pthread_mutex_lock(&g_sort_mu);
+  g_sort_y = y;
+  for (int64_t b = 0; b < nb; ++b)
+    if (bstart[b + 1] - bstart[b] > 1) qsort(bidx + bstart[b], (size_t)(bstart[b + 1] - bstart[b]), sizeof(int64_t), cmp_y_idx);
+  pthread_mutex_unlock(&g_sort_mu);
+  int nth = n_threads > 0 ? n_threads : 1;
+  if (nth > 512) nth = 512;
+  if ((int64_t)nth > ns) nth = ns > 0 ? (int)ns : 1;
+  pthread_t th[512];
+  follow_job jobs[512];
+  for (int i = 0; i < nth; ++i) {
+    follow_job jj = {c, fc, y, z, sy2, sz2, bstart, bidx, ns, seed_state, seed_cov, seed_row, seed_sector,
+                     att, n_att, status, state_out, best2, edge, i, nth};
+    jobs[i] = jj;
+    if (nth == 1) follow_worker(&jobs[i]);
+    else pthread_create(&th[i], NULL, follow_worker, &jobs[i]);
+  }
+  if (nth > 1) for (int i = 0; i < nth; ++i) pthread_join(th[i], NULL);
+  free(bstart); free(bidx); free(cur);
+  return 0;
+}

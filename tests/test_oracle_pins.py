@@ -5,6 +5,8 @@ all), so every pin here is a closed form, an invariant, an independent
 implementation (the global-circle generator, the global least-squares fit,
 a straight-line regression) or a statistical property of the Kalman filter.
 """
+import types
+
 import numpy as np
 import pytest
 
@@ -400,3 +402,65 @@ def test_residual_codes_clip_and_round_half_even():
         rr["state"][t, 0] = float(f.y[k]) - want * step  # exact in binary64
         qq = oracle.residuals(f, rr, step=(step, step))
         assert qq["raw_y"][k] == want and qq["res_y"][k] == code_y, (want, qq["raw_y"][k], qq["res_y"][k])
+
+
+# ---------------------------------------------------------------------------
+# Track following (reading: seeds carried row by row, nearest-chi2 cluster in
+# a +-4 sigma window of the seed's sector and row, fit's own update and MS)
+# ---------------------------------------------------------------------------
+def _follow_inputs(f, smear=0.0, seed=1):
+    first = f.offsets[:-1]
+    fc = oracle.FollowConfig()
+    st = f.truth[first].copy()
+    if smear:
+        st += np.random.default_rng(seed).normal(0, 1, st.shape) * np.sqrt(np.array(fc.seed_cov)) * smear
+    hits = types.SimpleNamespace(y=f.y, z=f.z, sy2=f.sy2, sz2=f.sz2, row=f.row, sectors=oracle.cluster_sectors(f))
+    return hits, dict(state=st, row=f.row[first], sector=f.sector), fc
+
+
+def _own_fraction(f, r):
+    own = wrong = 0
+    for t in range(f.n_tracks):
+        a = r["att"][t][r["att"][t] >= 0]
+        ok = (a >= f.offsets[t]) & (a < f.offsets[t + 1])
+        own += ok.sum()
+        wrong += (~ok).sum()
+    return own, wrong
+
+
+def test_following_noise_free_isolated_tracks_finds_exactly_their_clusters():
+    f = tpcgen.generate("sector1k", truth=True, sigma_y=0.0, sigma_z=0.0, seed=5)
+    hits, seeds, fc = _follow_inputs(f)
+    r = oracle.follow(hits, seeds, oracle.FitConfig(xx0=0.0), fc)
+    own, wrong = _own_fraction(f, r)
+    assert wrong == 0 and own == f.n_clusters and np.all(r["status"] == 0)
+    assert np.array_equal(r["n_att"], np.diff(f.offsets))
+    # every attached cluster is exactly on the followed helix
+    rows = r["att"] >= 0
+    assert np.nanmax(r["best2"][..., 0][rows]) < 1e-6
+
+
+def test_following_with_noise_and_scattering_one_sector():
+    f = tpcgen.generate("sector1k", truth=True, xx0=5e-4, seed=6)
+    hits, seeds, fc = _follow_inputs(f, smear=0.3)
+    r = oracle.follow(hits, seeds, oracle.FitConfig(xx0=5e-4), fc)
+    own, wrong = _own_fraction(f, r)
+    # greedy nearest-chi2 attachment: a foreign cluster inside the window can be
+    # closer than the track's own, about once per hundred rows at this density
+    assert own >= 0.985 * f.n_clusters and wrong <= 0.015 * own, (own, wrong, f.n_clusters)
+
+
+def test_following_invariants():
+    f = tpcgen.generate("detector50k", truth=True, n_tracks=3000, seed=7)
+    hits, seeds, fc = _follow_inputs(f, smear=0.3)
+    cfg = oracle.FitConfig()
+    r = oracle.follow(hits, seeds, cfg, fc)
+    sec = oracle.cluster_sectors(f)
+    for t in range(f.n_tracks):
+        rows = np.nonzero(r["att"][t] >= 0)[0]
+        k = r["att"][t][rows]
+        assert np.all(f.row[k] == rows) and np.all(sec[k] == f.sector[t])  # own sector, the row it was found on
+        assert np.all(rows >= seeds["row"][t]) and r["n_att"][t] == len(rows)
+        b2 = r["best2"][t, rows]
+        assert np.all(b2[:, 0] <= cfg.chi2_max) and np.all(b2[:, 0] <= b2[:, 1])
+    assert set(np.unique(r["status"])) <= {0, 1, 2}
