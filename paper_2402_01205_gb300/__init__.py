@@ -24,7 +24,8 @@ from . import _build
 __all__ = ["TpcfitError", "Config", "default_config", "create", "destroy", "fit", "fit_async", "sync", "submit",
            "poll", "wait", "last_timing", "reset_timing", "probe_fma_rates", "strerror", "now", "Fitter",
            "library_path", "alloc_result", "STATUS_NAMES", "Batch", "EventViews", "batch_create", "batch_launch",
-           "batch_sync", "batch_destroy", "fit_noalloc", "rans_bound", "rans_encode", "rans_decode"]
+           "batch_sync", "batch_destroy", "fit_noalloc", "rans_bound", "rans_encode", "rans_decode", "FollowConfig",
+           "follow_config", "follow", "gather_tracks"]
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_NOTFOUND, E_NODEV = 0, -1, -2, -3, -4, -5, -6, -7
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -74,6 +75,28 @@ class _Timing(ctypes.Structure):
                 ("fit_ms_sum", ctypes.c_double), ("total_ms_sum", ctypes.c_double)]
 
 
+class FollowConfig(ctypes.Structure):
+    _fields_ = [("window_sigma", ctypes.c_float), ("nominal_v", ctypes.c_float), ("max_miss", ctypes.c_int32),
+                ("tan_edge", ctypes.c_float), ("z_max", ctypes.c_float), ("seed_cov", ctypes.c_float * 5),
+                ("n_sectors", ctypes.c_int32), ("n_ybins", ctypes.c_int32), ("n_zbins", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class _Hits(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
+                                                    ("x", "y", "z", "sy2", "sz2", "row", "sector")]
+
+
+class _Seeds(ctypes.Structure):
+    _fields_ = [("n_seeds", ctypes.c_int64), ("state", ctypes.c_void_p), ("row", ctypes.c_void_p),
+                ("sector", ctypes.c_void_p)]
+
+
+class _Tracks(ctypes.Structure):
+    _fields_ = [("att", ctypes.c_void_p), ("n_att", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("state", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -119,6 +142,14 @@ def _load():
     lib.tpcfit_fit_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_Frame), ctypes.POINTER(_Result),
                                        ctypes.c_void_p]
     lib.tpcfit_fit_noalloc.restype = ctypes.c_int
+    lib.tpcfit_follow_default_config.argtypes = [ctypes.POINTER(FollowConfig)]
+    lib.tpcfit_follow_default_config.restype = None
+    lib.tpcfit_follow.argtypes = [H, ctypes.POINTER(FollowConfig), ctypes.POINTER(_Hits), ctypes.POINTER(_Seeds),
+                                  ctypes.POINTER(_Tracks), ctypes.c_void_p]
+    lib.tpcfit_follow.restype = ctypes.c_int
+    lib.tpcfit_gather_tracks.argtypes = [H, ctypes.POINTER(_Hits), ctypes.POINTER(_Tracks), ctypes.c_int64] + \
+        [ctypes.c_void_p] * 7 + [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    lib.tpcfit_gather_tracks.restype = ctypes.c_int
     lib.tpcfit_batch_create.argtypes = [H, ctypes.POINTER(_Frame), ctypes.POINTER(_Result), ctypes.POINTER(H)]
     lib.tpcfit_batch_launch.argtypes = [H, ctypes.c_void_p]
     lib.tpcfit_batch_sync.argtypes = [H, ctypes.c_double]
@@ -389,6 +420,74 @@ def rans_decode(handle: int, blob, size: int, n: int, out=None, stream=None):
     return out
 
 
+def follow_config(**overrides) -> FollowConfig:
+    c = FollowConfig()
+    _load().tpcfit_follow_default_config(ctypes.byref(c))
+    for k, v in overrides.items():
+        if k == "seed_cov":
+            c.seed_cov = (ctypes.c_float * 5)(*v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def _dev(a, dtype: str, name: str):
+    import torch
+    if not (_is_torch(a) and a.is_cuda and a.is_contiguous() and str(a.dtype) == "torch." + dtype):
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return a.data_ptr()
+
+
+def _hits_struct(hits) -> _Hits:
+    """hits: object with CUDA tensors x, y, z, sy2, sz2 (float32), row and sectors (uint8), one per cluster."""
+    n = int(hits.y.numel())
+    return _Hits(n, *[_dev(getattr(hits, k), "float32", k) for k in ("x", "y", "z", "sy2", "sz2")],
+                 _dev(hits.row, "uint8", "row"), _dev(hits.sectors, "uint8", "sectors"))
+
+
+def follow(handle: int, hits, seeds: dict, config: Optional[FollowConfig] = None, stream=None,
+           n_rows: int = 152) -> dict:
+    """Track following (tpcfit_follow): seeds dict of CUDA tensors state (float32 [ns, 5]),
+    row and sector (uint8 [ns]); returns CUDA tensors att [ns, n_rows], n_att, status, state."""
+    import torch
+    h = _hits_struct(hits)
+    ns = int(seeds["state"].shape[0])
+    sd = _Seeds(ns, _dev(seeds["state"], "float32", "state"), _dev(seeds["row"], "uint8", "row"),
+                _dev(seeds["sector"], "uint8", "sector"))
+    dev = seeds["state"].device
+    lib = _load()
+    out = dict(att=torch.empty((ns, n_rows), dtype=torch.int32, device=dev),
+               n_att=torch.empty(ns, dtype=torch.int32, device=dev), status=torch.empty(ns, dtype=torch.int32, device=dev),
+               state=torch.empty((ns, 5), dtype=torch.float32, device=dev))
+    tr = _Tracks(out["att"].data_ptr(), out["n_att"].data_ptr(), out["status"].data_ptr(), out["state"].data_ptr())
+    _check(lib.tpcfit_follow(handle, ctypes.byref(config) if config is not None else None, ctypes.byref(h),
+                             ctypes.byref(sd), ctypes.byref(tr), getattr(stream, "cuda_stream", stream)))
+    out["_keep"] = (hits, seeds)
+    return out
+
+
+def gather_tracks(handle: int, hits, tracks: dict, stream=None):
+    """tpcfit_gather_tracks: the followed tracks as a device frame (SimpleNamespace of CUDA tensors)."""
+    import types
+    import torch
+    h = _hits_struct(hits)
+    ns = int(tracks["n_att"].numel())
+    dev = tracks["n_att"].device
+    cap = int(tracks["n_att"].sum().item())
+    fr = types.SimpleNamespace(offsets=torch.empty(ns + 1, dtype=torch.int64, device=dev),
+                               **{k: torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
+                                  for k in ("x", "y", "z", "sy2", "sz2")},
+                               row=torch.empty(max(cap, 1), dtype=torch.uint8, device=dev))
+    tr = _Tracks(tracks["att"].data_ptr(), tracks["n_att"].data_ptr(), tracks["status"].data_ptr(), 0)
+    n = ctypes.c_int64()
+    _check(_load().tpcfit_gather_tracks(handle, ctypes.byref(h), ctypes.byref(tr), ns, fr.offsets.data_ptr(),
+                                        *[getattr(fr, k).data_ptr() for k in ("x", "y", "z", "sy2", "sz2", "row")],
+                                        max(cap, 1), ctypes.byref(n), getattr(stream, "cuda_stream", stream)))
+    for k in ("x", "y", "z", "sy2", "sz2", "row"):
+        setattr(fr, k, getattr(fr, k)[:n.value])
+    return fr
+
+
 class EventViews:
     """Per-event frames and results inside one concatenated device frame.
 
@@ -515,6 +614,12 @@ class Fitter:
 
     def timing(self) -> dict:
         return last_timing(self.handle)
+
+    def follow(self, hits, seeds: dict, config: Optional[FollowConfig] = None, stream=None) -> dict:
+        return follow(self.handle, hits, seeds, config, stream, n_rows=self.config.n_rows)
+
+    def gather_tracks(self, hits, tracks: dict, stream=None):
+        return gather_tracks(self.handle, hits, tracks, stream)
 
     def rans_encode(self, codes, segment_symbols: int = 0, out=None, stream=None):
         return rans_encode(self.handle, codes, segment_symbols, out, stream)

@@ -192,6 +192,7 @@ struct tpcfit_handle {
   Scratch scratch;
   Stage stage[2];
   DevBuf rans_buf;           // rANS codec scratch
+  DevBuf follow_buf;         // track-following scratch (cell grid)
   int32_t *h_err = nullptr;  // pinned
   // ring of event quadruples around prepare / sort / fit of timed calls
   static constexpr int kRing = 64;
@@ -226,6 +227,13 @@ int handle_rans_scratch(tpcfit_handle *h, size_t bytes, void **p) {
   int rc = h->rans_buf.ensure(bytes);
   if (rc) return rc;
   *p = h->rans_buf.p;
+  return TPCFIT_OK;
+}
+int handle_follow_scratch(tpcfit_handle *h, size_t bytes, void **p) {
+  if (bytes > h->follow_buf.cap) CU(cudaDeviceSynchronize());  // growing frees the old buffer
+  int rc = h->follow_buf.ensure(bytes);
+  if (rc) return rc;
+  *p = h->follow_buf.p;
   return TPCFIT_OK;
 }
 int32_t *handle_pinned_word(tpcfit_handle *h) { return h->h_err; }
@@ -351,6 +359,7 @@ extern "C" int tpcfit_destroy(tpcfit_handle *h) {
   if (h->d2h) cudaStreamSynchronize(h->d2h);
   h->scratch.buf.release();
   h->rans_buf.release();
+  h->follow_buf.release();
   for (auto &s : h->stage) {
     s.buf.release();
     if (s.free_ev) cudaEventDestroy(s.free_ev);

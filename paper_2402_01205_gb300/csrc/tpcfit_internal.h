@@ -41,6 +41,42 @@ struct FitArgs {
   int32_t min_clusters, n_rows;
 };
 
+// Track following (tpcfit_follow.cu builds the cell grid; the kernel lives
+// with the fit's device code).  Cell of a cluster: ((sector * n_rows + row) *
+// nz + iz) * ny + iy, iz from z over [-z_max, z_max], iy from y over
+// [-ymax_r, ymax_r] with ymax_r = row_x[row] * tan_edge * 1.02.
+struct FollowArgs {
+  int32_t n_sectors, n_rows, ny, nz;
+  float z_max, tan_edge;
+  const uint32_t *cell_start;             // n_cells + 1
+  const float *cy, *cz, *cvy, *cvz;       // clusters in cell order
+  const int32_t *cidx;                    // their indices in the caller's arrays
+  int64_t n_seeds;
+  const float *seed_state;                // n_seeds * 5
+  const uint8_t *seed_row, *seed_sector;
+  float seed_cov[5];
+  int32_t *att, *n_att, *status;          // att: n_seeds * n_rows (pre-set to -1)
+  float *state_out;                       // n_seeds * 5, may be null
+  const float *row_x;
+  float b, chi2_max;
+  double chi2_max_d;
+  float xx0, mass2, snp_max;
+  float window_sigma, nominal_v;
+  int32_t max_miss;
+};
+
+__host__ __device__ inline int follow_ybin(float y, float xr, float tan_edge, int ny) {
+  const float ym = xr * tan_edge * 1.02f;
+  int i = (int)floorf((y + ym) * ((float)ny / (2.0f * ym)));
+  return i < 0 ? 0 : (i >= ny ? ny - 1 : i);
+}
+__host__ __device__ inline int follow_zbin(float z, float z_max, int nz) {
+  int i = (int)floorf((z + z_max) * ((float)nz / (2.0f * z_max)));
+  return i < 0 ? 0 : (i >= nz ? nz - 1 : i);
+}
+
+cudaError_t launch_follow(const FollowArgs &a, cudaStream_t stream);
+
 // Launch helpers (all asynchronous on `stream`); each returns the CUDA error
 // of its launch.
 cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream);

@@ -56,8 +56,10 @@ def test_struct_layout_matches_header(lib, tmp_path):
     import subprocess
     import paper_2402_01205_gb300 as T
     structs = {"tpcfit_config": T.Config, "tpcfit_frame": T._Frame, "tpcfit_result": T._Result,
-               "tpcfit_timing": T._Timing}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tpcfit.h"', "int main(void){"]
+               "tpcfit_timing": T._Timing, "tpcfit_follow_config": T.FollowConfig, "tpcfit_hits": T._Hits,
+               "tpcfit_seeds": T._Seeds, "tpcfit_tracks": T._Tracks}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tpcfit.h"', '#include "tpcfit_follow.h"',
+             "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
