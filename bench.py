@@ -43,6 +43,9 @@ WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT
                            "10-20,000), tracks of 10-152 rows, pT log-uniform 0.2-10 GeV/c, 36 sectors, x/X0 5e-4 "
                            "per row, 5% dropout, 1% outliers, seed 0; one graph-captured persistent launch sequence "
                            "per step vs one plain launch sequence per event",
+             "tracking": "track following + gather + fit of a 50,000-track frame of the 36-sector detector "
+                         "(x/X0 5e-4 per row, 5% dropout, 1% outliers, seed 0); seeds: the true state at each "
+                         "track's first cluster smeared by 0.3 of the seed sigma (seeded)",
              "serving": "time frames arriving as a Poisson process at 50 frames/s, clusters per frame log-normal "
                         "(median 20 M, sigma_ln 0.6, 1-120 M), tracks as in the 36-sector detector workload; a pool "
                         "of 64 frames (windows of one pre-generated 1.1 M-track frame) replayed on a seeded "
@@ -629,6 +632,121 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe):
     return 0
 
 
+def tracking_inputs(n_tracks: int, rank: int, seed: int = 0):
+    f = tpcgen.generate("detector50k", n_tracks=n_tracks, seed=rank, truth=True)
+    first = f.offsets[:-1]
+    seed_cov = np.array([0.01, 0.01, 1e-4, 1e-4, 0.01])
+    st = (f.truth[first] + np.random.default_rng(seed + 91).normal(0, 1, (f.n_tracks, 5)) * np.sqrt(seed_cov) * 0.3)
+    sec = np.repeat(f.sector, np.diff(f.offsets)).astype(np.uint8)
+    return f, st.astype(np.float32), sec
+
+
+def run_tracking(args, ws, rank, local, T, torch, dist, probe):
+    """Track following + gather + fit (the tracking chain) on the GPU."""
+    import types
+    n_tracks = args.n_tracks or 50_000
+    f, st, sec = tracking_inputs(n_tracks, rank)
+    nc, nt = f.n_clusters, f.n_tracks
+    first = f.offsets[:-1]
+    dev = types.SimpleNamespace(**{k: torch.from_numpy(np.ascontiguousarray(getattr(f, k))).cuda()
+                                   for k in ("x", "y", "z", "sy2", "sz2", "row")}, sectors=torch.from_numpy(sec).cuda())
+    seeds = dict(state=torch.from_numpy(st).cuda(), row=torch.from_numpy(np.ascontiguousarray(f.row[first])).cuda(),
+                 sector=torch.from_numpy(np.ascontiguousarray(f.sector)).cuda())
+    fx = T.Fitter(device=local)
+    stream = torch.cuda.Stream()
+
+    def chain():
+        tr = fx.follow(dev, seeds, stream=stream)
+        fr = fx.gather_tracks(dev, tr, stream=stream)  # blocks on `stream`
+        fx.fit_async(fr, T.alloc_result(fr.offsets.numel() - 1, fr.x.numel(), device=torch.device("cuda", local)),
+                     stream=stream)
+        return tr
+
+    for _ in range(args.warmup):
+        tr = chain()
+    fx.sync()
+    torch.cuda.synchronize()
+    # following alone
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tr = fx.follow(dev, seeds, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_follow = reduce_max(dist, torch, e0.elapsed_time(e1)) / args.steps
+    # the whole chain
+    clocks = ClockSampler(gpu_index(local))
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(args.steps):
+        tr = chain()
+    fx.sync()
+    c1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = reduce_max(dist, torch, c0.elapsed_time(c1)) / args.steps
+    nc_all = reduce_sum(dist, torch, float(nc))
+    # efficiency and purity against the generator's truth
+    att = tr["att"].cpu().numpy()
+    own = wrong = 0
+    for t in range(0, nt, max(1, nt // 20000)):
+        a = att[t][att[t] >= 0]
+        ok = (a >= f.offsets[t]) & (a < f.offsets[t + 1])
+        own += int(ok.sum())
+        wrong += int((~ok).sum())
+    sample_true = int(sum(f.offsets[t + 1] - f.offsets[t] for t in range(0, nt, max(1, nt // 20000))))
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        k = min(nt, 20_000)
+        hits = types.SimpleNamespace(y=f.y, z=f.z, sy2=f.sy2, sz2=f.sz2, row=f.row, sectors=sec)
+        sd = dict(state=st[:k].astype(np.float64), row=f.row[first[:k]], sector=f.sector[:k])
+        t0 = time.perf_counter()
+        oracle.follow(hits, sd, oracle.FitConfig(), oracle.FollowConfig())
+        dt = time.perf_counter() - t0
+        cl = float(f.offsets[k])
+        cpu = {"value": cl / dt, "unit": "clusters/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"FP64 follower on the first {k} seeds ({int(cl)} clusters of their tracks) with the "
+                         f"whole frame's clusters bucketed, {dt:.1f} s (includes the bucketing)"}
+    peaks, peak_src = measured_peaks()
+    follow_bytes = 16 * nc + 24 * nt  # cell build reads y, z, sy2, sz2 (16 B/cluster); seeds + results per track
+    if rank == 0:
+        line = {
+            "metric": "clusters/s tracked on 1 GB300 (track following + gather + fit, FP32 with FP64 gate)",
+            "value": nc_all / (ms * 1e-3), "unit": "clusters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "tracking", "description": WORKLOADS["tracking"], "n_tracks": nt, "n_clusters": nc,
+                       "parallelism": f"replicas x{ws}", "l2": f"inputs {21 * nc / 1e9:.2f} GB; no flush"},
+            "tracks_per_s": reduce_sum(dist, torch, float(nt)) / (ms * 1e-3),
+            "follow_only": {"ms": ms_follow, "clusters_per_s": nc / (ms_follow * 1e-3),
+                            "hbm_frac_of_min_bytes": follow_bytes / (ms_follow * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+            "efficiency": own / max(sample_true, 1), "purity": own / max(own + wrong, 1),
+            "roofline": {"bound": "alu", "kernel": "k_follow + k_fit", "unit": "GB/s (minimum bytes)",
+                         "achieved": follow_bytes / (ms_follow * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                         "frac": follow_bytes / (ms_follow * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                         "traffic_note": "no ncu capture of k_follow; latency-bound like the fit (one thread per track)",
+                         "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "e2e": None,
+            "gpu_launches": 16 * args.steps,  # follow 6 (cells 5 + k_follow), gather 6, fit 4
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    fx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -669,6 +787,8 @@ def main():
         return run_events(args, ws, rank, local, T, torch, dist, probe)
     if args.workload == "serving":
         return run_serving(args, ws, rank, local, T, torch, dist, probe)
+    if args.workload == "tracking":
+        return run_tracking(args, ws, rank, local, T, torch, dist, probe)
     kw = {} if args.n_tracks is None else {"n_tracks": args.n_tracks}
     frame = tpcgen.generate(args.workload, seed=rank, **kw)
     nt, nc = frame.n_tracks, frame.n_clusters

@@ -473,6 +473,11 @@ def gather_tracks(handle: int, hits, tracks: dict, stream=None):
     h = _hits_struct(hits)
     ns = int(tracks["n_att"].numel())
     dev = tracks["n_att"].device
+    # the follow results are complete once the stream they were produced on is
+    if stream is None:
+        sync(handle)
+    else:
+        stream.synchronize()
     cap = int(tracks["n_att"].sum().item())
     fr = types.SimpleNamespace(offsets=torch.empty(ns + 1, dtype=torch.int64, device=dev),
                                **{k: torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
