@@ -120,8 +120,12 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2402_01205_gb300", "csrc", "fit_kernels.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the sources the fit kernel is compiled from (its file and the shared device code)."""
+    h = hashlib.sha256()
+    for name in ("fit_kernels.cu", "fit_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2402_01205_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 ISSUE_PER_SM_CLK = 4          # warp instructions issued per SM per clock (4 schedulers, one each)
