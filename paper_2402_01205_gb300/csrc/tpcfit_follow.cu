@@ -108,17 +108,13 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t
 
 __global__ void k_cell_fill(const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ sy2,
                             const float *__restrict__ sz2, int64_t nc, const uint32_t *__restrict__ cell_of,
-                            const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor, float *__restrict__ cy,
-                            float *__restrict__ cz, float *__restrict__ cvy, float *__restrict__ cvz,
-                            int32_t *__restrict__ cidx) {
+                            const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
+                            float4 *__restrict__ crec, int32_t *__restrict__ cidx) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t c = cell_of[k];
     if (c == 0xffffffffu) continue;
     const uint32_t q = start[c] + atomicAdd(&cursor[c], 1u);
-    cy[q] = y[k];
-    cz[q] = z[k];
-    cvy[q] = sy2[k];
-    cvz[q] = sz2[k];
+    crec[q] = make_float4(y[k], z[k], sy2[k], sz2[k]);
     cidx[q] = (int32_t)k;
   }
 }
@@ -264,15 +260,13 @@ extern "C" int tpcfit_follow(tpcfit_handle *h, const tpcfit_follow_config *fc_in
   const int64_t n_tiles = (n_cells + kTile - 1) / kTile;
   const size_t o_cnt = 0, o_cur = o_cnt + a256(4 * (size_t)n_cells), o_start = o_cur + a256(4 * (size_t)n_cells);
   const size_t o_tiles = o_start + a256(4 * (size_t)(n_cells + 1)), o_tot = o_tiles + a256(4 * (size_t)n_tiles + 4);
-  const size_t o_of = o_tot + 256, o_y = o_of + a256(4 * (size_t)nc), o_z = o_y + a256(4 * (size_t)nc);
-  const size_t o_vy = o_z + a256(4 * (size_t)nc), o_vz = o_vy + a256(4 * (size_t)nc);
-  const size_t o_idx = o_vz + a256(4 * (size_t)nc), bytes = o_idx + a256(4 * (size_t)nc);
+  const size_t o_of = o_tot + 256, o_rec = o_of + a256(4 * (size_t)nc);
+  const size_t o_idx = o_rec + a256(16 * (size_t)nc), bytes = o_idx + a256(4 * (size_t)nc);
   void *base = nullptr;
   int rc = handle_follow_scratch(h, bytes, &base);
   if (rc) return rc;
   char *sc = static_cast<char *>(base);
   auto U = [&](size_t o) { return reinterpret_cast<uint32_t *>(sc + o); };
-  auto Fp = [&](size_t o) { return reinterpret_cast<float *>(sc + o); };
   FCU(cudaMemsetAsync(sc, 0, o_start, st), "memset cells");
   if (nc > 0) {
     k_cell_count<<<grid1d(nc, dev), 256, 0, st>>>(hits->y, hits->z, hits->row, hits->sector, nc, fc.n_sectors, nr,
@@ -283,7 +277,7 @@ extern "C" int tpcfit_follow(tpcfit_handle *h, const tpcfit_follow_config *fc_in
   if ((rc = scan_u32(U(o_cnt), n_cells, U(o_start), U(o_tiles), U(o_tot), dev, st))) return rc;
   if (nc > 0) {
     k_cell_fill<<<grid1d(nc, dev), 256, 0, st>>>(hits->y, hits->z, hits->sy2, hits->sz2, nc, U(o_of), U(o_start),
-                                                 U(o_cur), Fp(o_y), Fp(o_z), Fp(o_vy), Fp(o_vz),
+                                                 U(o_cur), reinterpret_cast<float4 *>(sc + o_rec),
                                                  reinterpret_cast<int32_t *>(sc + o_idx));
     FCU(cudaGetLastError(), "k_cell_fill");
   }
@@ -296,10 +290,7 @@ extern "C" int tpcfit_follow(tpcfit_handle *h, const tpcfit_follow_config *fc_in
   a.z_max = fc.z_max;
   a.tan_edge = fc.tan_edge;
   a.cell_start = U(o_start);
-  a.cy = Fp(o_y);
-  a.cz = Fp(o_z);
-  a.cvy = Fp(o_vy);
-  a.cvz = Fp(o_vz);
+  a.crec = reinterpret_cast<const float4 *>(sc + o_rec);
   a.cidx = reinterpret_cast<const int32_t *>(sc + o_idx);
   a.n_seeds = ns;
   a.seed_state = seeds->state;

@@ -49,7 +49,7 @@ struct FollowArgs {
   int32_t n_sectors, n_rows, ny, nz;
   float z_max, tan_edge;
   const uint32_t *cell_start;             // n_cells + 1
-  const float *cy, *cz, *cvy, *cvz;       // clusters in cell order
+  const float4 *crec;                     // clusters in cell order: (y, z, sy2, sz2)
   const int32_t *cidx;                    // their indices in the caller's arrays
   int64_t n_seeds;
   const float *seed_state;                // n_seeds * 5

@@ -117,31 +117,35 @@ __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
     const int iz0 = follow_zbin(zp - wz, A.z_max, A.nz), iz1 = follow_zbin(zp + wz, A.z_max, A.nz);
     const int64_t base = ((int64_t)sec * A.n_rows + r) * A.nz;
     int32_t best = -1;
-    int64_t bpos = -1;
     float bchi = INFINITY;
+    float4 bc = make_float4(0.f, 0.f, 0.f, 0.f);
     const float S01 = T.c[1];
     for (int iz = iz0; iz <= iz1; ++iz) {
       const int64_t row0 = (base + iz) * A.ny;
       const uint32_t q0 = A.cell_start[row0 + iy0], q1 = A.cell_start[row0 + iy1 + 1];
+      float4 nx = q0 < q1 ? A.crec[q0] : make_float4(0.f, 0.f, 0.f, 0.f);
       for (uint32_t q = q0; q < q1; ++q) {
-        const float r0v = (A.cy[q] - T.ya) - T.dy, r1v = (A.cz[q] - T.za) - T.dz;
+        const float4 c = nx;
+        if (q + 1 < q1) nx = A.crec[q + 1];  // the next record is in flight while this one is tested
+        const float r0v = (c.x - T.ya) - T.dy, r1v = (c.y - T.za) - T.dz;
         if (fabsf(r0v) > wy || fabsf(r1v) > wz) continue;
-        const float S00 = T.c[0] + A.cvy[q], S11 = T.c[2] + A.cvz[q];
+        const float S00 = T.c[0] + c.z, S11 = T.c[2] + c.w;
         const float det = fmaf(S00, S11, -S01 * S01);
         const float chi = (r0v * fmaf(S11, r0v, -S01 * r1v) + r1v * fmaf(S00, r1v, -S01 * r0v)) / det;
-        const int32_t k = A.cidx[q];
-        if (chi < bchi || (chi == bchi && k < best)) {
-          bchi = chi;
-          best = k;
-          bpos = q;
+        if (chi <= bchi) {
+          const int32_t k = A.cidx[q];
+          if (chi < bchi || k < best) {
+            bchi = chi;
+            best = k;
+            bc = c;
+          }
         }
       }
     }
     bool acc = false;
     if (best >= 0) {
       double chi2;
-      const int ust = update(T, A.cy[bpos], A.cz[bpos], A.cvy[bpos], A.cvz[bpos], A.chi2_max_d, gate_hi, gate_lo,
-                             false, acc, chi2);
+      const int ust = update(T, bc.x, bc.y, bc.z, bc.w, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
       if (ust != ST_OK) { status = ust; break; }
     }
     if (acc) {
