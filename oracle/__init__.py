@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 KB = 0.299792458e-2
-STATUS = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT"}
+STATUS = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT", 6: "STOPPED"}
 
 
 def build(force: bool = False) -> str:
@@ -43,7 +43,8 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("bz", ctypes.c_double), ("chi2_max", ctypes.c_double), ("xx0", ctypes.c_double),
                 ("mass", ctypes.c_double), ("snp_max", ctypes.c_double), ("seed_cov", ctypes.c_double * 5),
                 ("min_clusters", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("row_x", ctypes.c_void_p),
-                ("restart_scale", ctypes.c_double)]
+                ("restart_scale", ctypes.c_double), ("xrho", ctypes.c_double), ("eloss_za", ctypes.c_double),
+                ("eloss_i", ctypes.c_double)]
 
 
 class _Res(ctypes.Structure):
@@ -75,6 +76,10 @@ def _load():
         lib.orc_update.restype = ctypes.c_int
         lib.orc_ms_noise.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double]
         lib.orc_seed.argtypes = [_D, _D, _D, ctypes.c_double, _D]
+        lib.orc_dedx.argtypes = [ctypes.c_double] * 4
+        lib.orc_dedx.restype = ctypes.c_double
+        lib.orc_eloss.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Cfg), ctypes.c_double]
+        lib.orc_eloss.restype = ctypes.c_int
         lib.oracle_residuals.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64] * 2 + [ctypes.c_void_p] * 11
         lib.oracle_follow.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_FollowCfg), ctypes.c_int64] + \
             [ctypes.c_void_p] * 6 + [ctypes.c_int64] + [ctypes.c_void_p] * 10 + [ctypes.c_int]
@@ -98,9 +103,36 @@ class FitConfig:
     n_rows: int = 152
     row_x0: float = 85.0
     row_pitch: float = 162.0 / 151.0
+    xrho: float = 0.0          # energy-loss layer per crossed row, g/cm^2 (0: none)
+    eloss_za: float = 0.49555  # its Z/A (neon)
+    eloss_i_ev: float = 137.0  # its mean excitation energy, eV (neon)
 
     def row_x(self) -> np.ndarray:
         return (self.row_x0 + np.arange(self.n_rows, dtype=np.float64) * self.row_pitch).astype(np.float32)
+
+
+def _cfg_struct(cfg: "FitConfig", rx: np.ndarray) -> _Cfg:
+    return _Cfg(cfg.bz, cfg.chi2_max, cfg.xx0, cfg.mass, cfg.snp_max, (ctypes.c_double * 5)(*cfg.seed_cov),
+                cfg.min_clusters, cfg.n_rows, rx.ctypes.data, cfg.restart_scale, cfg.xrho, cfg.eloss_za,
+                cfg.eloss_i_ev * 1e-9)
+
+
+def dedx(p: float, mass: float, za: float = 0.49555, i_ev: float = 137.0) -> float:
+    """Mean stopping power (Bethe formula, no density effect) in GeV cm^2/g (orc_dedx)."""
+    lib = _load()
+    return float(lib.orc_dedx(float(p), float(mass), float(za), float(i_ev) * 1e-9))
+
+
+def eloss_step(state, cov, cfg: "FitConfig", direction: float):
+    """One energy-loss layer applied to (state, 5x5 cov) as the fit applies it
+    (orc_eloss); returns (status, state, cov)."""
+    lib = _load()
+    p = np.ascontiguousarray(state, dtype=np.float64).copy()
+    C = np.ascontiguousarray(cov, dtype=np.float64).copy()
+    rx = cfg.row_x()
+    c = _cfg_struct(cfg, rx)
+    st = lib.orc_eloss(p.ctypes.data, C.ctypes.data, ctypes.byref(c), ctypes.c_double(direction))
+    return int(st), p, C
 
 
 def _p(a: np.ndarray):
@@ -116,8 +148,7 @@ def fit(frame, cfg: Optional[FitConfig] = None, threads: Optional[int] = None, d
     row = np.ascontiguousarray(frame.row, dtype=np.uint8)
     nt, nc = off.shape[0] - 1, int(arrs[0].shape[0])
     rx = cfg.row_x()
-    c = _Cfg(cfg.bz, cfg.chi2_max, cfg.xx0, cfg.mass, cfg.snp_max, (ctypes.c_double * 5)(*cfg.seed_cov),
-             cfg.min_clusters, cfg.n_rows, rx.ctypes.data, cfg.restart_scale)
+    c = _cfg_struct(cfg, rx)
     out = dict(state=np.zeros((nt, 5)), cov=np.zeros((nt, 15)), x_ref=np.zeros(nt), chi2=np.zeros(nt),
                ndf=np.zeros(nt, np.int32), status=np.zeros(nt, np.int32), accept=np.zeros(nc, np.uint8))
     if diagnostics:
@@ -185,8 +216,7 @@ def follow(hits, seeds: dict, cfg: Optional[FitConfig] = None, fcfg: Optional[Fo
     scov = np.ascontiguousarray(fcfg.seed_cov, dtype=np.float64)
     ns, nc, nr = st.shape[0], y.shape[0], cfg.n_rows
     rx = cfg.row_x()
-    c = _Cfg(cfg.bz, cfg.chi2_max, cfg.xx0, cfg.mass, cfg.snp_max, (ctypes.c_double * 5)(*cfg.seed_cov),
-             cfg.min_clusters, cfg.n_rows, rx.ctypes.data, cfg.restart_scale)
+    c = _cfg_struct(cfg, rx)
     fc = _FollowCfg(fcfg.window_sigma, fcfg.nominal_v, fcfg.max_miss, fcfg.tan_edge, fcfg.z_max)
     out = dict(att=np.zeros((ns, nr), np.int32), n_att=np.zeros(ns, np.int32), status=np.zeros(ns, np.int32),
                state=np.zeros((ns, 5)), best2=np.zeros((ns, nr, 2)), edge=np.zeros((ns, nr)))

@@ -25,7 +25,10 @@
  *   lost the track for a stretch, typically after an outlier at the first
  *   cluster) it restarts instead from a fresh three-point seed at the
  *   outermost cluster;
- *   outputs at the innermost cluster.
+ *   outputs at the innermost cluster;
+ *   optional mean energy loss in a thin layer at every crossed row, crossed
+ *   right after the row's cluster in outward motion (outward pass: after the
+ *   update and the scattering; inward pass: added back before the update).
  * Status rule: clusters are validated when the outward pass reaches them, so the
  * first offending cluster decides; NaN never trips a numerical limit (it flows
  * to that cluster), and a completed fit with a non-finite state or covariance
@@ -38,8 +41,11 @@
 #include <string.h>
 
 #define ORC_KB 0.299792458e-2 /* GeV / (cm T) */
+#define ORC_ME 0.51099895e-3  /* electron mass, GeV */
+#define ORC_K 0.307075e-3     /* 4 pi N_A r_e^2 m_e c^2, GeV cm^2 / mol */
 
-enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5 };
+enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5,
+       ST_STOPPED = 6 };
 
 typedef struct {
   double bz;            /* Tesla */
@@ -52,6 +58,9 @@ typedef struct {
   int32_t n_rows;
   const float *row_x;   /* n_rows pad-row plane positions (cm) */
   double restart_scale; /* inward restart covariance: diag(min(restart_scale * C_out_ii, seed_cov_i)) */
+  double xrho;          /* energy-loss layer per crossed row, g/cm^2 (0: no energy loss) */
+  double eloss_za;      /* Z/A of its material */
+  double eloss_i;       /* mean excitation energy of its material, GeV */
 } orc_config;
 
 typedef struct {
@@ -203,6 +212,67 @@ void orc_ms_noise(const double p[5], double C[25], double xx0, double mass) {
 }
 
 /* ---------------------------------------------------------------------------
+ * Mean ionisation energy loss (Bethe formula as in the PDG Review of Particle
+ * Physics, passage of particles through matter, for |charge| 1 and without the
+ * density-effect term):
+ *   -dE/dx = K (Z/A) (1/beta^2) [ 1/2 ln(2 m_e c^2 beta^2 gamma^2 W_max / I^2) - beta^2 ],
+ *   W_max = 2 m_e c^2 beta^2 gamma^2 / (1 + 2 gamma m_e/M + (m_e/M)^2),
+ * in GeV cm^2/g for momentum p and mass M (GeV).  Readings: beta gamma is
+ * capped at 1e5 and the value clamped at 0 where the formula turns negative.
+ * ------------------------------------------------------------------------- */
+double orc_dedx(double p, double mass, double za, double i_gev) {
+  double E = sqrt(p * p + mass * mass);
+  double beta2 = (p * p) / (E * E);
+  double bg2 = (p * p) / (mass * mass);
+  if (bg2 > 1e10) bg2 = 1e10;
+  double gamma = sqrt(1.0 + bg2);
+  double ratio = ORC_ME / mass;
+  double wmax = 2.0 * ORC_ME * bg2 / (1.0 + 2.0 * gamma * ratio + ratio * ratio);
+  double v = ORC_K * za / beta2 * (0.5 * log(2.0 * ORC_ME * bg2 * wmax / (i_gev * i_gev)) - beta2);
+  return v > 0.0 ? v : 0.0;
+}
+
+/* ---------------------------------------------------------------------------
+ * The energy-loss layer of one pad row: x rho along the row normal, so
+ * xrho sqrt(1+t^2)/sqrt(1-sinphi^2) along the path.  dir = +1 when the pass
+ * moves with the particle (outward): E' = E - dE(E), the loss taken at the
+ * energy before the layer.  dir = -1 against it (inward): the energy before
+ * the layer solves E' - dE(E') = E; one fixed-point step from dE(E) gives it
+ * to O(dE^3).  The momentum scales by p'/p at fixed angles, so
+ * q/pT -> q/pT * k with k = p/p', and the covariance transforms with the
+ * Jacobian diag(1,1,1,1,k) (the loss taken as fixed).  Returns ST_STOPPED
+ * when p'^2 differs from p^2 by more than 50 % (also for the first estimate
+ * of the inward step).
+ * ------------------------------------------------------------------------- */
+int orc_eloss(double p[5], double C[25], const orc_config *c, double dir) {
+  if (!(c->xrho > 0.0)) return ST_OK;
+  double s = p[2], t = p[3], w = p[4];
+  double tt = 1.0 + t * t;
+  if (!(w * w / tt > 1e-30)) return ST_OK; /* p above 1e15 GeV (or infinite): no loss */
+  double mom = sqrt(tt) / fabs(w);
+  double m = sqrt(c->mass * c->mass);
+  double E = sqrt(mom * mom + m * m);
+  double path = c->xrho * sqrt(tt) / sqrt(1.0 - s * s);
+  double dE = orc_dedx(mom, m, c->eloss_za, c->eloss_i) * path;
+  double E2 = E - dir * dE;
+  double p2sq = E2 * E2 - m * m;
+  if (dir < 0.0) {
+    if (fabs(p2sq / (mom * mom) - 1.0) > 0.5) return ST_STOPPED;
+    dE = orc_dedx(sqrt(p2sq), m, c->eloss_za, c->eloss_i) * path;
+    E2 = E + dE;
+    p2sq = E2 * E2 - m * m;
+  }
+  if (fabs(p2sq / (mom * mom) - 1.0) > 0.5) return ST_STOPPED;
+  double k = mom / sqrt(p2sq);
+  p[4] = w * k;
+  for (int j = 0; j < 5; ++j) {
+    C[4 * 5 + j] *= k;
+    C[j * 5 + 4] *= k;
+  }
+  return ST_OK;
+}
+
+/* ---------------------------------------------------------------------------
  * Three-point seed: circle through clusters a=0, b=n/2, c=n-1 in the (x, y)
  * plane.  Signed curvature from the triangle (kappa = 2 cross / (|ab||ac||bc|)),
  * direction at a from the chord a->c minus half the turned angle,
@@ -284,6 +354,7 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
         cov_transport(C, F);
         xcur = xr;
         orc_ms_noise(p, C, c->xx0, c->mass);
+        if ((status = orc_eloss(p, C, c, 1.0)) != ST_OK) goto emit;
       }
     }
     if ((status = orc_propagate(p, xcur, x[k], c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
@@ -296,6 +367,8 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
     if (o->chi2_out_c) o->chi2_out_c[k] = chi2;
     if (acc) o->accept[k] |= 1;
     orc_ms_noise(p, C, c->xx0, c->mass);
+    /* the energy-loss layer of row[k], crossed after its cluster */
+    if ((status = orc_eloss(p, C, c, 1.0)) != ST_OK) goto emit;
   }
 
   /* ---- inward pass restart.  If the outward pass accepted at least 90 % of
@@ -337,6 +410,7 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
         memcpy(p, pn, sizeof(pn));
         cov_transport(C, F);
         xcur = xr;
+        if ((status = orc_eloss(p, C, c, -1.0)) != ST_OK) goto emit;
         orc_ms_noise(p, C, c->xx0, c->mass);
       }
     }
@@ -344,6 +418,8 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
     memcpy(p, pn, sizeof(pn));
     cov_transport(C, F);
     xcur = x[k];
+    /* moving inward, the layer of row[k] comes before its cluster: its loss is added back first */
+    if ((status = orc_eloss(p, C, c, -1.0)) != ST_OK) goto emit;
     double chi2;
     int acc;
     if ((status = orc_update(p, C, y[k], z[k], sy2[k], sz2[k], c->chi2_max, &chi2, &acc)) != ST_OK) goto emit;

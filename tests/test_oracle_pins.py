@@ -464,3 +464,115 @@ def test_following_invariants():
         b2 = r["best2"][t, rows]
         assert np.all(b2[:, 0] <= cfg.chi2_max) and np.all(b2[:, 0] <= b2[:, 1])
     assert set(np.unique(r["status"])) <= {0, 1, 2}
+
+
+# ---------------------------------------------------------------- energy loss
+PROTON = 0.938272
+
+
+def test_minimum_ionisation_matches_the_pdg_tables():
+    """Bethe formula minimum for neon (Z/A 0.49555, I 137 eV) and argon
+    (0.45059, 188 eV): the PDG atomic and nuclear properties tables list
+    1.724 and 1.519 MeV cm^2/g, at beta gamma near 3.2 (Review of Particle
+    Physics, passage of particles through matter: minimum near beta gamma 3-3.5)."""
+    mu = 0.1056584
+    bg = np.exp(np.linspace(np.log(0.5), np.log(50.0), 3000))
+    for za, i_ev, table in ((0.49555, 137.0, 1.724), (0.45059, 188.0, 1.519)):
+        v = np.array([oracle.dedx(b * mu, mu, za, i_ev) for b in bg]) * 1e3
+        k = int(np.argmin(v))
+        assert abs(v[k] / table - 1.0) < 3e-3, (za, v[k])
+        assert 3.0 < bg[k] < 3.6
+    # at fixed beta gamma the stopping power hardly depends on the mass (only through W_max)
+    assert abs(oracle.dedx(3.2 * PROTON, PROTON) / oracle.dedx(3.2 * mu, mu) - 1.0) < 0.03
+    # 1/beta^2 rise below the minimum: a proton at 0.3 GeV loses several times more than at minimum
+    assert 3.0 < oracle.dedx(0.3, PROTON) / oracle.dedx(3.2 * PROTON, PROTON) < 8.0
+
+
+def _track_state(p_gev, s=0.3, t=0.5, q=1.0):
+    return np.array([1.0, -2.0, s, t, q * np.sqrt(1 + t * t) / p_gev])
+
+
+def test_energy_loss_layers_integrate_the_stopping_power():
+    """150 outward layers (Euler steps of the fit) against an ODE solution of
+    dE/dn = -S(p) x rho / (cos lambda cos phi) (scipy solve_ivp, tight tolerance);
+    the loss taken is about 2 % of the momentum, so a wrong path factor, sign or
+    momentum scaling shows at the 1e-3 level."""
+    from scipy.integrate import solve_ivp
+    cfg = _cfg(xrho=0.02, mass=PROTON)
+    s, t, p0 = 0.3, 0.5, 0.6
+    st, C = _track_state(p0, s, t), np.eye(5)
+    for _ in range(150):
+        rc, st, C = oracle.eloss_step(st, C, cfg, 1.0)
+        assert rc == 0
+    p_fit = np.sqrt(1 + t * t) / abs(st[4])
+    path = 0.02 * np.sqrt(1 + t * t) / np.sqrt(1 - s * s)
+
+    def rhs(_, E):
+        p = np.sqrt(E[0] ** 2 - PROTON ** 2)
+        return [-oracle.dedx(p, PROTON) * path]
+
+    E0 = np.hypot(p0, PROTON)
+    sol = solve_ivp(rhs, (0.0, 150.0), [E0], rtol=1e-12, atol=1e-14)
+    p_ode = np.sqrt(sol.y[0, -1] ** 2 - PROTON ** 2)
+    assert 0.01 < 1 - p_fit / p0 < 0.05
+    assert abs(p_fit / p_ode - 1.0) < 2e-5
+    # angles and positions untouched
+    assert np.array_equal(st[:4], _track_state(p0, s, t)[:4])
+
+
+def test_energy_loss_inward_step_inverts_the_outward_step():
+    cfg = _cfg(xrho=0.02, mass=PROTON)
+    rng = np.random.default_rng(17)
+    for _ in range(20):
+        st0 = _track_state(rng.uniform(0.4, 3.0), rng.uniform(-0.7, 0.7), rng.uniform(-1, 1), rng.choice([-1.0, 1.0]))
+        A = rng.normal(size=(5, 5))
+        C0 = A @ A.T + np.eye(5)
+        rc, st1, C1 = oracle.eloss_step(st0, C0, cfg, 1.0)
+        assert rc == 0 and abs(st1[4]) > abs(st0[4])  # the particle slowed down: |q/pT| grows
+        k = st1[4] / st0[4]
+        J = np.diag([1, 1, 1, 1, k])
+        assert np.allclose(C1, J @ C0 @ J.T, rtol=1e-14, atol=0)
+        rc, st2, C2 = oracle.eloss_step(st1, C1, cfg, -1.0)
+        assert rc == 0
+        assert abs(st2[4] / st0[4] - 1.0) < 1e-9  # the fixed-point step leaves O(dE^3)
+        assert np.allclose(C2, C0, rtol=1e-8)
+
+
+def test_energy_loss_stops_a_slow_particle_and_ignores_a_massless_limit():
+    cfg = _cfg(xrho=1.0, mass=PROTON)
+    assert oracle.eloss_step(_track_state(0.1), np.eye(5), cfg, 1.0)[0] == 6
+    assert oracle.eloss_step(_track_state(0.1), np.eye(5), cfg, -1.0)[0] == 6
+    st = _track_state(0.1)
+    st[4] = 0.0  # infinite momentum: nothing to lose
+    rc, st2, _ = oracle.eloss_step(st, np.eye(5), cfg, 1.0)
+    assert rc == 0 and st2[4] == 0.0
+    rc, st2, _ = oracle.eloss_step(_track_state(0.5), np.eye(5), _cfg(xrho=0.0, mass=PROTON), 1.0)
+    assert rc == 0 and np.array_equal(st2, _track_state(0.5))
+
+
+def test_energy_loss_fit_recovers_the_truth_of_the_generator():
+    """Noise-free protons through thick layers (0.05 g/cm^2 per row), simulated
+    by the generator's own stopping power, on tracks of 100+ clusters with
+    rows lost to dropout (their layers count too).  With
+    energy loss the fit returns the true q/pT at every cluster (inward states)
+    to the floor of a frame without any energy loss -- which also fixes where
+    the inward pass adds a layer back (before the row's update: after it, every
+    inward state is off by one layer's loss); without it the fit is off by percents."""
+    kw = dict(truth=True, sigma_y=0.0, sigma_z=0.0, seed=5, n_tracks=200, mass=PROTON, pt_min=0.5, pt_max=2.0,
+              min_clusters=100, p_drop=0.1)  # 10 % of the rows crossed without a cluster
+    f = tpcgen.generate("sector1k", xrho=0.05, **kw)
+    f0 = tpcgen.generate("sector1k", **kw)
+    first, first0 = f.offsets[:-1], f0.offsets[:-1]
+    r = oracle.fit(f, _cfg(xx0=0.0, xrho=0.05, mass=PROTON, min_clusters=100), diagnostics=True)
+    r_no = oracle.fit(f, _cfg(xx0=0.0, mass=PROTON, min_clusters=100))
+    r0 = oracle.fit(f0, _cfg(xx0=0.0, mass=PROTON, min_clusters=100), diagnostics=True)
+    assert np.all(r["status"] == 0) and np.all(r0["status"] == 0)
+    rel = np.abs(r["state_in_c"][:, 4] / f.truth[:, 4] - 1)
+    rel0 = np.abs(r0["state_in_c"][:, 4] / f0.truth[:, 4] - 1)
+    assert np.median(rel) < 2 * np.median(rel0) and rel.max() < 2 * rel0.max()
+    fin = np.abs(r["state"][:, 4] / f.truth[first, 4] - 1)
+    fin0 = np.abs(r0["state"][:, 4] / f0.truth[first0, 4] - 1)
+    assert fin.max() < 2 * fin0.max() + 1e-7
+    rel_no = np.abs(r_no["state"][:, 4] / f.truth[first, 4] - 1)
+    assert np.median(rel_no) > 1e-3 and rel_no.max() > 3e-2
+    assert np.abs(r["state_in_c"][:, :2] - f.truth[:, :2]).max() < 2e-5

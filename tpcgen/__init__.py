@@ -54,6 +54,7 @@ class _Config(ctypes.Structure):
         ("tgl_max", ctypes.c_double), ("z_max", ctypes.c_double), ("snp_max", ctypes.c_double),
         ("max_attempts", ctypes.c_int32), ("n_threads", ctypes.c_int32),
         ("track_id_offset", ctypes.c_int64),
+        ("xrho", ctypes.c_double), ("eloss_za", ctypes.c_double), ("eloss_i_ev", ctypes.c_double),
     ]
 
 
@@ -87,6 +88,7 @@ BASE = dict(
     sigma_y=0.1, sigma_z=0.1, pt_mode=0, pt_min=0.2, pt_max=10.0, pt_mean=0.6,
     sector_half_angle=math.radians(10.0), vtx_sigma=0.01, tgl_max=0.9, z_max=250.0,
     snp_max=0.99, min_clusters=10, max_attempts=1000,
+    xrho=0.0, eloss_za=0.49555, eloss_i_ev=137.0,  # no energy loss unless xrho > 0 (neon material)
 )
 PRESETS = {
     # single sector, 1,000 tracks, no scattering / dropout / outliers

@@ -3,8 +3,8 @@
  *
  * Produces helix tracks in a uniform solenoid field crossing the TPC pad-row
  * planes of one sector frame, with Gaussian cluster noise, optional Highland
- * multiple-scattering kicks, random cluster dropout and uniformly displaced
- * outlier clusters.  This stands in for the ALICE Monte-Carlo and Pb-Pb data of
+ * multiple-scattering kicks, optional mean ionisation energy loss in every
+ * crossed row, random cluster dropout and uniformly displaced outlier clusters.  This stands in for the ALICE Monte-Carlo and Pb-Pb data of
  * the paper's Sec. 7, which are not available.
  *
  * The trajectory is represented as a GLOBAL CIRCLE (centre, radius) in the
@@ -48,6 +48,9 @@ typedef struct {
   int32_t max_attempts;
   int32_t n_threads;
   int64_t track_id_offset;  /* added to the track index to key the RNG */
+  double xrho;              /* g/cm^2 of material per crossed row (mean energy loss); 0 = none */
+  double eloss_za;          /* its Z/A */
+  double eloss_i_ev;        /* its mean excitation energy, eV */
 } tpcgen_config;
 
 typedef struct {
@@ -59,6 +62,22 @@ typedef struct {
   uint8_t *flags;   /* per cluster: bit0 outlier */
   double *truth_vertex; /* 6 per track: vx, vy, vz, phi0, tanl0, q/pT0 */
 } tpcgen_out;
+
+/* Mean stopping power in MeV cm^2/g of a singly charged particle of momentum
+ * p and mass m (GeV) in a material (Z/A, I in eV): the Bethe formula of the
+ * PDG review (no density effect), with the maximum energy transfer to one
+ * electron in MeV. */
+static double stopping_power(double p, double m, double za, double i_ev) {
+  const double me_mev = 0.51099895;
+  double e = sqrt(p * p + m * m);
+  double beta = p / e, gam = e / m, bg = p / m;
+  double mr = 0.51099895e-3 / m;
+  double tmax = 2.0 * me_mev * bg * bg / (1.0 + 2.0 * gam * mr + mr * mr);
+  double i_mev = i_ev * 1e-6;
+  double L = 0.5 * log(2.0 * me_mev * bg * bg * tmax / (i_mev * i_mev)) - beta * beta;
+  double v = 0.307075 * za * L / (beta * beta);
+  return v > 0 ? v : 0;
+}
 
 /* ---- counter-based RNG ---------------------------------------------------- */
 typedef struct { uint64_t s; } rng_t;
@@ -193,6 +212,16 @@ static int gen_one(const tpcgen_config *c, rng_t *r, int64_t base, const tpcgen_
       phi = atan2(dy3, dx3);
       tgl = dz3 / dt;
       pt = p * dt / sqrt(dt * dt + dz3 * dz3);
+    }
+    /* mean energy loss in the row's layer (thickness xrho along x), after the kick */
+    if (c->xrho > 0) {
+      double path = c->xrho * sqrt(1.0 + tgl * tgl) / fabs(cos(phi));
+      double de = 1e-3 * stopping_power(p, c->mass, c->eloss_za, c->eloss_i_ev) * path; /* GeV */
+      double e2 = sqrt(p * p + c->mass * c->mass) - de;
+      if (!(e2 > c->mass * (1.0 + 1e-6))) break; /* stopped in this row */
+      double p2 = sqrt(e2 * e2 - c->mass * c->mass);
+      pt *= p2 / p;
+      p = p2;
     }
   }
   return n;
