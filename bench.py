@@ -46,10 +46,14 @@ WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT
              "tracking": "track following + gather + fit of a 50,000-track frame of the 36-sector detector "
                          "(x/X0 5e-4 per row, 5% dropout, 1% outliers, seed 0); seeds: the true state at each "
                          "track's first cluster smeared by 0.3 of the seed sigma (seeded)",
+             "pbpb2m_eloss": "the Pb-Pb-scale frame with mean energy loss (Bethe, neon, 0.0145 g/cm^2 per row, the "
+                             "layer of x/X0 5e-4) in the generator and in the fit (its energy-loss kernel); pions",
              "serving": "time frames arriving as a Poisson process at 50 frames/s, clusters per frame log-normal "
                         "(median 20 M, sigma_ln 0.6, 1-120 M), tracks as in the 36-sector detector workload; a pool "
                         "of 64 frames (windows of one pre-generated 1.1 M-track frame) replayed on a seeded "
                         "arrival schedule; 120 GB HBM budget, 8 slots"}
+# fit parameters of a workload beyond the defaults (library / oracle names)
+FIT_PARAMS = {"pbpb2m_eloss": ({"xrho_per_row": 0.0145}, {"xrho": 0.0145})}
 FP64_PER_CLUSTER = 11         # FP64 lane-instructions per cluster: 4 (outward update) + 7 (inward update + sum)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
@@ -131,7 +135,7 @@ def kernel_source_hash() -> str:
 ISSUE_PER_SM_CLK = 4          # warp instructions issued per SM per clock (4 schedulers, one each)
 
 
-def profiled_counters(n_clusters: int, launch: tuple):
+def profiled_counters(n_clusters: int, launch: tuple, variant: str = ""):
     """ncu counters of one fit-kernel launch from the committed record
     (profiles/fit_kernel_counters.json): DRAM bytes and warp instructions,
     for this frame when it is the captured one, else scaled by clusters for a
@@ -142,6 +146,10 @@ def profiled_counters(n_clusters: int, launch: tuple):
         return None, "no ncu record"
     with open(p) as fh:
         d = json.load(fh)
+    if variant:
+        if variant not in d.get("variants", {}):
+            return None, f"no ncu record of the {variant} variant"
+        d = dict(d["variants"][variant], kernel_sha256_16=d.get("kernel_sha256_16"))
     if d.get("kernel_sha256_16") != kernel_source_hash():
         return None, "kernel changed since the ncu capture"
     if tuple(launch) != tuple(d.get("launch", (0, 0))):
@@ -156,7 +164,7 @@ def profiled_counters(n_clusters: int, launch: tuple):
     return out, note
 
 
-def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz):
+def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz, variant: str = ""):
     """Roofline of the fit kernel.  Primary: instruction issue (the unit that
     binds), achieved = ncu warp instructions per launch / mean launch time,
     peak = 4 per SM per clock at the sampled SM clock.  Beside it the
@@ -164,7 +172,7 @@ def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz):
     live FP64 FMA probe, FP32 flops against 2x the FP32 FMA probe, HBM bytes
     (22 per cluster + 108 per track) against the measured copy bandwidth."""
     peaks, peak_src = measured_peaks()
-    c, note = profiled_counters(nc, launch)
+    c, note = profiled_counters(nc, launch, variant)
     fp64 = FP64_PER_CLUSTER * nc_fit / fit_s
     hbm = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
     sub = {
@@ -195,7 +203,29 @@ def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz):
     return roof
 
 
-def cpu_baseline(frame, seconds_target: float = 15.0):
+def link_rates(nbytes: int = 1 << 30, reps: int = 3) -> dict:
+    """Host<->device copy rates of this machine (pinned host memory, one copy at a time), in GB/s."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            b.synchronize()
+            best = min(best, a.elapsed_time(b) * 1e-3)
+        out[name] = nbytes / best / 1e9
+    del h, d
+    return out
+
+
+def cpu_baseline(frame, seconds_target: float = 15.0, workload: str = "pbpb2m"):
     """Time the FP64 oracle with every host core on a bounded sample of the
     frame: the whole frame when a 20k-track probe predicts <= ~2x the target,
     else the first tracks sized for about `seconds_target` seconds."""
@@ -205,13 +235,13 @@ def cpu_baseline(frame, seconds_target: float = 15.0):
     n = min(20_000, frame.n_tracks)
     sub = frame.subset(0, n)
     t0 = time.perf_counter()
-    oracle.fit(sub, oracle.FitConfig(), threads=cores)
+    oracle.fit(sub, oracle.FitConfig(**FIT_PARAMS.get(workload, ({}, {}))[1]), threads=cores)
     dt = time.perf_counter() - t0
     predicted = dt * frame.n_clusters / max(sub.n_clusters, 1)
     n2 = frame.n_tracks if predicted <= 2 * seconds_target else int(n * seconds_target / max(dt, 1e-6))
     sub = frame.subset(0, min(n2, frame.n_tracks))
     t0 = time.perf_counter()
-    r = oracle.fit(sub, oracle.FitConfig(), threads=cores)
+    r = oracle.fit(sub, oracle.FitConfig(**FIT_PARAMS.get(workload, ({}, {}))[1]), threads=cores)
     dt = time.perf_counter() - t0
     what = "the whole frame" if sub.n_tracks == frame.n_tracks else f"the first {sub.n_tracks} tracks of the frame"
     return {"value": sub.n_clusters / dt, "unit": "clusters/s", "cores": int(r["threads"]), "kind": "oracle",
@@ -238,10 +268,10 @@ def run_reference(args, ws, rank):
         frame = tpcgen.generate(args.workload, n_tracks=n, seed=0)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.fit(frame.subset(0, min(n, 2000)), oracle.FitConfig(), threads=cores)
+        oracle.fit(frame.subset(0, min(n, 2000)), oracle.FitConfig(**FIT_PARAMS.get(args.workload, ({}, {}))[1]), threads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.fit(frame, oracle.FitConfig(), threads=cores)
+        oracle.fit(frame, oracle.FitConfig(**FIT_PARAMS.get(args.workload, ({}, {}))[1]), threads=cores)
     dt = time.perf_counter() - t0
     value = frame.n_clusters * args.steps / dt
     line = {
@@ -387,7 +417,7 @@ def run_events(args, ws, rank, local, T, torch, dist, probe):
                "path": "tpcfit_fit of the concatenated events, TPCFIT_MEM_HOST pinned, chunked overlap"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(frame)
+        cpu = cpu_baseline(frame, workload=args.workload)
     if rank == 0:
         sizes = np.diff(ev)
         line = {
@@ -804,7 +834,8 @@ def main():
     dev = F()
     for k in names:
         setattr(dev, k, torch.from_numpy(np.ascontiguousarray(getattr(frame, k))).cuda())
-    fx = T.Fitter(device=local, block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm)
+    fx = T.Fitter(device=local, block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
+                  **FIT_PARAMS.get(args.workload, ({}, {}))[0])
     res = T.alloc_result(nt, nc, device=torch.device("cuda", local))
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
@@ -845,7 +876,8 @@ def main():
     nc_fit = int(lens[ok].sum())
     fit_s = tm["fit_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    roofline = fit_roofline(nc, nt, nc_fit, fit_s, (tm["fit_grid"], tm["fit_block"]), probe, sms, clk.get("sm_mhz"))
+    roofline = fit_roofline(nc, nt, nc_fit, fit_s, (tm["fit_grid"], tm["fit_block"]), probe, sms, clk.get("sm_mhz"),
+                            "eloss" if args.workload == "pbpb2m_eloss" else "")
     roofline["fp32_fma_peak_per_s"] = probe["fp32_fma_per_s"]
     # the same steps with the track-model compression residual codes written (4 B per cluster more)
     res_r = T.alloc_result(nt, nc, device=torch.device("cuda", local), residuals=True)
@@ -921,12 +953,17 @@ def main():
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
+        h2d_b, d2h_b = int(21 * nc + 8 * (nt + 1)), int(100 * nt + nc)
+        link = link_rates()
         e2e = {"value": nc_all * args.e2e_steps / dt, "unit": "clusters/s",
-               "h2d_bytes_per_step": int(21 * nc + 8 * (nt + 1)), "d2h_bytes_per_step": int(100 * nt + nc),
-               "ms_per_step": dt / args.e2e_steps * 1e3, "path": "tpcfit_fit, TPCFIT_MEM_HOST pinned, chunked overlap"}
+               "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
+               "ms_per_step": dt / args.e2e_steps * 1e3, "path": "tpcfit_fit, TPCFIT_MEM_HOST pinned, chunked overlap",
+               "link": dict(link, floor_ms=1e3 * h2d_b / (link["h2d_gbs"] * 1e9),
+                            note="pinned copies of 1 GiB timed on this box; floor = the frame's host-to-device "
+                                 "bytes at that rate")}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(frame)
+        cpu = cpu_baseline(frame, workload=args.workload)
     if rank == 0:
         line = {
             "metric": "clusters/s fitted on 1 GB300 (FP32 fit, FP64 innovation inverse and chi2)",

@@ -60,6 +60,7 @@ extern "C" {
 #define TPCFIT_TRACK_NOT_PD 3     /* innovation matrix not positive definite */
 #define TPCFIT_TRACK_NONFINITE 4  /* non-finite cluster value, or non-finite fitted state */
 #define TPCFIT_TRACK_BAD_INPUT 5  /* rows not ascending, row >= n_rows, variance <= 0, bad offsets */
+#define TPCFIT_TRACK_STOPPED 6    /* energy loss: one row would change p^2 by more than 50 % */
 
 /* ticket states for tpcfit_poll */
 #define TPCFIT_PENDING 0
@@ -90,7 +91,18 @@ typedef struct tpcfit_config {
   int32_t sort_tracks;    /* 1: fit tracks longest-first (default); 0: in frame order */
   float res_step_y_cm;    /* residual code step in y (0.01 cm), see tpcfit_result.res_y */
   float res_step_z_cm;    /* residual code step in z (0.01 cm) */
-  int32_t reserved[5];
+  /* Mean ionisation energy loss (Bethe formula without density effect, |charge| 1,
+   * particle of mass mass_gev) in a thin layer at every crossed pad row, of
+   * x*rho = xrho_per_row g/cm^2 along the row normal.  The layer of row r is
+   * crossed right after the row-r cluster in outward motion: the outward pass
+   * subtracts its loss after the update at row r, the inward pass adds it back
+   * before the update.  q/pT scales by p/p' and row/column 4 of the covariance
+   * with it; no straggling.  A row that would change p^2 by more than 50 %
+   * ends the fit with TPCFIT_TRACK_STOPPED. */
+  float xrho_per_row;     /* g/cm^2 per crossed row (0 = no energy loss, the default) */
+  float eloss_z_over_a;   /* Z/A of the layer material (0 = neon, 0.49555) */
+  float eloss_i_ev;       /* mean excitation energy of the material in eV (0 = neon, 137) */
+  int32_t reserved[2];
   int64_t host_chunk_clusters; /* host frames are copied and fitted in chunks of about this many clusters (16M) */
 } tpcfit_config;
 

@@ -30,7 +30,7 @@ __all__ = ["TpcfitError", "Config", "default_config", "create", "destroy", "fit"
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_NOTFOUND, E_NODEV = 0, -1, -2, -3, -4, -5, -6, -7
 MEM_HOST, MEM_DEVICE = 0, 1
 PENDING, DONE, FAILED = 0, 1, 2
-STATUS_NAMES = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT"}
+STATUS_NAMES = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT", 6: "STOPPED"}
 
 
 class TpcfitError(RuntimeError):
@@ -47,7 +47,8 @@ class Config(ctypes.Structure):
         ("row_x0_cm", ctypes.c_float), ("row_pitch_cm", ctypes.c_float), ("hbm_budget_bytes", ctypes.c_uint64),
         ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32), ("block_threads", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32), ("sort_tracks", ctypes.c_int32), ("res_step_y_cm", ctypes.c_float),
-        ("res_step_z_cm", ctypes.c_float), ("reserved", ctypes.c_int32 * 5),
+        ("res_step_z_cm", ctypes.c_float), ("xrho_per_row", ctypes.c_float), ("eloss_z_over_a", ctypes.c_float),
+        ("eloss_i_ev", ctypes.c_float), ("reserved", ctypes.c_int32 * 2),
         ("host_chunk_clusters", ctypes.c_int64),
     ]
 

@@ -11,7 +11,8 @@
 
 namespace tpcfit {
 
-enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5 };
+enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5,
+       ST_STOPPED = 6 };
 
 // ---------------------------------------------------------------------------
 // binary32 -> binary64 widening with integer operations (IEEE 754: the
@@ -199,6 +200,63 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   fast_two_sum(T.c[9], fmaf(th2, tt * tt, T.c9l), T.c[9], T.c9l);
   fast_two_sum(T.c[14], fmaf(th2, w * w * t * t, T.c14l), T.c[14], T.c14l);
   T.c[13] = fmaf(th2, tt * w * t, T.c[13]);
+}
+
+// Mean stopping power (Bethe formula, PDG Review of Particle Physics, passage
+// of particles through matter; |charge| 1, no density effect) from 1/p^2.
+// With m2p = m^2/p^2:  1/beta^2 = 1 + m2p,  (beta gamma)^2 = bg2 = min(1/m2p, 1e10),
+//   W_max = 2 m_e bg2 / D,  D = 1 + 2 gamma m_e/M + (m_e/M)^2,
+//   -dE/dx = K Z/A (1/beta^2) [ln(2 m_e bg2 W_max / I^2)/2 - beta^2]
+//          = kza ((1/beta^2) ln(a^2/D)/2 - 1),  a = (2 m_e / I) bg2,
+// clamped at 0 where the formula turns negative (GeV cm^2/g).
+__device__ __forceinline__ float stopping_power(float pinv2, float kza, float a_coef, float ratio, float mass2) {
+  const float m2p = mass2 * pinv2;
+  const float ib2 = 1.0f + m2p;
+  const float bg2 = fminf(1.0f / m2p, 1e10f);
+  const float gam = sqrtf(1.0f + bg2);
+  const float aa = a_coef * bg2;
+  const float D = fmaf(2.0f * gam, ratio, fmaf(ratio, ratio, 1.0f));
+  return fmaxf(kza * fmaf(0.5f * ib2, logf(aa * (aa / D)), -1.0f), 0.0f);
+}
+
+// The energy-loss layer of one pad row: x rho along the row normal, so
+// xrho / (cos lambda cos phi) along the path.  dir = +1 (outward: the particle
+// loses dE, evaluated at its momentum before the layer) or -1 (inward: the
+// loss is added back; the energy before the layer solves E_b - dE(E_b) = E,
+// taken with one fixed-point step from dE(E), error O(dE^3)).
+// p'^2 = p^2 (1 - r) with r = s (2E - s) / p^2, s = dir dE, written without
+// E - m cancellation; q/pT grows by k = (1 - r)^-1/2, applied as w (k - 1) with
+// k - 1 = r / (sqrt(1-r) (1 + sqrt(1-r))), exact to rounding even when r is
+// of order 1e-7; row/column 4 of the covariance scale by k.  Returns false
+// when |r| > 1/2 (the fit stops there); momenta above 1e15 GeV lose nothing.
+__device__ __forceinline__ bool eloss(Trk &T, float xrho, float kza, float a_coef, float ratio, float mass2,
+                                      float dir) {
+  const float s = T.snp(), t = T.tl(), w = T.w();
+  const float tt = fmaf(t, t, 1.0f);
+  const float cs2 = fmaf(-s, s, 1.0f);
+  const float pinv2 = (w * w) / tt;  // 1/p^2
+  if (!(pinv2 > 1e-30f)) return true;
+  const float path = xrho * sqrtf(tt / cs2);
+  const float e2p = 2.0f * sqrtf(fmaf(mass2, pinv2, 1.0f) * pinv2);  // 2 E / p^2
+  float sd = dir * (stopping_power(pinv2, kza, a_coef, ratio, mass2) * path);
+  float r = sd * fmaf(-sd, pinv2, e2p);
+  if (dir < 0.0f) {
+    if (fabsf(r) > 0.5f) return false;
+    sd = -(stopping_power(pinv2 / (1.0f - r), kza, a_coef, ratio, mass2) * path);
+    r = sd * fmaf(-sd, pinv2, e2p);
+  }
+  if (fabsf(r) > 0.5f) return false;
+  const float q = sqrtf(1.0f - r);
+  const float km1 = r / (q * (1.0f + q));
+  T.dw = fmaf(w, km1, T.dw);
+  const float k = 1.0f + km1, k2 = k * k;
+  T.c[10] *= k;
+  T.c[11] *= k;
+  T.c[12] *= k;
+  T.c[13] *= k;
+  T.c[14] *= k2;
+  T.c14l *= k2;
+  return true;
 }
 
 // Error-free product of two binary32 numbers: a * b = p + e exactly.

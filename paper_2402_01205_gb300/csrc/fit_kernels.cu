@@ -261,7 +261,7 @@ __device__ __forceinline__ Clu read_staged(const float *stg, int lk, uint32_t ro
   return c;
 }
 
-template <int BLOCK>
+template <int BLOCK, bool ELOSS>
 __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
   const int st0 = A.status[t];
@@ -348,6 +348,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           }
         }
         if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
+        if (ELOSS && !eloss(T, A.xrho, A.el_kza, A.el_a, A.el_ratio, A.mass2, 1.0f)) { st = ST_STOPPED; break; }
         if (kc == n) break;
       }
       // ---------------- restart ----------------
@@ -411,6 +412,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           const float xt = has ? cand.x : s_rowx[r];
           if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
           xcur = xt;
+          // the layer of row r lies beyond the plane in outward motion: its loss is added back first
+          if (ELOSS && !eloss(T, A.xrho, A.el_kza, A.el_a, A.el_ratio, A.mass2, -1.0f)) { st = ST_STOPPED; break; }
           if (has) {
             bool acc;
             double chi2;
@@ -471,7 +474,9 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   A.status[t] = st;
 }
 
-template <int BLOCK, int MINB>
+// ELOSS: the variant with the energy-loss step (a separate instantiation, so
+// that the fit without it keeps its own register allocation and schedule).
+template <int BLOCK, int MINB, bool ELOSS>
 __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   float *s_rowx = reinterpret_cast<float *>(smem);
@@ -490,7 +495,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
     const int64_t i = (int64_t)base + lane;
     if (i < A.n_tracks) {
       const int64_t t = A.perm ? (int64_t)A.perm[i] : i;
-      fit_track<BLOCK>(A, t, bits, s_rowx, stg);
+      fit_track<BLOCK, ELOSS>(A, t, bits, s_rowx, stg);
     }
     __syncwarp();
   }
@@ -517,40 +522,45 @@ cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches) {
 
 // Raise the dynamic shared memory limit of one k_fit instantiation, once per
 // device (the attribute belongs to the function in the current device's context).
-template <int BLOCK, int MINB> static cudaError_t set_fit_smem() {
+template <int BLOCK, int MINB, bool ELOSS> static cudaError_t set_fit_smem() {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_fit<BLOCK, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem<BLOCK>());
+  e = cudaFuncSetAttribute(k_fit<BLOCK, MINB, ELOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fit_smem<BLOCK>());
   if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
 
-cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {
-  if (a.n_tracks <= 0) return cudaSuccess;
-  cudaError_t e;
-  if (block == 128) {
-    if ((e = set_fit_smem<128, 4>()) != cudaSuccess) return e;
-    k_fit<128, 4><<<grid, 128, fit_smem<128>(), stream>>>(a);
-  } else {
-    if ((e = set_fit_smem<256, 2>()) != cudaSuccess) return e;
-    k_fit<256, 2><<<grid, 256, fit_smem<256>(), stream>>>(a);
-  }
+template <int BLOCK, int MINB, bool ELOSS> static cudaError_t launch_fit_as(const FitArgs &a, int grid,
+                                                                             cudaStream_t stream) {
+  cudaError_t e = set_fit_smem<BLOCK, MINB, ELOSS>();
+  if (e != cudaSuccess) return e;
+  k_fit<BLOCK, MINB, ELOSS><<<grid, BLOCK, fit_smem<BLOCK>(), stream>>>(a);
   return cudaGetLastError();
 }
 
+cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  const bool el = a.xrho > 0.0f;
+  if (block == 128) return el ? launch_fit_as<128, 4, true>(a, grid, stream) : launch_fit_as<128, 4, false>(a, grid, stream);
+  return el ? launch_fit_as<256, 2, true>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
+}
+
+// Occupancy of the fit without energy loss (the variant is compiled under the
+// same launch bounds, so it reaches at least 512 threads per SM as well).
 int fit_blocks_per_sm(int block) {
   int n = 0;
   cudaError_t e;
   if (block == 128) {
-    set_fit_smem<128, 4>();
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<128, 4>, 128, fit_smem<128>());
+    set_fit_smem<128, 4, false>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<128, 4, false>, 128, fit_smem<128>());
   } else {
-    set_fit_smem<256, 2>();
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<256, 2>, 256, fit_smem<256>());
+    set_fit_smem<256, 2, false>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<256, 2, false>, 256, fit_smem<256>());
   }
   if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
@@ -569,7 +579,7 @@ int fit_default_blocks_per_sm(int block) {
 
 int fit_regs_per_thread() {
   cudaFuncAttributes at;
-  if (cudaFuncGetAttributes(&at, k_fit<256, 2>) != cudaSuccess) return -1;
+  if (cudaFuncGetAttributes(&at, k_fit<256, 2, false>) != cudaSuccess) return -1;
   return at.numRegs;
 }
 

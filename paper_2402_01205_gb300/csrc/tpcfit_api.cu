@@ -289,6 +289,7 @@ static int check_config(const tpcfit_config &c) {
     return fail(TPCFIT_E_INVAL, "block_threads must be 0, 128 or 256");
   if (c.blocks_per_sm < 0) return fail(TPCFIT_E_INVAL, "blocks_per_sm < 0");
   if (!(c.res_step_y_cm > 0.0f) || !(c.res_step_z_cm > 0.0f)) return fail(TPCFIT_E_INVAL, "residual steps must be > 0");
+  if (const char *why = check_eloss_params(c)) return fail(TPCFIT_E_INVAL, "%s", why);
   return TPCFIT_OK;
 }
 
@@ -407,16 +408,7 @@ FitArgs make_args(tpcfit_handle *h, const tpcfit_frame *f, const tpcfit_result *
   a.work = s.work;
   a.frame_error = s.err;
   a.row_x = h->d_rowx;
-  a.b = (float)(-0.299792458e-2 * (double)c.bz_tesla);
-  a.chi2_max = c.chi2_max;
-  a.chi2_max_d = (double)c.chi2_max;
-  a.xx0 = c.xx0_per_row;
-  a.mass2 = c.mass_gev * c.mass_gev;
-  a.snp_max = c.snp_max;
-  a.restart_scale = c.restart_scale;
-  for (int i = 0; i < 5; ++i) a.seed_cov[i] = c.seed_cov[i];
-  a.min_clusters = c.min_clusters;
-  a.n_rows = c.n_rows;
+  fit_params(a, c);
   return a;
 }
 

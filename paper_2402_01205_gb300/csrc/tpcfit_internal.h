@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "tpcfit.h"
+
 namespace tpcfit {
 
 constexpr int kMaxRows = 256;        // row index is uint8
@@ -37,9 +39,40 @@ struct FitArgs {
   float chi2_max;
   double chi2_max_d;
   float xx0, mass2, snp_max, restart_scale;
+  float xrho;                    // energy-loss layer per row (g/cm^2); 0 = none
+  float el_kza, el_a, el_ratio;  // K Z/A (GeV cm^2/g), 2 m_e / I, m_e / M
   float seed_cov[5];
   int32_t min_clusters, n_rows;
 };
+
+// The fit parameters of FitArgs from a configuration (both entry points).
+inline void fit_params(FitArgs &a, const tpcfit_config &c) {
+  a.b = (float)(-0.299792458e-2 * (double)c.bz_tesla);
+  a.chi2_max = c.chi2_max;
+  a.chi2_max_d = (double)c.chi2_max;
+  a.xx0 = c.xx0_per_row;
+  a.mass2 = c.mass_gev * c.mass_gev;
+  a.snp_max = c.snp_max;
+  a.restart_scale = c.restart_scale;
+  const double za = c.eloss_z_over_a > 0.0f ? c.eloss_z_over_a : 0.49555;  // neon: 10 / 20.1797
+  const double iev = c.eloss_i_ev > 0.0f ? c.eloss_i_ev : 137.0;            // neon
+  const double me = 0.51099895e-3;                                           // electron mass, GeV
+  a.xrho = c.xrho_per_row;
+  a.el_kza = (float)(0.307075e-3 * za);  // K = 0.307075 MeV cm^2 / mol
+  a.el_a = (float)(2.0 * me / (iev * 1e-9));
+  a.el_ratio = c.mass_gev > 0.0f ? (float)(me / (double)c.mass_gev) : 0.0f;
+  for (int i = 0; i < 5; ++i) a.seed_cov[i] = c.seed_cov[i];
+  a.min_clusters = c.min_clusters;
+  a.n_rows = c.n_rows;
+}
+
+// NULL, or why the energy-loss parameters of a configuration are invalid.
+inline const char *check_eloss_params(const tpcfit_config &c) {
+  if (!(c.xrho_per_row >= 0.0f) || !(c.eloss_z_over_a >= 0.0f) || !(c.eloss_i_ev >= 0.0f))
+    return "energy-loss parameters must be >= 0";
+  if (c.xrho_per_row > 0.0f && !(c.mass_gev > 0.0f)) return "energy loss needs mass_gev > 0";
+  return nullptr;
+}
 
 // Track following (tpcfit_follow.cu builds the cell grid; the kernel lives
 // with the fit's device code).  Cell of a cluster: ((sector * n_rows + row) *

@@ -101,6 +101,7 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   if (cfg.n_rows < 1 || cfg.n_rows > kMaxRows || !(cfg.snp_max > 0.f && cfg.snp_max < 1.f) ||
       !(cfg.chi2_max > 0.f) || cfg.device < 0 || cfg.device >= kMaxDevices)
     return fail(TPCFIT_E_INVAL, "configuration out of range");
+  if (const char *why = check_eloss_params(cfg)) return fail(TPCFIT_E_INVAL, why);
   if (cudaSetDevice(cfg.device) != cudaSuccess) {
     cudaGetLastError();
     return fail(TPCFIT_E_NODEV, "cannot select the CUDA device");
@@ -131,16 +132,7 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   a.seed = reinterpret_cast<float *>(sc + kSeedOff);
   a.perm = cfg.sort_tracks ? reinterpret_cast<int32_t *>(sc + kPermOff) : nullptr;
   a.row_x = reinterpret_cast<const float *>(sc + kRowxOff);
-  a.b = (float)(-0.299792458e-2 * (double)cfg.bz_tesla);
-  a.chi2_max = cfg.chi2_max;
-  a.chi2_max_d = (double)cfg.chi2_max;
-  a.xx0 = cfg.xx0_per_row;
-  a.mass2 = cfg.mass_gev * cfg.mass_gev;
-  a.snp_max = cfg.snp_max;
-  a.restart_scale = cfg.restart_scale;
-  for (int i = 0; i < 5; ++i) a.seed_cov[i] = cfg.seed_cov[i];
-  a.min_clusters = cfg.min_clusters;
-  a.n_rows = cfg.n_rows;
+  fit_params(a, cfg);
 
   // the row table as the handle-based path builds it (exact 162/151 pitch for the default geometry)
   double pitch = (double)cfg.row_pitch_cm;

@@ -32,7 +32,7 @@ def test_counter_record_matches_only_its_kernel_and_launch(monkeypatch):
 
 
 def test_roofline_fractions(monkeypatch):
-    monkeypatch.setattr(bench, "profiled_counters", lambda n, l: (
+    monkeypatch.setattr(bench, "profiled_counters", lambda n, l, v="": (
         {"dram_bytes": 64.0 * n, "warp_inst": 40.0 * n, "thread_inst": 40.0 * 28 * n, "fp32_flop_per_cluster": 700.0},
         "test"))
     nc, nt, t = 1_000_000, 10_000, 1e-3
@@ -48,7 +48,7 @@ def test_roofline_fractions(monkeypatch):
 
 
 def test_roofline_without_counters_falls_back_to_the_fp64_pipe(monkeypatch):
-    monkeypatch.setattr(bench, "profiled_counters", lambda n, l: (None, "no record"))
+    monkeypatch.setattr(bench, "profiled_counters", lambda n, l, v="": (None, "no record"))
     r = bench.fit_roofline(1000, 10, 1000, 1e-6, (1, 1), PROBE, 152, None)
     assert "FP64" in r["unit"] and r["traffic"] is None and r["frac"] == pytest.approx(11 * 1000 / 1e-6 / 5e11)
 

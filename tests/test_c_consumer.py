@@ -39,6 +39,14 @@ int main(int argc, char **argv) {
   c.block_threads = 96;
   CHECK(tpcfit_create(&c, &h) == TPCFIT_E_INVAL);
   tpcfit_default_config(&c);
+  CHECK(c.xrho_per_row == 0.0f && c.eloss_z_over_a == 0.0f && c.eloss_i_ev == 0.0f);
+  c.xrho_per_row = 0.01f;
+  c.mass_gev = 0.0f;  /* energy loss needs a mass */
+  CHECK(tpcfit_create(&c, &h) == TPCFIT_E_INVAL && h == 0);
+  c.mass_gev = 0.938f;
+  c.eloss_i_ev = -1.0f;
+  CHECK(tpcfit_create(&c, &h) == TPCFIT_E_INVAL && h == 0);
+  tpcfit_default_config(&c);
   int rc = tpcfit_create(&c, &h);
   if (have_gpu) {
     CHECK(rc == TPCFIT_OK && h != 0);

@@ -1,0 +1,102 @@
+"""CUDA fit with mean energy loss in the pad-row layers vs the FP64 oracle,
+element by element through the C-ABI, with the fit's tolerances.
+
+The energy-loss kernel is its own instantiation of the fit; these frames
+(protons and pions, thin gas layers and thick ones, rows lost to dropout,
+scattering and outliers) exercise it, the tracks it stops included.
+"""
+import types
+
+import numpy as np
+import pytest
+
+import oracle
+import tpcgen
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+PROTON = 0.938272
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_01205_gb300 as T
+    from paper_2402_01205_gb300 import _build
+    _build.build()
+    return T
+
+
+def fit_gpu(T, f, **cfg):
+    g = types.SimpleNamespace(**{k: torch.from_numpy(np.ascontiguousarray(getattr(f, k))).cuda()
+                                 for k in ("offsets", "x", "y", "z", "sy2", "sz2", "row")})
+    with T.Fitter(**cfg) as fx:
+        res = fx.fit(g)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in res.items()}
+
+
+def check(f, gpu, orc, min_compared=0.97):
+    rep = compare(f.offsets, gpu, orc)
+    print(rep.summary())
+    assert not rep.status_mismatch, rep.status_mismatch[:10]
+    assert not rep.accept_mismatch, rep.accept_mismatch[:10]
+    assert rep.ndf_mismatch == 0
+    assert rep.max_state < 1e-3, rep.worst
+    assert rep.max_cov < 1e-4, rep.worst
+    assert rep.max_chi2 < 1e-4, rep.worst
+    n_ok = int(((gpu["status"] == 0) & (orc["status"] == 0)).sum())
+    assert rep.n_compared >= min_compared * n_ok
+    return rep
+
+
+@pytest.mark.parametrize("mass,xrho,pt", [(PROTON, 0.01, (0.3, 5.0)), (0.13957, 0.0016, (0.1, 10.0))])
+def test_parity_with_energy_loss(T, mass, xrho, pt):
+    f = tpcgen.generate("detector50k", n_tracks=30_011, seed=21, mass=mass, xrho=xrho, pt_min=pt[0], pt_max=pt[1])
+    gpu = fit_gpu(T, f, xrho_per_row=xrho, mass_gev=mass)
+    orc = oracle.fit(f, oracle.FitConfig(xx0=5e-4, xrho=xrho, mass=mass), diagnostics=True)
+    check(f, gpu, orc)
+    # the variant is not the plain fit: without energy loss q/pT differs
+    plain = fit_gpu(T, f, mass_gev=mass)
+    ok = (gpu["status"] == 0) & (plain["status"] == 0)
+    assert np.median(np.abs(plain["state"][ok, 4] / gpu["state"][ok, 4] - 1)) > 1e-4
+
+
+def test_noise_free_energy_loss_fit_recovers_truth(T):
+    kw = dict(truth=True, sigma_y=0.0, sigma_z=0.0, seed=5, n_tracks=500, mass=PROTON, pt_min=0.5, pt_max=2.0,
+              min_clusters=100, p_drop=0.1)
+    f = tpcgen.generate("sector1k", xrho=0.05, **kw)
+    gpu = fit_gpu(T, f, xx0_per_row=0.0, xrho_per_row=0.05, mass_gev=PROTON, min_clusters=100)
+    plain = fit_gpu(T, f, xx0_per_row=0.0, mass_gev=PROTON, min_clusters=100)
+    assert np.all(gpu["status"] == 0)
+    tr = f.truth[f.offsets[:-1]]
+    d = np.abs(gpu["state"].astype(np.float64) - tr)
+    assert np.all(d.max(0) < [1e-4, 1e-4, 1e-5, 1e-5, 5e-2])
+    rel = np.abs(gpu["state"][:, 4] / tr[:, 4] - 1)
+    rel_plain = np.abs(plain["state"][:, 4] / tr[:, 4] - 1)
+    assert np.median(rel) < 1e-5 and np.median(rel_plain) > 1e-3
+
+
+def test_stopped_tracks_match_the_oracle(T):
+    """Slow protons fitted with far more material than they crossed: the fit
+    stops many of them (TPCFIT_TRACK_STOPPED) at the same track as the oracle."""
+    f = tpcgen.generate("detector50k", n_tracks=4_000, seed=23, mass=PROTON, xrho=0.01, pt_min=0.2, pt_max=0.6)
+    gpu = fit_gpu(T, f, xrho_per_row=0.3, mass_gev=PROTON)
+    orc = oracle.fit(f, oracle.FitConfig(xx0=5e-4, xrho=0.3, mass=PROTON), diagnostics=True)
+    n_stop = int((orc["status"] == 6).sum())
+    print("stopped", n_stop, "of", f.n_tracks)
+    assert n_stop > 100 and np.array_equal(gpu["status"], orc["status"])
+    check(f, gpu, orc)
+
+
+def test_energy_loss_through_the_host_path(T):
+    f = tpcgen.generate("detector50k", n_tracks=5_000, seed=24, mass=PROTON, xrho=0.01, pt_min=0.3, pt_max=5.0)
+    dev = fit_gpu(T, f, xrho_per_row=0.01, mass_gev=PROTON)
+    host = types.SimpleNamespace(**{k: np.ascontiguousarray(getattr(f, k)) for k in
+                                    ("offsets", "x", "y", "z", "sy2", "sz2", "row")})
+    with T.Fitter(xrho_per_row=0.01, mass_gev=PROTON, host_chunk_clusters=100_000) as fx:
+        hres = fx.fit(host)
+    for k in ("state", "cov", "chi2", "status", "accept"):
+        assert np.array_equal(np.asarray(hres[k]), dev[k]), k

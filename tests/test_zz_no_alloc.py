@@ -81,3 +81,15 @@ def test_noalloc_rejects_frames_above_the_limit(T):
     with pytest.raises(T.TpcfitError) as ei:
         T.fit_noalloc(dev_frame(f), T.alloc_result(f.n_tracks, f.n_clusters, device="cuda"))
     assert ei.value.code == T.E_INVAL
+
+
+def test_noalloc_with_energy_loss_equals_fit(T):
+    f = tpcgen.generate("detector50k", n_tracks=8_000, seed=34, mass=0.938272, xrho=0.01, pt_min=0.3, pt_max=5.0)
+    d = dev_frame(f)
+    with T.Fitter(xrho_per_row=0.01, mass_gev=0.938272) as fx:
+        ref = host(fx.fit(d))
+    out = T.alloc_result(f.n_tracks, f.n_clusters, device="cuda")
+    T.fit_noalloc(d, out, T.default_config(xrho_per_row=0.01, mass_gev=0.938272))
+    got = host(out)
+    assert_same_fit(got, ref)
+    assert np.array_equal(got["state"], ref["state"])  # same kernel, same inputs: bit-identical

@@ -99,6 +99,10 @@ PRESETS = {
     # Pb-Pb-scale frame: 2,000,000 tracks, exponential pT spectrum (mean 0.6, floor 0.05)
     "pbpb2m": dict(BASE, n_tracks=2_000_000, xx0=5e-4, p_drop=0.05, p_outlier=0.01, outlier_half=2.0,
                    n_phi_sectors=18, pt_mode=1, pt_min=0.05),
+    # the same with mean energy loss: the layer that scatters with x/X0 = 5e-4, taken as neon
+    # (X0 = 28.93 g/cm^2), is 0.0145 g/cm^2 thick
+    "pbpb2m_eloss": dict(BASE, n_tracks=2_000_000, xx0=5e-4, p_drop=0.05, p_outlier=0.01, outlier_half=2.0,
+                         n_phi_sectors=18, pt_mode=1, pt_min=0.05, xrho=0.0145),
 }
 
 
