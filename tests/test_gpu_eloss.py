@@ -58,10 +58,12 @@ def test_parity_with_energy_loss(T, mass, xrho, pt):
     gpu = fit_gpu(T, f, xrho_per_row=xrho, mass_gev=mass)
     orc = oracle.fit(f, oracle.FitConfig(xx0=5e-4, xrho=xrho, mass=mass), diagnostics=True)
     check(f, gpu, orc)
-    # the variant is not the plain fit: without energy loss q/pT differs
+    # the variant is not the plain fit: at the innermost cluster the particle is at its fastest, so
+    # with energy loss |q/pT| there is smaller than the plain fit's average over the track
     plain = fit_gpu(T, f, mass_gev=mass)
     ok = (gpu["status"] == 0) & (plain["status"] == 0)
-    assert np.median(np.abs(plain["state"][ok, 4] / gpu["state"][ok, 4] - 1)) > 1e-4
+    rel = np.abs(plain["state"][ok, 4]).astype(np.float64) / np.abs(gpu["state"][ok, 4]) - 1
+    assert np.median(rel) > 2e-5 and (rel > 0).mean() > 0.8
 
 
 def test_noise_free_energy_loss_fit_recovers_truth(T):
