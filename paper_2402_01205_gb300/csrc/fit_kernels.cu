@@ -546,7 +546,8 @@ template <int BLOCK, int MINB, bool ELOSS> static cudaError_t launch_fit_as(cons
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {
   if (a.n_tracks <= 0) return cudaSuccess;
   const bool el = a.xrho > 0.0f;
-  if (block == 128) return el ? launch_fit_as<128, 4, true>(a, grid, stream) : launch_fit_as<128, 4, false>(a, grid, stream);
+  if (block == 128)
+    return el ? launch_fit_as<128, 4, true>(a, grid, stream) : launch_fit_as<128, 4, false>(a, grid, stream);
   return el ? launch_fit_as<256, 2, true>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
 }
 
@@ -577,9 +578,14 @@ int fit_default_blocks_per_sm(int block) {
   return occ < want ? occ : want;
 }
 
-int fit_regs_per_thread() {
+int fit_regs_per_thread(int block, bool eloss) {
   cudaFuncAttributes at;
-  if (cudaFuncGetAttributes(&at, k_fit<256, 2, false>) != cudaSuccess) return -1;
+  cudaError_t e;
+  if (block == 128)
+    e = eloss ? cudaFuncGetAttributes(&at, k_fit<128, 4, true>) : cudaFuncGetAttributes(&at, k_fit<128, 4, false>);
+  else
+    e = eloss ? cudaFuncGetAttributes(&at, k_fit<256, 2, true>) : cudaFuncGetAttributes(&at, k_fit<256, 2, false>);
+  if (e != cudaSuccess) return -1;
   return at.numRegs;
 }
 

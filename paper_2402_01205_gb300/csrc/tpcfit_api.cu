@@ -345,7 +345,7 @@ extern "C" int tpcfit_create(const tpcfit_config *cfg_in, tpcfit_handle **out) {
   h->fit_block = cfg.block_threads ? cfg.block_threads : 256;
   const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(h->fit_block);
   h->fit_grid = h->sms * bps;
-  h->fit_regs = fit_regs_per_thread();
+  h->fit_regs = fit_regs_per_thread(h->fit_block, cfg.xrho_per_row > 0.0f);
   h->chunk_clusters = cfg.host_chunk_clusters > 0 ? cfg.host_chunk_clusters : (int64_t)16 << 20;
   *out = h;
   return TPCFIT_OK;

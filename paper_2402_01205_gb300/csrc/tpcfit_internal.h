@@ -121,6 +121,6 @@ cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream);
 int fit_blocks_per_sm(int block);
 // tuned default residency (blocks per SM) for a block size
 int fit_default_blocks_per_sm(int block);
-int fit_regs_per_thread();
+int fit_regs_per_thread(int block, bool eloss);  // of the instantiation a handle launches
 
 }  // namespace tpcfit
