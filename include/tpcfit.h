@@ -103,7 +103,9 @@ typedef struct tpcfit_config {
   float eloss_z_over_a;   /* Z/A of the layer material (0 = neon, 0.49555) */
   float eloss_i_ev;       /* mean excitation energy of the material in eV (0 = neon, 137) */
   int32_t reserved[2];
-  int64_t host_chunk_clusters; /* host frames are copied and fitted in chunks of about this many clusters (16M) */
+  int64_t host_chunk_clusters; /* host frames: chunk scale C (16M clusters); chunks shrink from up to 4C at the
+                                 start of the frame to C/4 at its end (two device staging buffers of the
+                                 largest chunk); serving splits frames into parts of about C */
 } tpcfit_config;
 
 /* One time frame in SoA layout: the clusters of track t are

@@ -662,27 +662,53 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
   const int64_t nt = f->n_tracks;
   int rc = TPCFIT_OK;
   if (off[0] != 0 || off[nt] != f->n_clusters) return fail(TPCFIT_E_INVAL, "offsets do not span [0, n_clusters]");
-  // chunk boundaries by binary search on the offsets; the cut points are
-  // checked here, the offsets inside each chunk just before its copies are
-  // enqueued (so the check of chunk i overlaps the copies of chunk i-1)
+  // Chunk schedule.  A call costs the host->device copy of every input byte
+  // (the link is the bound) plus what no copy overlaps: the fit and the result
+  // copy of the last chunk, and a setup cost per copy (7 per chunk).  So the
+  // chunks grow from C/4 clusters at the end of the frame by a factor 1.4 per
+  // chunk towards its start, up to 4C (C = host_chunk_clusters): each chunk's
+  // copy still outlasts the fit and result copy of the chunk before it (the
+  // copy moves about 0.10 ms per M clusters, fit and results take about 0.06),
+  // so the copies run back to back.  The cut points come from a binary search
+  // on the offsets and are checked here; the offsets inside each chunk are
+  // checked after its copies are enqueued (so that check overlaps the copies).
+  const int64_t C = h->chunk_clusters, nc_all = f->n_clusters;
+  std::vector<int64_t> sizes;  // planned chunk sizes in clusters, the last chunk first
+  int64_t planned = 0;
+  for (double sz = std::max(1.0, (double)C / 4.0); planned < nc_all || sizes.empty();
+       sz = std::min(sz * 1.4, 4.0 * (double)C)) {
+    sizes.push_back(std::max<int64_t>(1, (int64_t)sz));
+    planned += sizes.back();
+  }
+  if (sizes.size() > 1 && planned - sizes.back() / 4 * 3 >= nc_all) {
+    // the first chunk would hold under a quarter of its planned size: the next one takes it
+    planned -= sizes.back();
+    sizes.pop_back();
+  }
   std::vector<int64_t> cuts{0};
-  while (cuts.back() < nt) {
-    int64_t t0 = cuts.back();
-    int64_t target = off[t0] + h->chunk_clusters;
-    int64_t lo = t0 + 1, hi = nt;  // first t1 in (t0, nt] with off[t1] >= target, or nt
-    while (lo < hi) {
-      int64_t mid = lo + (hi - lo) / 2;
-      if (off[mid] >= target) hi = mid;
-      else lo = mid + 1;
+  int64_t after = planned - sizes.back();  // clusters planned after the current chunk
+  for (size_t k = sizes.size(); k-- > 0 && cuts.back() < nt;) {
+    const int64_t t0 = cuts.back();
+    int64_t t1 = nt;  // the last chunk ends with the frame
+    if (k > 0) {
+      const int64_t target = nc_all - after;  // first t1 in (t0, nt] with off[t1] >= target, or nt
+      int64_t lo = t0 + 1, hi = nt;
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (off[mid] >= target) hi = mid;
+        else lo = mid + 1;
+      }
+      t1 = lo;
+      after -= sizes[k - 1];
     }
-    if (off[lo] < off[t0] || off[lo] > f->n_clusters)
-      return fail(TPCFIT_E_INVAL, "offsets decrease or leave [0, n_clusters] before track %lld", (long long)lo);
-    cuts.push_back(lo);
+    if (off[t1] < off[t0] || off[t1] > f->n_clusters)
+      return fail(TPCFIT_E_INVAL, "offsets decrease or leave [0, n_clusters] before track %lld", (long long)t1);
+    cuts.push_back(t1);
   }
   int64_t max_nt = 0, max_nc = 0;
   for (size_t i = 0; i + 1 < cuts.size(); ++i) {
     max_nt = std::max(max_nt, cuts[i + 1] - cuts[i]);
-    max_nc = std::max(max_nc, off[cuts[i + 1]] - off[cuts[i]]);
+    max_nc = std::max(max_nc, off[cuts[i + 1]] - off[cuts[i]] + 2 * kCopyAlign);
   }
   if ((rc = h->scratch.ensure(max_nt))) return rc;
   for (int i = 0; i < 2; ++i)
@@ -696,26 +722,31 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     const int64_t t0 = cuts[ci], t1 = cuts[ci + 1];
     const int64_t c0 = off[t0], c1 = off[t1];
     const int64_t cnt = t1 - t0, ncl = c1 - c0;
+    // the staged range [a0, a1): [c0, c1) widened to kCopyAlign-cluster boundaries
+    const int64_t a0 = c0 / kCopyAlign * kCopyAlign;
+    const int64_t a1 = std::min<int64_t>((c1 + kCopyAlign - 1) / kCopyAlign * kCopyAlign, f->n_clusters);
+    const int64_t nst = a1 - a0;
+    // inputs: wait until this stage's previous results have been copied out;
+    // the copies read [c0, c1) of the inputs, inside [0, n_clusters] (checked above)
+    CU(cudaStreamWaitEvent(h->h2d, S.free_ev, 0));
+    CU(cudaMemcpyAsync(S.off, off + t0, (size_t)(cnt + 1) * 8, cudaMemcpyHostToDevice, h->h2d));
+    if (ncl > 0) {
+      CU(cudaMemcpyAsync(S.x, f->x + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
+      CU(cudaMemcpyAsync(S.y, f->y + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
+      CU(cudaMemcpyAsync(S.z, f->z + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
+      CU(cudaMemcpyAsync(S.sy2, f->sy2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
+      CU(cudaMemcpyAsync(S.sz2, f->sz2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
+      CU(cudaMemcpyAsync(S.row, f->row + a0, (size_t)nst, cudaMemcpyHostToDevice, h->h2d));
+    }
+    CU(cudaEventRecord(h->ev_in[ci & 1], h->h2d));
     for (int64_t t = t0; t < t1; ++t)
       if (off[t + 1] < off[t]) {
-        // nothing of this chunk is enqueued; let the chunks in flight finish
+        // nothing of this chunk is fitted; let the copies in flight finish
         wait_stream(h->h2d, -1);
         wait_stream(h->stream, -1);
         wait_stream(h->d2h, -1);
         return fail(TPCFIT_E_INVAL, "offsets decrease at track %lld", (long long)t);
       }
-    // inputs: wait until this stage's previous results have been copied out
-    CU(cudaStreamWaitEvent(h->h2d, S.free_ev, 0));
-    CU(cudaMemcpyAsync(S.off, off + t0, (size_t)(cnt + 1) * 8, cudaMemcpyHostToDevice, h->h2d));
-    if (ncl > 0) {
-      CU(cudaMemcpyAsync(S.x, f->x + c0, (size_t)ncl * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.y, f->y + c0, (size_t)ncl * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.z, f->z + c0, (size_t)ncl * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.sy2, f->sy2 + c0, (size_t)ncl * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.sz2, f->sz2 + c0, (size_t)ncl * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.row, f->row + c0, (size_t)ncl, cudaMemcpyHostToDevice, h->h2d));
-    }
-    CU(cudaEventRecord(h->ev_in[ci & 1], h->h2d));
     // fit
     CU(cudaStreamWaitEvent(h->stream, h->ev_in[ci & 1], 0));
     CU(cudaMemsetAsync(h->scratch.hist, 0, 2 * kKeyBins * sizeof(uint32_t) + 16, h->stream));
@@ -723,7 +754,8 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     cf.n_tracks = cnt;
     cf.n_clusters = ncl;
     cf.track_offsets = S.off;
-    cf.x = S.x; cf.y = S.y; cf.z = S.z; cf.sy2 = S.sy2; cf.sz2 = S.sz2; cf.row = S.row;
+    const int64_t d = c0 - a0;  // cluster c0 sits d elements into the staged arrays
+    cf.x = S.x + d; cf.y = S.y + d; cf.z = S.z + d; cf.sy2 = S.sy2 + d; cf.sz2 = S.sz2 + d; cf.row = S.row + d;
     tpcfit_result cr = *r;
     cr.chi2_out_cluster = cr.chi2_in_cluster = nullptr;
     cr.restart_state = nullptr;

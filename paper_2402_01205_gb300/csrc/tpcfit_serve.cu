@@ -19,6 +19,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -168,7 +169,12 @@ static bool launch(ServeState *S, const Part &P, int si) {
   tpcfit_frame df;
   tpcfit_result dr;
   void *scratch = nullptr;
-  carve(L.mem, nt, nc, R.res.res_y != nullptr, R.res.res_z != nullptr, &df, &dr, &scratch);
+  // inputs are copied over [a0, a1), [c0, c1) widened to kCopyAlign-cluster
+  // boundaries; the fit sees the part from cluster c0, d elements in
+  const int64_t a0 = c0 / kCopyAlign * kCopyAlign;
+  const int64_t a1 = std::min<int64_t>((c1 + kCopyAlign - 1) / kCopyAlign * kCopyAlign, F.n_clusters);
+  const int64_t nst = a1 - a0, d = c0 - a0;
+  carve(L.mem, nt, nc + 2 * kCopyAlign, R.res.res_y != nullptr, R.res.res_z != nullptr, &df, &dr, &scratch);
   bool ok = true;
   auto cp = [&](const void *dst, const void *src, size_t b, cudaMemcpyKind k) {
     if (!b || !ok) return;
@@ -179,12 +185,16 @@ static bool launch(ServeState *S, const Part &P, int si) {
     }
   };
   cp(df.track_offsets, F.track_offsets + P.t0, (size_t)(nt + 1) * 8, cudaMemcpyHostToDevice);
-  cp(df.x, F.x + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.y, F.y + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.z, F.z + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.sy2, F.sy2 + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.sz2, F.sz2 + c0, (size_t)nc * 4, cudaMemcpyHostToDevice);
-  cp(df.row, F.row + c0, (size_t)nc, cudaMemcpyHostToDevice);
+  if (nc > 0) {
+    cp(df.x, F.x + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
+    cp(df.y, F.y + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
+    cp(df.z, F.z + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
+    cp(df.sy2, F.sy2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
+    cp(df.sz2, F.sz2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
+    cp(df.row, F.row + a0, (size_t)nst, cudaMemcpyHostToDevice);
+  }
+  df.x += d; df.y += d; df.z += d; df.sy2 += d; df.sz2 += d; df.row += d;
+  df.n_clusters = nc;
   const int32_t *err_dev = nullptr;
   if (ok && serve_launch_frame(S->h, &df, &dr, scratch, c0, L.stream, &err_dev) != TPCFIT_OK) ok = false;
   if (ok) cp(L.h_err, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost);
@@ -338,7 +348,7 @@ void serve_stop(tpcfit_handle *h) {
 int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint64_t *ticket) {
   ServeState *S = handle_serve(h);
   const int n_res = (r->res_y ? 1 : 0) + (r->res_z ? 1 : 0);
-  const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters, n_res);
+  const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters + 2 * kCopyAlign, n_res);
   if (bytes > S->budget) return TPCFIT_E_NOMEM;
   // parts of about host_chunk_clusters clusters (offsets were checked by the caller)
   const int64_t *off = f->track_offsets;
@@ -354,7 +364,7 @@ int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint
     Part P;
     P.t0 = t0;
     P.t1 = lo;
-    P.bytes = frame_bytes(lo - t0, off[lo] - off[t0], n_res);
+    P.bytes = frame_bytes(lo - t0, off[lo] - off[t0] + 2 * kCopyAlign, n_res);  // room for the widened copy
     parts.push_back(P);
     t0 = lo;
   }
