@@ -655,24 +655,19 @@ static int validate_host_offsets(const tpcfit_frame *f) {
 
 // host frame (and host or device results): chunks of tracks, copies and fits
 // of consecutive chunks overlapped (two staging buffers).
-static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
-  if (r->chi2_out_cluster || r->chi2_in_cluster || r->restart_state)
-    return fail(TPCFIT_E_INVAL, "diagnostic outputs need a device frame and device results");
-  const int64_t *off = f->track_offsets;
-  const int64_t nt = f->n_tracks;
-  int rc = TPCFIT_OK;
-  if (off[0] != 0 || off[nt] != f->n_clusters) return fail(TPCFIT_E_INVAL, "offsets do not span [0, n_clusters]");
-  // Chunk schedule.  A call costs the host->device copy of every input byte
-  // (the link is the bound) plus what no copy overlaps: the fit and the result
-  // copy of the last chunk, and a setup cost per copy (7 per chunk).  So the
-  // chunks grow from C/4 clusters at the end of the frame by a factor 1.4 per
-  // chunk towards its start, up to 4C (C = host_chunk_clusters): each chunk's
-  // copy still outlasts the fit and result copy of the chunk before it (the
-  // copy moves about 0.10 ms per M clusters, fit and results take about 0.06),
-  // so the copies run back to back.  The cut points come from a binary search
-  // on the offsets and are checked here; the offsets inside each chunk are
-  // checked after its copies are enqueued (so that check overlaps the copies).
-  const int64_t C = h->chunk_clusters, nc_all = f->n_clusters;
+// Chunk schedule of a host frame (host path and serving).  A call costs the
+// host->device copy of every input byte (the link is the bound) plus what no
+// copy overlaps: the fit and the result copy of the last chunk, and a setup
+// cost per copy (7 per chunk).  So the chunks grow from C/4 clusters at the
+// end of the frame by a factor 1.4 per chunk towards its start, up to 4C
+// (C = host_chunk_clusters): each chunk's copy still outlasts the fit and
+// result copy of the chunk before it (the copy moves about 0.10 ms per M
+// clusters, fit and results take about 0.06), so the copies run back to back.
+// Cut points (track indices, 0 first, nt last, whole tracks per chunk) come
+// from a binary search on the offsets; returns -1, or the track at which the
+// offsets decrease or leave [0, n_clusters] (the offsets inside a chunk are
+// the caller's to check).
+int64_t tpcfit::chunk_cuts(const int64_t *off, int64_t nt, int64_t nc_all, int64_t C, std::vector<int64_t> &cuts) {
   std::vector<int64_t> sizes;  // planned chunk sizes in clusters, the last chunk first
   int64_t planned = 0;
   for (double sz = std::max(1.0, (double)C / 4.0); planned < nc_all || sizes.empty();
@@ -685,7 +680,7 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     planned -= sizes.back();
     sizes.pop_back();
   }
-  std::vector<int64_t> cuts{0};
+  cuts.assign(1, 0);
   int64_t after = planned - sizes.back();  // clusters planned after the current chunk
   for (size_t k = sizes.size(); k-- > 0 && cuts.back() < nt;) {
     const int64_t t0 = cuts.back();
@@ -701,14 +696,27 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
       t1 = lo;
       after -= sizes[k - 1];
     }
-    if (off[t1] < off[t0] || off[t1] > f->n_clusters)
-      return fail(TPCFIT_E_INVAL, "offsets decrease or leave [0, n_clusters] before track %lld", (long long)t1);
+    if (off[t1] < off[t0] || off[t1] > nc_all) return t1;
     cuts.push_back(t1);
   }
+  return -1;
+}
+
+static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
+  if (r->chi2_out_cluster || r->chi2_in_cluster || r->restart_state)
+    return fail(TPCFIT_E_INVAL, "diagnostic outputs need a device frame and device results");
+  const int64_t *off = f->track_offsets;
+  const int64_t nt = f->n_tracks;
+  int rc = TPCFIT_OK;
+  if (off[0] != 0 || off[nt] != f->n_clusters) return fail(TPCFIT_E_INVAL, "offsets do not span [0, n_clusters]");
+  std::vector<int64_t> cuts;
+  const int64_t bad = chunk_cuts(off, nt, f->n_clusters, h->chunk_clusters, cuts);
+  if (bad >= 0)
+    return fail(TPCFIT_E_INVAL, "offsets decrease or leave [0, n_clusters] before track %lld", (long long)bad);
   int64_t max_nt = 0, max_nc = 0;
   for (size_t i = 0; i + 1 < cuts.size(); ++i) {
     max_nt = std::max(max_nt, cuts[i + 1] - cuts[i]);
-    max_nc = std::max(max_nc, off[cuts[i + 1]] - off[cuts[i]] + 2 * kCopyAlign);
+    max_nc = std::max(max_nc, off[cuts[i + 1]] - off[cuts[i]] + 2 * kCopyPad);
   }
   if ((rc = h->scratch.ensure(max_nt))) return rc;
   for (int i = 0; i < 2; ++i)
@@ -722,22 +730,12 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     const int64_t t0 = cuts[ci], t1 = cuts[ci + 1];
     const int64_t c0 = off[t0], c1 = off[t1];
     const int64_t cnt = t1 - t0, ncl = c1 - c0;
-    // the staged range [a0, a1): [c0, c1) widened to kCopyAlign-cluster boundaries
-    const int64_t a0 = c0 / kCopyAlign * kCopyAlign;
-    const int64_t a1 = std::min<int64_t>((c1 + kCopyAlign - 1) / kCopyAlign * kCopyAlign, f->n_clusters);
-    const int64_t nst = a1 - a0;
     // inputs: wait until this stage's previous results have been copied out;
     // the copies read [c0, c1) of the inputs, inside [0, n_clusters] (checked above)
     CU(cudaStreamWaitEvent(h->h2d, S.free_ev, 0));
     CU(cudaMemcpyAsync(S.off, off + t0, (size_t)(cnt + 1) * 8, cudaMemcpyHostToDevice, h->h2d));
-    if (ncl > 0) {
-      CU(cudaMemcpyAsync(S.x, f->x + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.y, f->y + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.z, f->z + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.sy2, f->sy2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.sz2, f->sz2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice, h->h2d));
-      CU(cudaMemcpyAsync(S.row, f->row + a0, (size_t)nst, cudaMemcpyHostToDevice, h->h2d));
-    }
+    tpcfit_frame cf = *f;
+    CU(copy_clusters_in(*f, c0, c1, ClusterArrays{S.x, S.y, S.z, S.sy2, S.sz2, S.row}, cf, h->h2d));
     CU(cudaEventRecord(h->ev_in[ci & 1], h->h2d));
     for (int64_t t = t0; t < t1; ++t)
       if (off[t + 1] < off[t]) {
@@ -750,12 +748,8 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     // fit
     CU(cudaStreamWaitEvent(h->stream, h->ev_in[ci & 1], 0));
     CU(cudaMemsetAsync(h->scratch.hist, 0, 2 * kKeyBins * sizeof(uint32_t) + 16, h->stream));
-    tpcfit_frame cf = *f;
     cf.n_tracks = cnt;
-    cf.n_clusters = ncl;
     cf.track_offsets = S.off;
-    const int64_t d = c0 - a0;  // cluster c0 sits d elements into the staged arrays
-    cf.x = S.x + d; cf.y = S.y + d; cf.z = S.z + d; cf.sy2 = S.sy2 + d; cf.sz2 = S.sz2 + d; cf.row = S.row + d;
     tpcfit_result cr = *r;
     cr.chi2_out_cluster = cr.chi2_in_cluster = nullptr;
     cr.restart_state = nullptr;

@@ -1,6 +1,7 @@
 // Internal interface between the C-ABI runtime and the CUDA kernels.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "tpcfit.h"
@@ -45,12 +46,48 @@ struct FitArgs {
   int32_t min_clusters, n_rows;
 };
 
-// Host frames are copied to the device in ranges widened to multiples of this
-// many clusters (256 bytes of each float array), inside [0, n_clusters]:
-// host-to-device copies that start or end off a 256-byte boundary run well
-// below the link rate (on GB300: 12 chunks of a 4 GB frame in 20.8 ms
-// unaligned against 19.4 ms aligned).
-constexpr int64_t kCopyAlign = 64;
+// Host-to-device copies of the clusters [c0, c1) of a host frame into staging
+// arrays that hold c1 - c0 + 2 * kCopyPad elements each.  Each array's copy is
+// widened so that it starts and ends on a 256-byte boundary of its host
+// address, where the array allows it (never before its element 0 or past
+// n_clusters): copies off those boundaries run well below the link rate (on
+// GB300: a 4 GB frame in 12 chunks took 20.8 ms unaligned against 19.4 ms
+// aligned; one copy: 19.2 ms).  `view` receives the staging arrays advanced to
+// cluster c0 (n_clusters = c1 - c0).  Returns the first failing CUDA error.
+constexpr int64_t kCopyPad = 256;  // elements: a 256-byte boundary lies within 256 elements of any address
+
+struct ClusterArrays {
+  float *x, *y, *z, *sy2, *sz2;
+  uint8_t *row;
+};
+
+inline cudaError_t copy_clusters_in(const tpcfit_frame &f, int64_t c0, int64_t c1, const ClusterArrays &stage,
+                                    tpcfit_frame &view, cudaStream_t st) {
+  cudaError_t err = cudaSuccess;
+  auto one = [&](const void *src, void *dst, size_t elem) -> const void * {
+    const uintptr_t base = reinterpret_cast<uintptr_t>(src);
+    int64_t a0 = c0 - (int64_t)(((base + (uintptr_t)c0 * elem) & 255u) / elem);
+    if (a0 < 0) a0 = 0;
+    int64_t a1 = c1 + (int64_t)(((256u - ((base + (uintptr_t)c1 * elem) & 255u)) & 255u) / elem);
+    if (a1 > f.n_clusters) a1 = f.n_clusters;
+    if (c1 > c0 && err == cudaSuccess)
+      err = cudaMemcpyAsync(dst, static_cast<const char *>(src) + a0 * (int64_t)elem, (size_t)(a1 - a0) * elem,
+                            cudaMemcpyHostToDevice, st);
+    return static_cast<const char *>(dst) + (c0 - a0) * (int64_t)elem;
+  };
+  view.x = static_cast<const float *>(one(f.x, stage.x, 4));
+  view.y = static_cast<const float *>(one(f.y, stage.y, 4));
+  view.z = static_cast<const float *>(one(f.z, stage.z, 4));
+  view.sy2 = static_cast<const float *>(one(f.sy2, stage.sy2, 4));
+  view.sz2 = static_cast<const float *>(one(f.sz2, stage.sz2, 4));
+  view.row = static_cast<const uint8_t *>(one(f.row, stage.row, 1));
+  view.n_clusters = c1 - c0;
+  return err;
+}
+
+// Chunk schedule of a host frame (tpcfit_api.cu): cut points in track indices;
+// -1, or the track at which the offsets decrease or leave [0, nc_all].
+int64_t chunk_cuts(const int64_t *off, int64_t nt, int64_t nc_all, int64_t C, std::vector<int64_t> &cuts);
 
 // The fit parameters of FitArgs from a configuration (both entry points).
 inline void fit_params(FitArgs &a, const tpcfit_config &c) {

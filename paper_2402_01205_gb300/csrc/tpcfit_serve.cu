@@ -90,6 +90,7 @@ struct Slot {
   Part part;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t in_done = nullptr;  // recorded after this slot's input copies
   void *mem = nullptr;
   size_t bytes = 0;
   int32_t *h_err = nullptr;  // pinned
@@ -111,6 +112,7 @@ struct ServeState {
   uint64_t next_ticket = 1;
   double head_blocked_since = -1.0;
   cudaMemPool_t pool = nullptr;
+  cudaEvent_t last_in = nullptr;  // input copies of the latest launched part (the next part's copies wait for it)
 };
 
 // Carve one allocation into the frame and result arrays of a resident frame.
@@ -169,12 +171,7 @@ static bool launch(ServeState *S, const Part &P, int si) {
   tpcfit_frame df;
   tpcfit_result dr;
   void *scratch = nullptr;
-  // inputs are copied over [a0, a1), [c0, c1) widened to kCopyAlign-cluster
-  // boundaries; the fit sees the part from cluster c0, d elements in
-  const int64_t a0 = c0 / kCopyAlign * kCopyAlign;
-  const int64_t a1 = std::min<int64_t>((c1 + kCopyAlign - 1) / kCopyAlign * kCopyAlign, F.n_clusters);
-  const int64_t nst = a1 - a0, d = c0 - a0;
-  carve(L.mem, nt, nc + 2 * kCopyAlign, R.res.res_y != nullptr, R.res.res_z != nullptr, &df, &dr, &scratch);
+  carve(L.mem, nt, nc + 2 * kCopyPad, R.res.res_y != nullptr, R.res.res_z != nullptr, &df, &dr, &scratch);
   bool ok = true;
   auto cp = [&](const void *dst, const void *src, size_t b, cudaMemcpyKind k) {
     if (!b || !ok) return;
@@ -184,17 +181,23 @@ static bool launch(ServeState *S, const Part &P, int si) {
                                    (unsigned long long)P.ticket, b, cudaGetErrorString(e));
     }
   };
+  // input copies in launch order, one part at a time: the link is shared, and a
+  // part whose bytes arrive first can be fitted while the next one is copied
+  if (S->last_in && cudaStreamWaitEvent(L.stream, S->last_in, 0) != cudaSuccess) ok = false;
   cp(df.track_offsets, F.track_offsets + P.t0, (size_t)(nt + 1) * 8, cudaMemcpyHostToDevice);
-  if (nc > 0) {
-    cp(df.x, F.x + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
-    cp(df.y, F.y + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
-    cp(df.z, F.z + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
-    cp(df.sy2, F.sy2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
-    cp(df.sz2, F.sz2 + a0, (size_t)nst * 4, cudaMemcpyHostToDevice);
-    cp(df.row, F.row + a0, (size_t)nst, cudaMemcpyHostToDevice);
+  if (ok) {
+    const ClusterArrays stage{const_cast<float *>(df.x), const_cast<float *>(df.y), const_cast<float *>(df.z),
+                              const_cast<float *>(df.sy2), const_cast<float *>(df.sz2), const_cast<uint8_t *>(df.row)};
+    if (cudaError_t e = copy_clusters_in(F, c0, c1, stage, df, L.stream); e != cudaSuccess) {
+      ok = false;
+      if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: input copy failed: %s\n",
+                                   (unsigned long long)P.ticket, cudaGetErrorString(e));
+    }
   }
-  df.x += d; df.y += d; df.z += d; df.sy2 += d; df.sz2 += d; df.row += d;
-  df.n_clusters = nc;
+  if (ok) {
+    if (cudaError_t e = cudaEventRecord(L.in_done, L.stream); e != cudaSuccess) ok = false;
+    else S->last_in = L.in_done;
+  }
   const int32_t *err_dev = nullptr;
   if (ok && serve_launch_frame(S->h, &df, &dr, scratch, c0, L.stream, &err_dev) != TPCFIT_OK) ok = false;
   if (ok) cp(L.h_err, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost);
@@ -312,6 +315,7 @@ int serve_start(tpcfit_handle *h) {
   for (auto &L : S->slots) {
     if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L.in_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&L.h_err, sizeof(int32_t)) != cudaSuccess) {
       cudaGetLastError();
       handle_serve(h) = S;
@@ -337,6 +341,7 @@ void serve_stop(tpcfit_handle *h) {
   for (auto &L : S->slots) {
     if (L.stream) cudaStreamSynchronize(L.stream);
     if (L.done) cudaEventDestroy(L.done);
+    if (L.in_done) cudaEventDestroy(L.in_done);
     if (L.stream) cudaStreamDestroy(L.stream);
     if (L.h_err) cudaFreeHost(L.h_err);
   }
@@ -348,25 +353,19 @@ void serve_stop(tpcfit_handle *h) {
 int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint64_t *ticket) {
   ServeState *S = handle_serve(h);
   const int n_res = (r->res_y ? 1 : 0) + (r->res_z ? 1 : 0);
-  const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters + 2 * kCopyAlign, n_res);
+  const size_t bytes = frame_bytes(f->n_tracks, f->n_clusters + 2 * kCopyPad, n_res);
   if (bytes > S->budget) return TPCFIT_E_NOMEM;
-  // parts of about host_chunk_clusters clusters (offsets were checked by the caller)
+  // parts by the chunk schedule of the host path (offsets were checked by the caller)
   const int64_t *off = f->track_offsets;
-  const int64_t target = handle_chunk_clusters(h);
+  std::vector<int64_t> cuts;
+  if (chunk_cuts(off, f->n_tracks, f->n_clusters, handle_chunk_clusters(h), cuts) >= 0) return TPCFIT_E_INVAL;
   std::vector<Part> parts;
-  for (int64_t t0 = 0; t0 < f->n_tracks;) {
-    int64_t lo = t0 + 1, hi = f->n_tracks;  // first t1 with off[t1] >= off[t0] + target, or nt
-    while (lo < hi) {
-      const int64_t mid = lo + (hi - lo) / 2;
-      if (off[mid] >= off[t0] + target) hi = mid;
-      else lo = mid + 1;
-    }
+  for (size_t i = 0; i + 1 < cuts.size(); ++i) {
     Part P;
-    P.t0 = t0;
-    P.t1 = lo;
-    P.bytes = frame_bytes(lo - t0, off[lo] - off[t0] + 2 * kCopyAlign, n_res);  // room for the widened copy
+    P.t0 = cuts[i];
+    P.t1 = cuts[i + 1];
+    P.bytes = frame_bytes(P.t1 - P.t0, off[P.t1] - off[P.t0] + 2 * kCopyPad, n_res);  // room for the widened copy
     parts.push_back(P);
-    t0 = lo;
   }
   std::lock_guard<std::mutex> lk(S->mu);
   const uint64_t tk = S->next_ticket++;

@@ -112,6 +112,38 @@ def test_host_path_chunked_equals_device_path(T):
         assert np.array_equal(dev[k], host[k], equal_nan=k in ('state', 'cov')), k
 
 
+def test_host_chunk_schedules_and_unaligned_host_arrays_agree_with_device(T):
+    """Host frames are copied in chunks shrinking towards the end of the frame,
+    over ranges widened to 64-cluster boundaries: every chunk scale (down to
+    chunks smaller than one track) and host arrays that start off a 256-byte
+    boundary give the device path's results bit for bit."""
+    f = tpcgen.generate("detector50k", n_tracks=7_001, seed=41)
+    dev = fit_gpu(T, f)
+
+    def shifted(a, k):  # a copy of `a` whose data starts k elements into a fresh buffer
+        buf = np.empty(a.shape[0] + k, dtype=a.dtype)
+        buf[k:] = a
+        return buf[k:]
+
+    for chunk, shift in ((1_000, 0), (50, 3), (100_000, 1), (10_000_000, 5)):
+        host = types.SimpleNamespace(offsets=f.offsets, **{k: shifted(np.ascontiguousarray(getattr(f, k)), shift)
+                                                           for k in ("x", "y", "z", "sy2", "sz2", "row")})
+        with T.Fitter(host_chunk_clusters=chunk) as fx:
+            got = fx.fit(host)
+        for k in dev:
+            assert np.array_equal(dev[k], got[k], equal_nan=k in ("state", "cov")), (chunk, shift, k)
+
+
+def test_host_frame_of_empty_tracks(T):
+    off = np.zeros(6, dtype=np.int64)
+    empty = np.zeros(0, dtype=np.float32)
+    host = types.SimpleNamespace(offsets=off, x=empty, y=empty, z=empty, sy2=empty, sz2=empty,
+                                 row=np.zeros(0, dtype=np.uint8))
+    with T.Fitter() as fx:
+        got = fx.fit(host)
+    assert np.all(got["status"] == 1)  # TOO_FEW
+
+
 def test_sorted_and_unsorted_orders_agree(T):
     f = tpcgen.generate("detector50k", n_tracks=10_000)
     a = fit_gpu(T, f, sort_tracks=1)
