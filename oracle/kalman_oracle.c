@@ -28,7 +28,9 @@
  *   outputs at the innermost cluster;
  *   optional mean energy loss in a thin layer at every crossed row, crossed
  *   right after the row's cluster in outward motion (outward pass: after the
- *   update and the scattering; inward pass: added back before the update).
+ *   update and the scattering; inward pass: added back before the update);
+ *   optional seed iteration: the fitted state seeds another outward pass
+ *   (seed covariance), restart and inward pass, n_iterations times.
  * Status rule: clusters are validated when the outward pass reaches them, so the
  * first offending cluster decides; NaN never trips a numerical limit (it flows
  * to that cluster), and a completed fit with a non-finite state or covariance
@@ -61,6 +63,7 @@ typedef struct {
   double xrho;          /* energy-loss layer per crossed row, g/cm^2 (0: no energy loss) */
   double eloss_za;      /* Z/A of its material */
   double eloss_i;       /* mean excitation energy of its material, GeV */
+  int32_t n_iterations; /* refits seeded from the previous fit's state (0: none) */
 } orc_config;
 
 typedef struct {
@@ -337,7 +340,9 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
     orc_seed(A, B, D, c->bz, p);
   }
   if (fabs(p[2]) >= c->snp_max) { status = ST_SNP_LIMIT; goto emit; }
+  int iteration = 0;
 
+refit:;
   /* ---- outward pass: rows row[a] .. row[e-1] ---- */
   double xcur = x[a];
   for (int64_t k = a; k < e; ++k) {
@@ -432,6 +437,22 @@ static void fit_track(const orc_config *c, int64_t t, const int64_t *off, const 
   /* a fit that completed with a non-finite state or covariance */
   for (int i = 0; i < 25; ++i)
     if (!isfinite(C[i]) || (i < 5 && !isfinite(p[i]))) { status = ST_NONFINITE; break; }
+
+  /* seed iteration: the fitted state at the innermost cluster seeds a new
+     outward pass with the seed covariance, then restart and inward pass */
+  if (status == ST_OK && iteration < c->n_iterations) {
+    ++iteration;
+    seed_cov(c, C);
+    chi2_in = 0.0;
+    nacc_in = 0;
+    for (int64_t k = a; k < e; ++k) {
+      o->accept[k] = 0;
+      if (o->chi2_out_c) o->chi2_out_c[k] = NAN;
+      if (o->chi2_in_c) o->chi2_in_c[k] = NAN;
+      if (o->state_in_c) for (int i = 0; i < 5; ++i) o->state_in_c[5 * k + i] = NAN;
+    }
+    goto refit;
+  }
 
 emit:
   for (int i = 0; i < 5; ++i) o->state[5 * t + i] = p[i];

@@ -576,3 +576,62 @@ def test_energy_loss_fit_recovers_the_truth_of_the_generator():
     rel_no = np.abs(r_no["state"][:, 4] / f.truth[first, 4] - 1)
     assert np.median(rel_no) > 1e-3 and rel_no.max() > 3e-2
     assert np.abs(r["state_in_c"][:, :2] - f.truth[:, :2]).max() < 2e-5
+
+
+# ---------------------------------------------------------------- seed iteration
+def test_seed_iteration_converges_to_the_least_squares_minimum():
+    """With a seed prior as strong as the clusters (seed variances 1e-8 cm^2,
+    cluster variances 1e-8 cm^2) the fit is pulled towards its three-point
+    seed.  Each iteration re-centres that prior on the previous fit, so the
+    fixed point is the minimum of the clusters' chi2 alone: the distance to
+    that minimum (Gauss-Newton with the prior switched off) must shrink about
+    tenfold per iteration down to the extended filter's linearisation error.
+    The last inward pass is still the Gauss-Newton minimum with its own
+    restart prior, state and covariance.  With the default (weak) seed
+    covariance iterating changes nothing measurable."""
+    sm = 1e-4
+    f = tpcgen.generate("sector1k", truth=True, n_tracks=30, n_rows=10, min_clusters=3, sigma_y=sm, sigma_z=sm, seed=3)
+    strong = (1e-8, 1e-8, 1e-8, 1e-8, 1e-4)
+    med, worst, chi2 = {}, {}, {}
+    for it in (0, 1, 2, 4, 8):
+        cfg = _cfg(xx0=0.0, n_rows=10, min_clusters=3, chi2_max=1e30, seed_cov=strong, iterations=it)
+        r = oracle.fit(f, cfg, diagnostics=True)
+        assert np.all(r["status"] == 0)
+        assert np.array_equal(r["ndf"], 2 * np.diff(f.offsets) - 5)  # one pass's clusters, not accumulated
+        chi2[it] = np.median(r["chi2"])
+        d = []
+        for t in range(f.n_tracks):
+            a, b = f.offsets[t], f.offsets[t + 1]
+            cl = [getattr(f, k)[a:b].astype(float) for k in ("x", "y", "z", "sy2", "sz2")]
+            p, cov = lsq.fit_inward(*cl, r["state"][t], np.diag([1e12] * 5), cfg.bz, p_start=r["state"][t])
+            d.append(np.max(np.abs(p - r["state"][t]) / np.sqrt(np.diag(cov))))
+            if it == 8:  # the last inward pass against Gauss-Newton with its restart prior
+                p2, cov2 = lsq.fit_inward(*cl, r["state_out_t"][t], np.diag(r["restart_t"][t]), cfg.bz,
+                                          p_start=r["state"][t])
+                s2 = np.sqrt(np.diag(cov2))
+                assert np.max(np.abs(p2 - r["state"][t]) / s2) < 2e-3
+                assert np.max(np.abs(oracle.unpack_cov(r["cov"][t]) - cov2) / np.outer(s2, s2)) < 5e-5
+        med[it], worst[it] = np.median(d), np.max(d)
+    assert med[0] > 1e-2 and worst[0] > 5e-2
+    assert med[1] < med[0] / 4 and med[2] < med[1] / 4
+    assert med[4] < 1e-4 and worst[8] < 5e-4
+    assert chi2[8] < 1.5 * chi2[0]
+    weak = [oracle.fit(f, _cfg(xx0=0.0, n_rows=10, min_clusters=3, chi2_max=1e30, iterations=it)) for it in (0, 3)]
+    C = oracle.unpack_cov(weak[0]["cov"])
+    sig = np.sqrt(np.diagonal(C, axis1=1, axis2=2))
+    assert np.max(np.abs(weak[1]["state"] - weak[0]["state"]) / sig) < 1e-3
+
+
+def test_seed_iteration_accept_flags_and_ndf_are_those_of_the_last_pass():
+    """Gated fits with scattering and outliers, iterated twice: the accept
+    flags and ndf are the last pass's (ndf = 2 x inward-accepted - 5 on every
+    track), and some clusters near the gate do change their decision between
+    passes (so the flags are really recomputed)."""
+    f = tpcgen.generate("detector50k", n_tracks=5_000, seed=12)
+    r0 = oracle.fit(f, _cfg(chi2_max=9.0))  # a gate with clusters on both sides of it that move between passes
+    r2 = oracle.fit(f, _cfg(chi2_max=9.0, iterations=2))
+    ok = r2["status"] == 0
+    inward = np.add.reduceat((r2["accept"] >> 1) & 1, f.offsets[:-1]).astype(np.int64)
+    assert np.array_equal(r2["ndf"][ok], 2 * inward[ok] - 5)
+    flips = ((r0["accept"] >> 1) & 1).astype(int) - ((r2["accept"] >> 1) & 1)
+    assert int((flips == 1).sum()) > 0 and int((flips == -1).sum()) > 0
