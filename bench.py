@@ -164,7 +164,7 @@ def profiled_counters(n_clusters: int, launch: tuple, variant: str = ""):
     return out, note
 
 
-def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz, variant: str = ""):
+def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz, variant: str = "", passes: int = 1):
     """Roofline of the fit kernel.  Primary: instruction issue (the unit that
     binds), achieved = ncu warp instructions per launch / mean launch time,
     peak = 4 per SM per clock at the sampled SM clock.  Beside it the
@@ -173,7 +173,7 @@ def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz, variant: str
     (22 per cluster + 108 per track) against the measured copy bandwidth."""
     peaks, peak_src = measured_peaks()
     c, note = profiled_counters(nc, launch, variant)
-    fp64 = FP64_PER_CLUSTER * nc_fit / fit_s
+    fp64 = FP64_PER_CLUSTER * passes * nc_fit / fit_s  # each seed iteration repeats both passes
     hbm = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
     sub = {
         "fp64": {"achieved_tinst_s": fp64 / 1e12, "peak_tinst_s": probe["fp64_fma_per_s"] / 1e12,
@@ -183,7 +183,7 @@ def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz, variant: str
                 "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
     }
     if c and "fp32_flop_per_cluster" in c:
-        f32 = c["fp32_flop_per_cluster"] * nc_fit / fit_s
+        f32 = c["fp32_flop_per_cluster"] * passes * nc_fit / fit_s
         sub["fp32"] = {"achieved_tflops": f32 / 1e12, "peak_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
                        "frac": f32 / (2 * probe["fp32_fma_per_s"]), "flop_per_cluster": c["fp32_flop_per_cluster"],
                        "peak_source": "2 x measured live FP32 FMA chain probe"}
@@ -225,7 +225,7 @@ def link_rates(nbytes: int = 1 << 30, reps: int = 3) -> dict:
     return out
 
 
-def cpu_baseline(frame, seconds_target: float = 15.0, workload: str = "pbpb2m"):
+def cpu_baseline(frame, seconds_target: float = 15.0, workload: str = "pbpb2m", iterations: int = 0):
     """Time the FP64 oracle with every host core on a bounded sample of the
     frame: the whole frame when a 20k-track probe predicts <= ~2x the target,
     else the first tracks sized for about `seconds_target` seconds."""
@@ -235,13 +235,13 @@ def cpu_baseline(frame, seconds_target: float = 15.0, workload: str = "pbpb2m"):
     n = min(20_000, frame.n_tracks)
     sub = frame.subset(0, n)
     t0 = time.perf_counter()
-    oracle.fit(sub, oracle.FitConfig(**FIT_PARAMS.get(workload, ({}, {}))[1]), threads=cores)
+    oracle.fit(sub, oracle.FitConfig(iterations=iterations, **FIT_PARAMS.get(workload, ({}, {}))[1]), threads=cores)
     dt = time.perf_counter() - t0
     predicted = dt * frame.n_clusters / max(sub.n_clusters, 1)
     n2 = frame.n_tracks if predicted <= 2 * seconds_target else int(n * seconds_target / max(dt, 1e-6))
     sub = frame.subset(0, min(n2, frame.n_tracks))
     t0 = time.perf_counter()
-    r = oracle.fit(sub, oracle.FitConfig(**FIT_PARAMS.get(workload, ({}, {}))[1]), threads=cores)
+    r = oracle.fit(sub, oracle.FitConfig(iterations=iterations, **FIT_PARAMS.get(workload, ({}, {}))[1]), threads=cores)
     dt = time.perf_counter() - t0
     what = "the whole frame" if sub.n_tracks == frame.n_tracks else f"the first {sub.n_tracks} tracks of the frame"
     return {"value": sub.n_clusters / dt, "unit": "clusters/s", "cores": int(r["threads"]), "kind": "oracle",
@@ -795,6 +795,7 @@ def main():
     ap.add_argument("--rans-steps", type=int, default=5, help="pbpb2m: timed rANS encode/decode calls per stream")
     ap.add_argument("--block-threads", type=int, default=0, help="pbpb2m: fit kernel block size (0 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="pbpb2m: resident fit blocks per SM (0 = default)")
+    ap.add_argument("--fit-iterations", type=int, default=0, help="pbpb2m(_eloss): seed iterations of the fit (variant)")
     ap.add_argument("--n-events", type=int, default=4096, help="events4096: number of events (testing)")
     ap.add_argument("--per-event-steps", type=int, default=3, help="events4096: timed steps of the per-event arm")
     ap.add_argument("--tune-table", default=None, help="events4096: JSON tune table to read / extend")
@@ -835,7 +836,7 @@ def main():
     for k in names:
         setattr(dev, k, torch.from_numpy(np.ascontiguousarray(getattr(frame, k))).cuda())
     fx = T.Fitter(device=local, block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
-                  **FIT_PARAMS.get(args.workload, ({}, {}))[0])
+                  fit_iterations=args.fit_iterations, **FIT_PARAMS.get(args.workload, ({}, {}))[0])
     res = T.alloc_result(nt, nc, device=torch.device("cuda", local))
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
@@ -876,8 +877,10 @@ def main():
     nc_fit = int(lens[ok].sum())
     fit_s = tm["fit_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
     sms = torch.cuda.get_device_properties(local).multi_processor_count
+    variant = ("eloss" if args.workload == "pbpb2m_eloss" else "") + (f"iter{args.fit_iterations}" if args.fit_iterations
+                                                                       else "")
     roofline = fit_roofline(nc, nt, nc_fit, fit_s, (tm["fit_grid"], tm["fit_block"]), probe, sms, clk.get("sm_mhz"),
-                            "eloss" if args.workload == "pbpb2m_eloss" else "")
+                            variant, passes=1 + args.fit_iterations)
     roofline["fp32_fma_peak_per_s"] = probe["fp32_fma_per_s"]
     # the same steps with the track-model compression residual codes written (4 B per cluster more)
     res_r = T.alloc_result(nt, nc, device=torch.device("cuda", local), residuals=True)
@@ -963,7 +966,7 @@ def main():
                                  "bytes at that rate")}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(frame, workload=args.workload)
+        cpu = cpu_baseline(frame, workload=args.workload, iterations=args.fit_iterations)
     if rank == 0:
         line = {
             "metric": "clusters/s fitted on 1 GB300 (FP32 fit, FP64 innovation inverse and chi2)",
@@ -971,6 +974,7 @@ def main():
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n_tracks": nt,
+                       "fit_iterations": args.fit_iterations,
                        "n_clusters": nc, "tracks_fitted_ok": int(ok.sum()), "l2": "inputs 4.2 GB > L2; no flush",
                        "parallelism": f"replicas x{ws}", "fit_grid": tm["fit_grid"], "fit_block": tm["fit_block"],
                        "fit_regs": tm["fit_regs"]},

@@ -102,7 +102,13 @@ typedef struct tpcfit_config {
   float xrho_per_row;     /* g/cm^2 per crossed row (0 = no energy loss, the default) */
   float eloss_z_over_a;   /* Z/A of the layer material (0 = neon, 0.49555) */
   float eloss_i_ev;       /* mean excitation energy of the material in eV (0 = neon, 137) */
-  int32_t reserved[2];
+  /* Seed iteration: after the inward pass, the fitted state at the innermost
+   * cluster seeds another outward pass (with seed_cov), restart and inward
+   * pass, fit_iterations times (0-16; 0 = none, the default).  Outputs, accept
+   * flags and ndf are the last pass's; a failing pass ends the fit with its
+   * status.  Each iteration costs about one more fit. */
+  int32_t fit_iterations;
+  int32_t reserved[1];
   int64_t host_chunk_clusters; /* host frames: chunk scale C (16M clusters); chunks shrink from up to 4C at the
                                  start of the frame to C/4 at its end (two device staging buffers of the
                                  largest chunk); serving splits frames into parts of about C */

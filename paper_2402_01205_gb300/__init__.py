@@ -48,7 +48,7 @@ class Config(ctypes.Structure):
         ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32), ("block_threads", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32), ("sort_tracks", ctypes.c_int32), ("res_step_y_cm", ctypes.c_float),
         ("res_step_z_cm", ctypes.c_float), ("xrho_per_row", ctypes.c_float), ("eloss_z_over_a", ctypes.c_float),
-        ("eloss_i_ev", ctypes.c_float), ("reserved", ctypes.c_int32 * 2),
+        ("eloss_i_ev", ctypes.c_float), ("fit_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
         ("host_chunk_clusters", ctypes.c_int64),
     ]
 

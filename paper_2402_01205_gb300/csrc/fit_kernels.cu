@@ -261,7 +261,15 @@ __device__ __forceinline__ Clu read_staged(const float *stg, int lk, uint32_t ro
   return c;
 }
 
-template <int BLOCK, bool ELOSS>
+// Fitted state and covariance all finite.
+__device__ __forceinline__ bool state_finite(const Trk &T) {
+  bool fin = isfinite(T.dy) && isfinite(T.dz) && isfinite(T.snp()) && isfinite(T.tl()) && isfinite(T.w());
+#pragma unroll
+  for (int i = 0; i < 15; ++i) fin = fin && isfinite(T.c[i]);
+  return fin;
+}
+
+template <int BLOCK, bool VAR>
 __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
   const int st0 = A.status[t];
@@ -306,146 +314,173 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
     if (st0 == ST_OK) {
       uint32_t gate_hi, gate_lo;
       split64(A.chi2_max_d, gate_hi, gate_lo);
-      int nacc_out = 0;
-      // candidate: the next cluster to use, read from the lane's staged chunk;
-      // the following chunk is in flight (cp.async) while this one is used
       const int nch = (n + kChunk - 1) / kChunk;
-      int kc = 0;
       const uint32_t rsh = (uint32_t)(reinterpret_cast<uintptr_t>(A.row + a) & 3u);
-      stage_chunk<BLOCK>(A, a, e, 0, stg);
-      cp_async_wait_all();
-      uint32_t rows_cur = staged_rows<BLOCK>(stg, 0, rsh);
-      if (nch > 1) stage_chunk<BLOCK>(A, a, e, 1, stg);
-      Clu cand = read_staged<BLOCK>(stg, 0, rows_cur);
-      int rprev = -1;
-      st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
-      // ---------------- outward pass: rows row[0] .. row[n-1] ----------------
-      for (int r = cand.r; st == ST_OK; ++r) {
-        const bool has = (cand.r == r);
-        const float xt = has ? cand.x : s_rowx[r];
-        if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
-        xcur = xt;
-        if (has) {
-          bool acc;
-          double chi2;
-          const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo,
-                                 A.chi2_out_c != nullptr, acc, chi2);
-          if (ust != ST_OK) { st = ust; break; }
-          if (acc) bits[32 * (kc >> 5)] |= 1u << (kc & 31);
-          if (A.chi2_out_c) A.chi2_out_c[a + kc] = chi2;
-          ++out_done;
-          nacc_out += acc ? 1 : 0;
-          rprev = cand.r;
-          if (++kc < n) {
-            if (kc % kChunk == 0) {  // entering chunk kc/4
-              cp_async_wait_all();
-              rows_cur = staged_rows<BLOCK>(stg, kc / kChunk, rsh);
-              if (kc / kChunk + 1 < nch) stage_chunk<BLOCK>(A, a, e, kc / kChunk + 1, stg);
-            }
-            cand = read_staged<BLOCK>(stg, kc, rows_cur);
-            const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
-            if (vs != ST_OK) { st = vs; break; }
-          }
-        }
-        if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
-        if (ELOSS && !eloss(T, A.xrho, A.el_kza, A.el_a, A.el_ratio, A.mass2, 1.0f)) { st = ST_STOPPED; break; }
-        if (kc == n) break;
-      }
-      // ---------------- restart ----------------
-      if (st == ST_OK) {
-        // cand holds the outermost cluster n-1
-        if (10 * nacc_out < 9 * n) {
-          // the outward pass accepted fewer than 90 % of the clusters: re-seed
-          // at the outermost cluster (circle through clusters n-1, n/2, 0 for
-          // motion towards cluster 0, reversed) with the seed covariance
-          float p[5];
-          const int64_t m = a + n / 2;
-          seed3(cand.x, cand.y, cand.z, A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
-          T.sp = -p[2];
-          T.spl = 0.f;
-          T.tl0 = -p[3];
-          T.dtl = 0.f;
-          T.w0 = -p[4];
-          T.dw = 0.f;
-          T.ya = cand.y;
-          T.za = cand.z;
-          T.dy = 0.f;
-          T.dz = 0.f;
-#pragma unroll
-          for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
-          T.c[0] = A.seed_cov[0];
-          T.c[2] = A.seed_cov[1];
-          T.c[5] = A.seed_cov[2];
-          T.c[9] = A.seed_cov[3];
-          T.c[14] = A.seed_cov[4];
-        } else {
-          // inward restart: diagonal, outward variances inflated, capped at the seed's
-          const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
-          const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
-          const float d2 = fminf(A.restart_scale * T.c[5], A.seed_cov[2]);
-          const float d3 = fminf(A.restart_scale * (T.c[9] + T.c9l), A.seed_cov[3]);
-          const float d4 = fminf(A.restart_scale * (T.c[14] + T.c14l), A.seed_cov[4]);
-#pragma unroll
-          for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
-          T.c[0] = d0;
-          T.c[2] = d1;
-          T.c[5] = d2;
-          T.c[9] = d3;
-          T.c[14] = d4;
-        }
-        T.c9l = 0.f;
-        T.c14l = 0.f;
-        if (A.restart_state) {
-          float *rs = A.restart_state + 5 * t;
-          rs[0] = T.ya + T.dy;
-          rs[1] = T.za + T.dz;
-          rs[2] = T.snp();
-          rs[3] = T.tl();
-          rs[4] = T.w();
-        }
-        // ---------------- inward pass: rows row[n-1] .. row[0] ----------------
-        kc = n - 1;
-        // the last chunk is current; restage the one below it into the other buffer
-        if (nch > 1) stage_chunk<BLOCK>(A, a, e, nch - 2, stg);
-        for (int r = cand.r;; --r) {
+      // passes: one outward + inward pair, or (the variant) 1 + n_iter of them
+      for (int it = 0;; ++it) {
+        int nacc_out = 0;
+        // candidate: the next cluster to use, read from the lane's staged chunk;
+        // the following chunk is in flight (cp.async) while this one is used
+        int kc = 0;
+        stage_chunk<BLOCK>(A, a, e, 0, stg);
+        cp_async_wait_all();
+        uint32_t rows_cur = staged_rows<BLOCK>(stg, 0, rsh);
+        if (nch > 1) stage_chunk<BLOCK>(A, a, e, 1, stg);
+        Clu cand = read_staged<BLOCK>(stg, 0, rows_cur);
+        int rprev = -1;
+        st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
+        // ---------------- outward pass: rows row[0] .. row[n-1] ----------------
+        for (int r = cand.r; st == ST_OK; ++r) {
           const bool has = (cand.r == r);
           const float xt = has ? cand.x : s_rowx[r];
           if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
           xcur = xt;
-          // the layer of row r lies beyond the plane in outward motion: its loss is added back first
-          if (ELOSS && !eloss(T, A.xrho, A.el_kza, A.el_a, A.el_ratio, A.mass2, -1.0f)) { st = ST_STOPPED; break; }
           if (has) {
             bool acc;
             double chi2;
-            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc,
-                                   chi2);
+            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo,
+                                   A.chi2_out_c != nullptr, acc, chi2);
             if (ust != ST_OK) { st = ust; break; }
-            if (A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;
-            chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
-            nacc += acc ? 1 : 0;
-            const uint32_t ob = (bits[32 * (kc >> 5)] >> (kc & 31)) & 1u;
-            acc_t[kc] = (uint8_t)(ob | (acc ? 2u : 0u));
-            ++done;
-            if (--kc >= 0) {
-              if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above
+            if (acc) bits[32 * (kc >> 5)] |= 1u << (kc & 31);
+            if (A.chi2_out_c) A.chi2_out_c[a + kc] = chi2;
+            ++out_done;
+            nacc_out += acc ? 1 : 0;
+            rprev = cand.r;
+            if (++kc < n) {
+              if (kc % kChunk == 0) {  // entering chunk kc/4
                 cp_async_wait_all();
                 rows_cur = staged_rows<BLOCK>(stg, kc / kChunk, rsh);
-                if (kc / kChunk > 0) stage_chunk<BLOCK>(A, a, e, kc / kChunk - 1, stg);
+                if (kc / kChunk + 1 < nch) stage_chunk<BLOCK>(A, a, e, kc / kChunk + 1, stg);
               }
               cand = read_staged<BLOCK>(stg, kc, rows_cur);
+              const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
+              if (vs != ST_OK) { st = vs; break; }
             }
           }
           if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
-          if (kc < 0) break;
+          if (VAR && A.xrho > 0.f && !eloss(T, A.xrho, A.el_kza, A.el_a, A.el_ratio, A.mass2, 1.0f)) {
+            st = ST_STOPPED;
+            break;
+          }
+          if (kc == n) break;
         }
-      }
-      cp_async_wait_all();  // no copy may land in the column after this track
-      if (st == ST_OK) {
-        bool fin = isfinite(T.dy) && isfinite(T.dz) && isfinite(T.snp()) && isfinite(T.tl()) && isfinite(T.w());
+        // ---------------- restart ----------------
+        if (st == ST_OK) {
+          // cand holds the outermost cluster n-1
+          if (10 * nacc_out < 9 * n) {
+            // the outward pass accepted fewer than 90 % of the clusters: re-seed
+            // at the outermost cluster (circle through clusters n-1, n/2, 0 for
+            // motion towards cluster 0, reversed) with the seed covariance
+            float p[5];
+            const int64_t m = a + n / 2;
+            seed3(cand.x, cand.y, cand.z, A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
+            T.sp = -p[2];
+            T.spl = 0.f;
+            T.tl0 = -p[3];
+            T.dtl = 0.f;
+            T.w0 = -p[4];
+            T.dw = 0.f;
+            T.ya = cand.y;
+            T.za = cand.z;
+            T.dy = 0.f;
+            T.dz = 0.f;
 #pragma unroll
-        for (int i = 0; i < 15; ++i) fin = fin && isfinite(T.c[i]);
-        if (!fin) st = ST_NONFINITE;
-      }
+            for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+            T.c[0] = A.seed_cov[0];
+            T.c[2] = A.seed_cov[1];
+            T.c[5] = A.seed_cov[2];
+            T.c[9] = A.seed_cov[3];
+            T.c[14] = A.seed_cov[4];
+          } else {
+            // inward restart: diagonal, outward variances inflated, capped at the seed's
+            const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
+            const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
+            const float d2 = fminf(A.restart_scale * T.c[5], A.seed_cov[2]);
+            const float d3 = fminf(A.restart_scale * (T.c[9] + T.c9l), A.seed_cov[3]);
+            const float d4 = fminf(A.restart_scale * (T.c[14] + T.c14l), A.seed_cov[4]);
+#pragma unroll
+            for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+            T.c[0] = d0;
+            T.c[2] = d1;
+            T.c[5] = d2;
+            T.c[9] = d3;
+            T.c[14] = d4;
+          }
+          T.c9l = 0.f;
+          T.c14l = 0.f;
+          if (A.restart_state) {
+            float *rs = A.restart_state + 5 * t;
+            rs[0] = T.ya + T.dy;
+            rs[1] = T.za + T.dz;
+            rs[2] = T.snp();
+            rs[3] = T.tl();
+            rs[4] = T.w();
+          }
+          // ---------------- inward pass: rows row[n-1] .. row[0] ----------------
+          kc = n - 1;
+          // the last chunk is current; restage the one below it into the other buffer
+          if (nch > 1) stage_chunk<BLOCK>(A, a, e, nch - 2, stg);
+          for (int r = cand.r;; --r) {
+            const bool has = (cand.r == r);
+            const float xt = has ? cand.x : s_rowx[r];
+            if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
+            xcur = xt;
+            // the layer of row r lies beyond the plane in outward motion: its loss is added back first
+            if (VAR && A.xrho > 0.f && !eloss(T, A.xrho, A.el_kza, A.el_a, A.el_ratio, A.mass2, -1.0f)) {
+              st = ST_STOPPED;
+              break;
+            }
+            if (has) {
+              bool acc;
+              double chi2;
+              const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc,
+                                     chi2);
+              if (ust != ST_OK) { st = ust; break; }
+              if (A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;
+              chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
+              nacc += acc ? 1 : 0;
+              const uint32_t ob = (bits[32 * (kc >> 5)] >> (kc & 31)) & 1u;
+              acc_t[kc] = (uint8_t)(ob | (acc ? 2u : 0u));
+              ++done;
+              if (--kc >= 0) {
+                if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above
+                  cp_async_wait_all();
+                  rows_cur = staged_rows<BLOCK>(stg, kc / kChunk, rsh);
+                  if (kc / kChunk > 0) stage_chunk<BLOCK>(A, a, e, kc / kChunk - 1, stg);
+                }
+                cand = read_staged<BLOCK>(stg, kc, rows_cur);
+              }
+            }
+            if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
+            if (kc < 0) break;
+          }
+        }
+        if (!VAR || st != ST_OK || it >= A.n_iter) break;
+        // seed iteration: the fitted state at the innermost cluster (xcur) seeds
+        // another outward pass with the seed covariance; a non-finite state ends
+        // the fit instead.  Nothing is in flight: the inward pass ends on chunk 0.
+        if (!state_finite(T)) {
+          st = ST_NONFINITE;
+          break;
+        }
+#pragma unroll
+        for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+        T.c[0] = A.seed_cov[0];
+        T.c[2] = A.seed_cov[1];
+        T.c[5] = A.seed_cov[2];
+        T.c[9] = A.seed_cov[3];
+        T.c[14] = A.seed_cov[4];
+        T.c9l = 0.f;
+        T.c14l = 0.f;
+#pragma unroll
+        for (int w = 0; w < kBitWords; ++w) bits[32 * w] = 0u;
+        done = 0;
+        out_done = 0;
+        chi2sum = 0.0;
+        nacc = 0;
+      }  // passes
+      cp_async_wait_all();  // no copy may land in the column after this track
+      if (st == ST_OK && !state_finite(T)) st = ST_NONFINITE;
     }
     // accept bytes not written by the inward pass (failed or unfitted tracks): outward bits only
     for (int64_t k = a; k < e - done; ++k) {
@@ -474,9 +509,10 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   A.status[t] = st;
 }
 
-// ELOSS: the variant with the energy-loss step (a separate instantiation, so
-// that the fit without it keeps its own register allocation and schedule).
-template <int BLOCK, int MINB, bool ELOSS>
+// VAR: the variant -- energy loss and seed iteration, each checked at run
+// time (a separate instantiation, so that the plain fit keeps its own
+// register allocation and schedule).
+template <int BLOCK, int MINB, bool VAR>
 __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   float *s_rowx = reinterpret_cast<float *>(smem);
@@ -495,7 +531,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
     const int64_t i = (int64_t)base + lane;
     if (i < A.n_tracks) {
       const int64_t t = A.perm ? (int64_t)A.perm[i] : i;
-      fit_track<BLOCK, ELOSS>(A, t, bits, s_rowx, stg);
+      fit_track<BLOCK, VAR>(A, t, bits, s_rowx, stg);
     }
     __syncwarp();
   }
@@ -522,30 +558,30 @@ cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches) {
 
 // Raise the dynamic shared memory limit of one k_fit instantiation, once per
 // device (the attribute belongs to the function in the current device's context).
-template <int BLOCK, int MINB, bool ELOSS> static cudaError_t set_fit_smem() {
+template <int BLOCK, int MINB, bool VAR> static cudaError_t set_fit_smem() {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_fit<BLOCK, MINB, ELOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_fit<BLOCK, MINB, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fit_smem<BLOCK>());
   if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
 
-template <int BLOCK, int MINB, bool ELOSS> static cudaError_t launch_fit_as(const FitArgs &a, int grid,
+template <int BLOCK, int MINB, bool VAR> static cudaError_t launch_fit_as(const FitArgs &a, int grid,
                                                                              cudaStream_t stream) {
-  cudaError_t e = set_fit_smem<BLOCK, MINB, ELOSS>();
+  cudaError_t e = set_fit_smem<BLOCK, MINB, VAR>();
   if (e != cudaSuccess) return e;
-  k_fit<BLOCK, MINB, ELOSS><<<grid, BLOCK, fit_smem<BLOCK>(), stream>>>(a);
+  k_fit<BLOCK, MINB, VAR><<<grid, BLOCK, fit_smem<BLOCK>(), stream>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {
   if (a.n_tracks <= 0) return cudaSuccess;
-  const bool el = a.xrho > 0.0f;
+  const bool el = a.xrho > 0.0f || a.n_iter > 0;  // the variant
   if (block == 128)
     return el ? launch_fit_as<128, 4, true>(a, grid, stream) : launch_fit_as<128, 4, false>(a, grid, stream);
   return el ? launch_fit_as<256, 2, true>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
@@ -578,13 +614,13 @@ int fit_default_blocks_per_sm(int block) {
   return occ < want ? occ : want;
 }
 
-int fit_regs_per_thread(int block, bool eloss) {
+int fit_regs_per_thread(int block, bool variant) {
   cudaFuncAttributes at;
   cudaError_t e;
   if (block == 128)
-    e = eloss ? cudaFuncGetAttributes(&at, k_fit<128, 4, true>) : cudaFuncGetAttributes(&at, k_fit<128, 4, false>);
+    e = variant ? cudaFuncGetAttributes(&at, k_fit<128, 4, true>) : cudaFuncGetAttributes(&at, k_fit<128, 4, false>);
   else
-    e = eloss ? cudaFuncGetAttributes(&at, k_fit<256, 2, true>) : cudaFuncGetAttributes(&at, k_fit<256, 2, false>);
+    e = variant ? cudaFuncGetAttributes(&at, k_fit<256, 2, true>) : cudaFuncGetAttributes(&at, k_fit<256, 2, false>);
   if (e != cudaSuccess) return -1;
   return at.numRegs;
 }

@@ -289,7 +289,7 @@ static int check_config(const tpcfit_config &c) {
     return fail(TPCFIT_E_INVAL, "block_threads must be 0, 128 or 256");
   if (c.blocks_per_sm < 0) return fail(TPCFIT_E_INVAL, "blocks_per_sm < 0");
   if (!(c.res_step_y_cm > 0.0f) || !(c.res_step_z_cm > 0.0f)) return fail(TPCFIT_E_INVAL, "residual steps must be > 0");
-  if (const char *why = check_eloss_params(c)) return fail(TPCFIT_E_INVAL, "%s", why);
+  if (const char *why = check_variant_params(c)) return fail(TPCFIT_E_INVAL, "%s", why);
   return TPCFIT_OK;
 }
 
@@ -345,7 +345,7 @@ extern "C" int tpcfit_create(const tpcfit_config *cfg_in, tpcfit_handle **out) {
   h->fit_block = cfg.block_threads ? cfg.block_threads : 256;
   const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(h->fit_block);
   h->fit_grid = h->sms * bps;
-  h->fit_regs = fit_regs_per_thread(h->fit_block, cfg.xrho_per_row > 0.0f);
+  h->fit_regs = fit_regs_per_thread(h->fit_block, cfg.xrho_per_row > 0.0f || cfg.fit_iterations > 0);
   h->chunk_clusters = cfg.host_chunk_clusters > 0 ? cfg.host_chunk_clusters : (int64_t)16 << 20;
   *out = h;
   return TPCFIT_OK;

@@ -42,6 +42,7 @@ struct FitArgs {
   float xx0, mass2, snp_max, restart_scale;
   float xrho;                    // energy-loss layer per row (g/cm^2); 0 = none
   float el_kza, el_a, el_ratio;  // K Z/A (GeV cm^2/g), 2 m_e / I, m_e / M
+  int32_t n_iter;                // seed iterations: refits seeded from the fitted state
   float seed_cov[5];
   int32_t min_clusters, n_rows;
 };
@@ -105,16 +106,18 @@ inline void fit_params(FitArgs &a, const tpcfit_config &c) {
   a.el_kza = (float)(0.307075e-3 * za);  // K = 0.307075 MeV cm^2 / mol
   a.el_a = (float)(2.0 * me / (iev * 1e-9));
   a.el_ratio = c.mass_gev > 0.0f ? (float)(me / (double)c.mass_gev) : 0.0f;
+  a.n_iter = c.fit_iterations;
   for (int i = 0; i < 5; ++i) a.seed_cov[i] = c.seed_cov[i];
   a.min_clusters = c.min_clusters;
   a.n_rows = c.n_rows;
 }
 
-// NULL, or why the energy-loss parameters of a configuration are invalid.
-inline const char *check_eloss_params(const tpcfit_config &c) {
+// NULL, or why the variant parameters (energy loss, seed iteration) of a configuration are invalid.
+inline const char *check_variant_params(const tpcfit_config &c) {
   if (!(c.xrho_per_row >= 0.0f) || !(c.eloss_z_over_a >= 0.0f) || !(c.eloss_i_ev >= 0.0f))
     return "energy-loss parameters must be >= 0";
   if (c.xrho_per_row > 0.0f && !(c.mass_gev > 0.0f)) return "energy loss needs mass_gev > 0";
+  if (c.fit_iterations < 0 || c.fit_iterations > 16) return "fit_iterations must be in [0, 16]";
   return nullptr;
 }
 
@@ -165,6 +168,6 @@ cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream);
 int fit_blocks_per_sm(int block);
 // tuned default residency (blocks per SM) for a block size
 int fit_default_blocks_per_sm(int block);
-int fit_regs_per_thread(int block, bool eloss);  // of the instantiation a handle launches
+int fit_regs_per_thread(int block, bool variant);  // of the instantiation a handle launches
 
 }  // namespace tpcfit

@@ -101,7 +101,7 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   if (cfg.n_rows < 1 || cfg.n_rows > kMaxRows || !(cfg.snp_max > 0.f && cfg.snp_max < 1.f) ||
       !(cfg.chi2_max > 0.f) || cfg.device < 0 || cfg.device >= kMaxDevices)
     return fail(TPCFIT_E_INVAL, "configuration out of range");
-  if (const char *why = check_eloss_params(cfg)) return fail(TPCFIT_E_INVAL, why);
+  if (const char *why = check_variant_params(cfg)) return fail(TPCFIT_E_INVAL, why);
   if (cudaSetDevice(cfg.device) != cudaSuccess) {
     cudaGetLastError();
     return fail(TPCFIT_E_NODEV, "cannot select the CUDA device");

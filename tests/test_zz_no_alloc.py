@@ -93,3 +93,15 @@ def test_noalloc_with_energy_loss_equals_fit(T):
     got = host(out)
     assert_same_fit(got, ref)
     assert np.array_equal(got["state"], ref["state"])  # same kernel, same inputs: bit-identical
+
+
+def test_noalloc_with_seed_iteration_equals_fit(T):
+    f = tpcgen.generate("detector50k", n_tracks=8_000, seed=35)
+    d = dev_frame(f)
+    with T.Fitter(fit_iterations=2) as fx:
+        ref = host(fx.fit(d))
+    out = T.alloc_result(f.n_tracks, f.n_clusters, device="cuda")
+    T.fit_noalloc(d, out, T.default_config(fit_iterations=2))
+    got = host(out)
+    assert_same_fit(got, ref)
+    assert np.array_equal(got["state"], ref["state"])
