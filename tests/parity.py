@@ -1,6 +1,6 @@
 """GPU-vs-oracle comparison with the tolerances of the fit's precision split.
 
-Tolerances (stated in the north-star of this project and kept here):
+Tolerances of the parity bar:
   state      |dp_i| / sqrt(C_ii oracle) < 1e-3
   covariance |dC_ij| / sqrt(C_ii C_jj)  < 1e-4   (normalised by the diagonal)
   chi2       |dchi2| <= 1e-4 * max(chi2, 1)
