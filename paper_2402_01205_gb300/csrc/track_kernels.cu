@@ -116,7 +116,11 @@ __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
     const int iy0 = follow_ybin(yp - wy, xr, A.tan_edge, A.ny), iy1 = follow_ybin(yp + wy, xr, A.tan_edge, A.ny);
     const int iz0 = follow_zbin(zp - wz, A.z_max, A.nz), iz1 = follow_zbin(zp + wz, A.z_max, A.nz);
     const int64_t base = ((int64_t)sec * A.n_rows + r) * A.nz;
-    int32_t best = -1;
+    // best candidate: its position bq in cell order; its cluster index bk is
+    // read only to break an exact tie (ties: lowest index), else once after
+    // the search, while the update runs
+    int64_t bq = -1;
+    int32_t bk = -1;
     float bchi = INFINITY;
     float4 bc = make_float4(0.f, 0.f, 0.f, 0.f);
     const float S01 = T.c[1];
@@ -131,17 +135,25 @@ __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
         if (fabsf(r0v) > wy || fabsf(r1v) > wz) continue;
         const float S00 = T.c[0] + c.z, S11 = T.c[2] + c.w;
         const float det = fmaf(S00, S11, -S01 * S01);
-        const float chi = (r0v * fmaf(S11, r0v, -S01 * r1v) + r1v * fmaf(S00, r1v, -S01 * r0v)) / det;
-        if (chi <= bchi) {
+        // ranking only (the gated update recomputes chi2 with its FP64 island)
+        const float chi = __fdividef(r0v * fmaf(S11, r0v, -S01 * r1v) + r1v * fmaf(S00, r1v, -S01 * r0v), det);
+        if (chi < bchi) {
+          bchi = chi;
+          bq = q;
+          bk = -1;
+          bc = c;
+        } else if (chi == bchi && bq >= 0) {
+          if (bk < 0) bk = A.cidx[bq];
           const int32_t k = A.cidx[q];
-          if (chi < bchi || k < best) {
-            bchi = chi;
-            best = k;
+          if (k < bk) {
+            bq = q;
+            bk = k;
             bc = c;
           }
         }
       }
     }
+    const int32_t best = bq < 0 ? -1 : (bk >= 0 ? bk : A.cidx[bq]);
     bool acc = false;
     if (best >= 0) {
       double chi2;
