@@ -30,18 +30,19 @@ namespace {
 
 constexpr int kTile = 4096;  // exclusive-scan tile: 1024 threads x 4
 
-// cell of every cluster (or n_cells for clusters outside the grid's sectors/rows)
+// cell of every cluster (or 0xffffffff for clusters outside the grid's sectors/rows) and its rank in the cell
 __global__ void k_cell_count(const float *__restrict__ y, const float *__restrict__ z, const uint8_t *__restrict__ row,
                              const uint8_t *__restrict__ sector, int64_t nc, int n_sectors, int n_rows, int ny,
                              int nz, float z_max, float tan_edge, const float *__restrict__ row_x,
-                             uint32_t *__restrict__ cell_of, uint32_t *__restrict__ count) {
+                             uint32_t *__restrict__ cell_of, uint32_t *__restrict__ rank,
+                             uint32_t *__restrict__ count) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
     const int r = row[k], s = sector[k];
     uint32_t cell = 0xffffffffu;
     if (r < n_rows && s < n_sectors) {
       const int iz = follow_zbin(z[k], z_max, nz), iy = follow_ybin(y[k], row_x[r], tan_edge, ny);
       cell = (uint32_t)((((int64_t)s * n_rows + r) * nz + iz) * ny + iy);
-      atomicAdd(&count[cell], 1u);
+      rank[k] = atomicAdd(&count[cell], 1u);  // the cluster's place in its cell
     }
     cell_of[k] = cell;
   }
@@ -108,12 +109,12 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t
 
 __global__ void k_cell_fill(const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ sy2,
                             const float *__restrict__ sz2, int64_t nc, const uint32_t *__restrict__ cell_of,
-                            const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
+                            const uint32_t *__restrict__ rank, const uint32_t *__restrict__ start,
                             float4 *__restrict__ crec, int32_t *__restrict__ cidx) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t c = cell_of[k];
     if (c == 0xffffffffu) continue;
-    const uint32_t q = start[c] + atomicAdd(&cursor[c], 1u);
+    const uint32_t q = start[c] + rank[k];
     crec[q] = make_float4(y[k], z[k], sy2[k], sz2[k]);
     cidx[q] = (int32_t)k;
   }
@@ -256,11 +257,11 @@ extern "C" int tpcfit_follow(tpcfit_handle *h, const tpcfit_follow_config *fc_in
   const int dev = handle_device(h);
   if (ns > 0) FCU(cudaMemsetAsync(tr->att, 0xff, (size_t)ns * nr * sizeof(int32_t), st), "memset att");
   if (ns == 0) return TPCFIT_OK;
-  // scratch: count, cursor, start (n_cells+1), tiles, total, cell_of (nc), cell arrays (nc)
+  // scratch: count, start (n_cells+1), tiles, total, cell_of and rank (nc), cell arrays (nc)
   const int64_t n_tiles = (n_cells + kTile - 1) / kTile;
-  const size_t o_cnt = 0, o_cur = o_cnt + a256(4 * (size_t)n_cells), o_start = o_cur + a256(4 * (size_t)n_cells);
+  const size_t o_cnt = 0, o_start = o_cnt + a256(4 * (size_t)n_cells);
   const size_t o_tiles = o_start + a256(4 * (size_t)(n_cells + 1)), o_tot = o_tiles + a256(4 * (size_t)n_tiles + 4);
-  const size_t o_of = o_tot + 256, o_rec = o_of + a256(4 * (size_t)nc);
+  const size_t o_of = o_tot + 256, o_rank = o_of + a256(4 * (size_t)nc), o_rec = o_rank + a256(4 * (size_t)nc);
   const size_t o_idx = o_rec + a256(16 * (size_t)nc), bytes = o_idx + a256(4 * (size_t)nc);
   void *base = nullptr;
   int rc = handle_follow_scratch(h, bytes, &base);
@@ -271,13 +272,13 @@ extern "C" int tpcfit_follow(tpcfit_handle *h, const tpcfit_follow_config *fc_in
   if (nc > 0) {
     k_cell_count<<<grid1d(nc, dev), 256, 0, st>>>(hits->y, hits->z, hits->row, hits->sector, nc, fc.n_sectors, nr,
                                                   fc.n_ybins, fc.n_zbins, fc.z_max, fc.tan_edge, handle_rowx(h),
-                                                  U(o_of), U(o_cnt));
+                                                  U(o_of), U(o_rank), U(o_cnt));
     FCU(cudaGetLastError(), "k_cell_count");
   }
   if ((rc = scan_u32(U(o_cnt), n_cells, U(o_start), U(o_tiles), U(o_tot), dev, st))) return rc;
   if (nc > 0) {
-    k_cell_fill<<<grid1d(nc, dev), 256, 0, st>>>(hits->y, hits->z, hits->sy2, hits->sz2, nc, U(o_of), U(o_start),
-                                                 U(o_cur), reinterpret_cast<float4 *>(sc + o_rec),
+    k_cell_fill<<<grid1d(nc, dev), 256, 0, st>>>(hits->y, hits->z, hits->sy2, hits->sz2, nc, U(o_of), U(o_rank),
+                                                 U(o_start), reinterpret_cast<float4 *>(sc + o_rec),
                                                  reinterpret_cast<int32_t *>(sc + o_idx));
     FCU(cudaGetLastError(), "k_cell_fill");
   }
