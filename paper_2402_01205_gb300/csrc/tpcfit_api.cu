@@ -653,8 +653,6 @@ static int validate_host_offsets(const tpcfit_frame *f) {
   return TPCFIT_OK;
 }
 
-// host frame (and host or device results): chunks of tracks, copies and fits
-// of consecutive chunks overlapped (two staging buffers).
 // Chunk schedule of a host frame (host path and serving).  A call costs the
 // host->device copy of every input byte (the link is the bound) plus what no
 // copy overlaps: the fit and the result copy of the last chunk, and a setup
@@ -702,6 +700,8 @@ int64_t tpcfit::chunk_cuts(const int64_t *off, int64_t nt, int64_t nc_all, int64
   return -1;
 }
 
+// host frame (and host or device results): chunks of tracks, copies and fits
+// of consecutive chunks overlapped (two staging buffers).
 static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
   if (r->chi2_out_cluster || r->chi2_in_cluster || r->restart_state)
     return fail(TPCFIT_E_INVAL, "diagnostic outputs need a device frame and device results");

@@ -214,7 +214,7 @@ def test_malformed_offsets_rejected(T):
             fx.fit(dev_frame(bad))
         assert ei.value.code == T.E_INVAL
         with pytest.raises(T.TpcfitError) as ei:
-            fx.fit(bad)  # host frame: rejected before any copy
+            fx.fit(bad)  # host frame: rejected before any fit
         assert ei.value.code == T.E_INVAL
         # the handle stays usable
         ok = fx.fit(dev_frame(f))
