@@ -128,3 +128,18 @@ def test_batch_rejects_host_frames(T, events):
         with pytest.raises(T.TpcfitError) as ei:
             T.Batch(fx, f.subset(0, 10), T.alloc_result(10, int(f.offsets[10])))
         assert ei.value.code == T.E_INVAL
+
+
+def test_batch_graph_of_the_fit_variant_equals_its_plain_fit(T, events):
+    """The graph-captured sequence launches the variant instantiation when the
+    handle's configuration asks for it (energy loss, seed iteration)."""
+    f, ev = events
+    g = dev_frame(f)
+    with T.Fitter(xrho_per_row=0.01, fit_iterations=1) as fx:
+        plain = host(fx.fit(g))
+        with T.Batch(fx, g) as b:
+            b.launch()
+            b.sync(timeout_s=60)
+            same(plain, host(b.res))
+    with T.Fitter() as fx:
+        assert not np.array_equal(host(fx.fit(g))["state"], plain["state"])

@@ -129,3 +129,16 @@ def test_frame_split_into_parts_equals_plain_fit(T):
     for r in res:
         for k in ref:
             assert np.array_equal(ref[k], r[k].numpy(), equal_nan=k in ("state", "cov")), k
+
+
+def test_served_fit_variant_equals_its_plain_fit(T):
+    """Served frames (split into parts) use the handle's fit variant too."""
+    f = tpcgen.generate("detector50k", n_tracks=8_000, seed=7)
+    cfg = dict(xrho_per_row=0.01, fit_iterations=1)
+    with T.Fitter(**cfg) as fx:
+        ref = fx.fit(f)
+    with T.Fitter(host_chunk_clusters=200_000, max_slots=3, **cfg) as fx:
+        r = T.alloc_result(f.n_tracks, f.n_clusters, pinned=True)
+        assert fx.wait(fx.submit(pinned_frame(f), r), 60)[0] == T.DONE
+    for k in ref:
+        assert np.array_equal(ref[k], r[k].numpy(), equal_nan=k in ("state", "cov")), k
