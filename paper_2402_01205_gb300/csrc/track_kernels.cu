@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256) k_residuals(FitArgs A) {
 // (FP32; ties: lowest cluster index) goes through the fit's gated update.
 // ---------------------------------------------------------------------------
 enum { FL_END = 0, FL_MISSES = 1 };
+constexpr int kFollowBatch = 4;  // cluster records loaded together in the candidate search
 
 __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,28 +128,38 @@ __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
     for (int iz = iz0; iz <= iz1; ++iz) {
       const int64_t row0 = (base + iz) * A.ny;
       const uint32_t q0 = A.cell_start[row0 + iy0], q1 = A.cell_start[row0 + iy1 + 1];
-      float4 nx = q0 < q1 ? A.crec[q0] : make_float4(0.f, 0.f, 0.f, 0.f);
-      for (uint32_t q = q0; q < q1; ++q) {
-        const float4 c = nx;
-        if (q + 1 < q1) nx = A.crec[q + 1];  // the next record is in flight while this one is tested
-        const float r0v = (c.x - T.ya) - T.dy, r1v = (c.y - T.za) - T.dz;
-        if (fabsf(r0v) > wy || fabsf(r1v) > wz) continue;
-        const float S00 = T.c[0] + c.z, S11 = T.c[2] + c.w;
-        const float det = fmaf(S00, S11, -S01 * S01);
-        // ranking only (the gated update recomputes chi2 with its FP64 island)
-        const float chi = __fdividef(r0v * fmaf(S11, r0v, -S01 * r1v) + r1v * fmaf(S00, r1v, -S01 * r0v), det);
-        if (chi < bchi) {
-          bchi = chi;
-          bq = q;
-          bk = -1;
-          bc = c;
-        } else if (chi == bchi && bq >= 0) {
-          if (bk < 0) bk = A.cidx[bq];
-          const int32_t k = A.cidx[q];
-          if (k < bk) {
+      // records in batches of kFollowBatch, all loads of a batch in flight
+      // together (a window holds a few clusters: about one memory latency per
+      // z bin instead of one per candidate); tested in cell order
+      for (uint32_t qb = q0; qb < q1; qb += kFollowBatch) {
+        float4 cb[kFollowBatch];
+#pragma unroll
+        for (int u = 0; u < kFollowBatch; ++u)
+          cb[u] = (qb + u < q1) ? A.crec[qb + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kFollowBatch; ++u) {
+          const uint32_t q = qb + u;
+          if (q >= q1) break;
+          const float4 c = cb[u];
+          const float r0v = (c.x - T.ya) - T.dy, r1v = (c.y - T.za) - T.dz;
+          if (fabsf(r0v) > wy || fabsf(r1v) > wz) continue;
+          const float S00 = T.c[0] + c.z, S11 = T.c[2] + c.w;
+          const float det = fmaf(S00, S11, -S01 * S01);
+          // ranking only (the gated update recomputes chi2 with its FP64 island)
+          const float chi = __fdividef(r0v * fmaf(S11, r0v, -S01 * r1v) + r1v * fmaf(S00, r1v, -S01 * r0v), det);
+          if (chi < bchi) {
+            bchi = chi;
             bq = q;
-            bk = k;
+            bk = -1;
             bc = c;
+          } else if (chi == bchi && bq >= 0) {
+            if (bk < 0) bk = A.cidx[bq];
+            const int32_t k = A.cidx[q];
+            if (k < bk) {
+              bq = q;
+              bk = k;
+              bc = c;
+            }
           }
         }
       }
