@@ -966,6 +966,7 @@ def main():
         e2e = {"value": nc_all * args.e2e_steps / dt, "unit": "clusters/s",
                "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
                "ms_per_step": dt / args.e2e_steps * 1e3, "step_ms": step_ms,
+               "median_ms": float(np.median(step_ms)),
                "path": "tpcfit_fit, TPCFIT_MEM_HOST pinned, chunked overlap",
                "link": dict(link, floor_ms=1e3 * h2d_b / (link["h2d_gbs"] * 1e9),
                             note="pinned copies of 1 GiB timed on this box; floor = the frame's host-to-device "

@@ -737,14 +737,6 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     tpcfit_frame cf = *f;
     CU(copy_clusters_in(*f, c0, c1, ClusterArrays{S.x, S.y, S.z, S.sy2, S.sz2, S.row}, cf, h->h2d));
     CU(cudaEventRecord(h->ev_in[ci & 1], h->h2d));
-    for (int64_t t = t0; t < t1; ++t)
-      if (off[t + 1] < off[t]) {
-        // nothing of this chunk is fitted; let the copies in flight finish
-        wait_stream(h->h2d, -1);
-        wait_stream(h->stream, -1);
-        wait_stream(h->d2h, -1);
-        return fail(TPCFIT_E_INVAL, "offsets decrease at track %lld", (long long)t);
-      }
     // fit
     CU(cudaStreamWaitEvent(h->stream, h->ev_in[ci & 1], 0));
     CU(cudaMemsetAsync(h->scratch.hist, 0, 2 * kKeyBins * sizeof(uint32_t) + 16, h->stream));
@@ -774,9 +766,17 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     CU(cudaEventRecord(S.free_ev, h->d2h));
   }
   CU(cudaMemcpyAsync(h->h_err, h->scratch.err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  // the offsets inside the chunks, checked while the device works (everything
+  // is enqueued first, so a stalled host thread does not idle the link): the
+  // kernels reject such tracks on their own (k_prepare touches nothing of a
+  // track whose offsets leave its chunk); this names the first one
+  int64_t bad_track = -1;
+  for (int64_t t = 0; t < nt && bad_track < 0; ++t)
+    if (off[t + 1] < off[t]) bad_track = t;
   if ((rc = wait_stream(h->stream, -1))) return rc;
   if ((rc = wait_stream(h->d2h, -1))) return rc;
   h->last_launches = launches;
+  if (bad_track >= 0) return fail(TPCFIT_E_INVAL, "offsets decrease at track %lld", (long long)bad_track);
   if (*h->h_err) return fail(TPCFIT_E_INVAL, "malformed track offsets");
   return TPCFIT_OK;
 }
