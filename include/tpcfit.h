@@ -86,7 +86,7 @@ typedef struct tpcfit_config {
   uint64_t hbm_budget_bytes; /* serving: device bytes that resident frames may use (120 GB) */
   int32_t max_slots;      /* serving: frames resident at once (8) */
   int32_t device;         /* CUDA device ordinal (0) */
-  int32_t block_threads;  /* fit kernel block size: 128 or 256 (0 = 256) */
+  int32_t block_threads;  /* fit kernel block size: 128 or 256 (0 = 128) */
   int32_t blocks_per_sm;  /* fit kernel resident blocks per SM; 0 = tuned default (512 threads per SM) */
   int32_t sort_tracks;    /* 1: fit tracks longest-first (default); 0: in frame order */
   float res_step_y_cm;    /* residual code step in y (0.01 cm), see tpcfit_result.res_y */

@@ -102,6 +102,9 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
       !(cfg.chi2_max > 0.f) || cfg.device < 0 || cfg.device >= kMaxDevices)
     return fail(TPCFIT_E_INVAL, "configuration out of range");
   if (const char *why = check_variant_params(cfg)) return fail(TPCFIT_E_INVAL, why);
+  if (cfg.block_threads != 0 && cfg.block_threads != 128 && cfg.block_threads != 256)
+    return fail(TPCFIT_E_INVAL, "block_threads must be 0, 128 or 256");
+  if (cfg.blocks_per_sm < 0) return fail(TPCFIT_E_INVAL, "blocks_per_sm < 0");
   if (cudaSetDevice(cfg.device) != cudaSuccess) {
     cudaGetLastError();
     return fail(TPCFIT_E_NODEV, "cannot select the CUDA device");
@@ -139,14 +142,15 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   if (cfg.row_x0_cm == 85.0f && cfg.row_pitch_cm == (float)(162.0 / 151.0)) pitch = 162.0 / 151.0;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device);
-  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(256);
+  const int block = cfg.block_threads ? cfg.block_threads : 128;  // the handle path's default shape
+  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(block);
   cudaError_t e;
   if ((e = cudaMemsetAsync(sc, 0, kZeroBytes, st)) != cudaSuccess) goto cuda_fail;
   k_noalloc_rowx<<<1, kMaxRows, 0, st>>>(reinterpret_cast<float *>(sc + kRowxOff), (double)cfg.row_x0_cm, pitch);
   if ((e = cudaGetLastError()) != cudaSuccess) goto cuda_fail;
   if ((e = launch_prepare(a, st)) != cudaSuccess) goto cuda_fail;
   if ((e = launch_sort(a, st, nullptr)) != cudaSuccess) goto cuda_fail;
-  if ((e = launch_fit(a, sms * bps, 256, st)) != cudaSuccess) goto cuda_fail;
+  if ((e = launch_fit(a, sms * bps, block, st)) != cudaSuccess) goto cuda_fail;
   {
     int32_t err_host = 0;
     if ((e = cudaMemcpyAsync(&err_host, a.frame_error, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
