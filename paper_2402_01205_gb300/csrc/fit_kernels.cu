@@ -46,13 +46,14 @@ namespace tpcfit {
 
 constexpr int kBitWords = kMaxRows / 32;  // outward accept bits of one track (<= 256 clusters)
 constexpr int kChunk = 4;                 // clusters per staged chunk (per lane)
+constexpr int kStageBufs = 3;             // chunk buffers per lane: a ring, chunk c in buffer c % 3
 constexpr int kStageArrays = 5;           // x, y, z, sy2, sz2
 // dynamic shared memory of k_fit: row table, outward accept bits, staged clusters
 constexpr size_t kSmemRowx = kMaxRows * sizeof(float);
 template <int BLOCK> __host__ __device__ constexpr size_t smem_bits() { return (size_t)(BLOCK / 32) * kBitWords * 32 * sizeof(uint32_t); }
 // staged floats [buf][array][slot][lane], then staged row words [buf][word][lane]
-constexpr int kStageFloats = 2 * kStageArrays * kChunk;  // per lane
-constexpr int kStageRowWords = 2 * 2;                     // per lane: two aligned words per buffer
+constexpr int kStageFloats = kStageBufs * kStageArrays * kChunk;  // per lane
+constexpr int kStageRowWords = kStageBufs * 2;                    // per lane: two aligned words per buffer
 template <int BLOCK> __host__ __device__ constexpr size_t smem_stage() { return (size_t)(kStageFloats + kStageRowWords) * BLOCK * sizeof(float); }
 template <int BLOCK> __host__ __device__ constexpr size_t fit_smem() { return kSmemRowx + smem_bits<BLOCK>() + smem_stage<BLOCK>(); }
 
@@ -200,13 +201,12 @@ struct Clu {
 };
 
 // Issue the copies of chunk c (clusters a+4c .. a+4c+3, clipped to the track)
-// into buffer c&1 of this lane's staging column.  The chunk's four row bytes
+// into buffer `buf` (= c % kStageBufs) of this lane's staging column.  The chunk's four row bytes
 // are copied as the two aligned 32-bit words that hold them (the second only
 // when it holds a byte of the track; an aligned word that holds a byte of an
 // allocation lies inside it, allocations being at least 4-byte granular).
 template <int BLOCK>
-__device__ __forceinline__ void stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, float *stg) {
-  const int buf = c & 1;
+__device__ __forceinline__ void stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, int buf, float *stg) {
   const int64_t k0 = a + (int64_t)kChunk * c;
   float *dst0 = stg + (buf * kStageArrays) * kChunk * BLOCK;
   if (k0 + kChunk <= e) {  // full chunk: four consecutive clusters of each array
@@ -238,19 +238,18 @@ __device__ __forceinline__ void stage_chunk(const FitArgs &A, int64_t a, int64_t
   cp_async_commit();
 }
 
-// Rows of the staged chunk c (current), one byte per cluster; `rsh` is the
+// Rows of the chunk staged in buffer `buf`, one byte per cluster; `rsh` is the
 // byte offset of the track's first row byte within its aligned word.
 template <int BLOCK>
-__device__ __forceinline__ uint32_t staged_rows(const float *stg, int c, uint32_t rsh) {
-  const float *src = stg + (kStageFloats + 2 * (c & 1)) * BLOCK;
+__device__ __forceinline__ uint32_t staged_rows(const float *stg, int buf, uint32_t rsh) {
+  const float *src = stg + (kStageFloats + 2 * buf) * BLOCK;
   return __funnelshift_r(__float_as_uint(src[0]), __float_as_uint(src[BLOCK]), 8u * rsh);
 }
 
-// Cluster lk of the track from the staged chunk lk/4 (which must be current).
+// Cluster in `slot` of the chunk staged in buffer `buf` (whose rows are rows_cur).
 template <int BLOCK>
-__device__ __forceinline__ Clu read_staged(const float *stg, int lk, uint32_t rows_cur) {
-  const int ch = lk / kChunk, slot = lk % kChunk;
-  const float *src = stg + (((ch & 1) * kStageArrays) * kChunk + slot) * BLOCK;
+__device__ __forceinline__ Clu read_staged(const float *stg, int slot, int buf, uint32_t rows_cur) {
+  const float *src = stg + ((buf * kStageArrays) * kChunk + slot) * BLOCK;
   Clu c;
   c.x = src[0];
   c.y = src[kChunk * BLOCK];
@@ -319,18 +318,33 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       // passes: one outward + inward pair, or (the variant) 1 + n_iter of them
       for (int it = 0;; ++it) {
         int nacc_out = 0;
-        // candidate: the next cluster to use, read from the lane's staged chunk;
-        // the following chunk is in flight (cp.async) while this one is used
+        // candidate: the next cluster to use, read from the lane's staged chunks.
+        // The chunks sit in a ring of kStageBufs buffers; copies are issued and
+        // waited for at warp-uniform steps, every kChunk rows of a pass (the
+        // same rows for all lanes of a warp, whose tracks cross as many rows),
+        // so the lanes stage in step.  After each step the lane's current chunk
+        // and the next one have arrived, and a lane reaches at most one new
+        // chunk before the next step.  After an inward pass the ring already
+        // holds chunks 0..2, arrived.
         int kc = 0;
-        stage_chunk<BLOCK>(A, a, e, 0, stg);
+        int staged = nch < kStageBufs ? nch : kStageBufs;  // outward: chunks 0 .. staged-1 issued
+        if (it == 0)
+          for (int c = 0; c < staged; ++c) stage_chunk<BLOCK>(A, a, e, c, c, stg);
         cp_async_wait_all();
+        int cbuf = 0;  // buffer of the current chunk
         uint32_t rows_cur = staged_rows<BLOCK>(stg, 0, rsh);
-        if (nch > 1) stage_chunk<BLOCK>(A, a, e, 1, stg);
-        Clu cand = read_staged<BLOCK>(stg, 0, rows_cur);
+        Clu cand = read_staged<BLOCK>(stg, 0, 0, rows_cur);
         int rprev = -1;
         st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
         // ---------------- outward pass: rows row[0] .. row[n-1] ----------------
-        for (int r = cand.r; st == ST_OK; ++r) {
+        for (int r = cand.r, step = 0; st == ST_OK; ++r, ++step) {
+          if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
+            cp_async_wait_all();
+            if (staged < nch && staged <= kc / kChunk + 2) {  // the buffer of chunk staged-3 is consumed
+              stage_chunk<BLOCK>(A, a, e, staged, staged % kStageBufs, stg);
+              ++staged;
+            }
+          }
           const bool has = (cand.r == r);
           const float xt = has ? cand.x : s_rowx[r];
           if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
@@ -347,12 +361,11 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             nacc_out += acc ? 1 : 0;
             rprev = cand.r;
             if (++kc < n) {
-              if (kc % kChunk == 0) {  // entering chunk kc/4
-                cp_async_wait_all();
-                rows_cur = staged_rows<BLOCK>(stg, kc / kChunk, rsh);
-                if (kc / kChunk + 1 < nch) stage_chunk<BLOCK>(A, a, e, kc / kChunk + 1, stg);
+              if (kc % kChunk == 0) {  // entering chunk kc/4 (arrived)
+                cbuf = cbuf == kStageBufs - 1 ? 0 : cbuf + 1;
+                rows_cur = staged_rows<BLOCK>(stg, cbuf, rsh);
               }
-              cand = read_staged<BLOCK>(stg, kc, rows_cur);
+              cand = read_staged<BLOCK>(stg, kc % kChunk, cbuf, rows_cur);
               const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
               if (vs != ST_OK) { st = vs; break; }
             }
@@ -418,9 +431,17 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           }
           // ---------------- inward pass: rows row[n-1] .. row[0] ----------------
           kc = n - 1;
-          // the last chunk is current; restage the one below it into the other buffer
-          if (nch > 1) stage_chunk<BLOCK>(A, a, e, nch - 2, stg);
-          for (int r = cand.r;; --r) {
+          // the ring holds the last kStageBufs chunks (the outward pass reached
+          // the last one, so all of them have arrived); the last is current
+          int lowest = nch > kStageBufs ? nch - kStageBufs : 0;  // inward: the lowest chunk issued
+          for (int r = cand.r, step = 0;; --r, ++step) {
+            if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
+              cp_async_wait_all();
+              if (lowest > 0 && lowest + 1 >= kc / kChunk) {  // the buffer of chunk lowest+2 is consumed
+                --lowest;
+                stage_chunk<BLOCK>(A, a, e, lowest, lowest % kStageBufs, stg);
+              }
+            }
             const bool has = (cand.r == r);
             const float xt = has ? cand.x : s_rowx[r];
             if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
@@ -443,12 +464,11 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
               acc_t[kc] = (uint8_t)(ob | (acc ? 2u : 0u));
               ++done;
               if (--kc >= 0) {
-                if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above
-                  cp_async_wait_all();
-                  rows_cur = staged_rows<BLOCK>(stg, kc / kChunk, rsh);
-                  if (kc / kChunk > 0) stage_chunk<BLOCK>(A, a, e, kc / kChunk - 1, stg);
+                if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above (arrived)
+                  cbuf = cbuf == 0 ? kStageBufs - 1 : cbuf - 1;
+                  rows_cur = staged_rows<BLOCK>(stg, cbuf, rsh);
                 }
-                cand = read_staged<BLOCK>(stg, kc, rows_cur);
+                cand = read_staged<BLOCK>(stg, kc % kChunk, cbuf, rows_cur);
               }
             }
             if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
@@ -458,7 +478,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         if (!VAR || st != ST_OK || it >= A.n_iter) break;
         // seed iteration: the fitted state at the innermost cluster (xcur) seeds
         // another outward pass with the seed covariance; a non-finite state ends
-        // the fit instead.  Nothing is in flight: the inward pass ends on chunk 0.
+        // the fit instead.  The ring holds chunks 0..2: the inward pass ended on chunk 0.
         if (!state_finite(T)) {
           st = ST_NONFINITE;
           break;
