@@ -23,9 +23,9 @@ import os
 import statistics
 from typing import Callable, Iterable, Optional
 
-# occupancy ceilings of the two instantiations (96 registers per thread: 5 blocks
-# of 128 or 2 of 256 threads per SM)
-MAX_BLOCKS_PER_SM = {128: 5, 256: 2}
+# occupancy ceilings of the two plain instantiations (105 registers per thread:
+# 4 blocks of 128 or 2 of 256 threads per SM)
+MAX_BLOCKS_PER_SM = {128: 4, 256: 2}
 TUNABLE = ("block_threads", "blocks_per_sm", "sort_tracks")
 
 
