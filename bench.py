@@ -790,7 +790,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pbpb2m", choices=sorted(WORKLOADS))
     ap.add_argument("--n-tracks", type=int, default=None, help="override the workload's track count (testing)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20, help="timed end-to-end steps (the mean over them is reported)")
     ap.add_argument("--ref-tracks", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rans-steps", type=int, default=5, help="pbpb2m: timed rANS encode/decode calls per stream")
