@@ -962,6 +962,24 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         h2d_b, d2h_b = int(21 * nc + 8 * (nt + 1)), int(100 * nt + nc)
+        # the same frame without x: its clusters lie on the pad-row planes, and
+        # the library derives x from the rows on the device (17 B per cluster copied)
+        ref_state, ref_accept = hres["state"].clone(), hres["accept"].clone()
+        nox = F()
+        for k in names:
+            setattr(nox, k, None if k == "x" else getattr(host, k))
+        for _ in range(max(3, args.warmup)):
+            fx.fit(nox, hres)
+        nox_ms = []
+        for _ in range(args.e2e_steps):
+            ts = time.perf_counter()
+            fx.fit(nox, hres)
+            _ = float(hres["chi2"][0])
+            nox_ms.append(round(1e3 * (time.perf_counter() - ts), 3))
+        nox_s = reduce_max(dist, torch, sum(nox_ms) * 1e-3)
+        nox_same = bool(torch.equal(ref_state.view(torch.int32), hres["state"].view(torch.int32))  # bitwise (NaN too)
+                        and torch.equal(ref_accept, hres["accept"]))
+        del ref_state, ref_accept
         link = link_rates()
         e2e = {"value": nc_all * args.e2e_steps / dt, "unit": "clusters/s",
                "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
@@ -971,6 +989,11 @@ def main():
                "link": dict(link, floor_ms=1e3 * h2d_b / (link["h2d_gbs"] * 1e9),
                             note="pinned copies of 1 GiB timed on this box; floor = the frame's host-to-device "
                                  "bytes at that rate")}
+        e2e["without_x"] = {
+            "value": nc_all * args.e2e_steps / nox_s, "unit": "clusters/s", "median_ms": float(np.median(nox_ms)),
+            "step_ms": nox_ms, "h2d_bytes_per_step": int(17 * nc + 8 * (nt + 1)), "d2h_bytes_per_step": d2h_b,
+            "what": "the same frame passed without x (its clusters lie on the pad-row planes: x derived on the device "
+                    "from the rows)", "results_identical_to_e2e": nox_same}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(frame, workload=args.workload, iterations=args.fit_iterations)

@@ -122,7 +122,11 @@ typedef struct tpcfit_config {
 typedef struct tpcfit_frame {
   int64_t n_tracks, n_clusters;
   const int64_t *track_offsets; /* n_tracks+1 */
-  const float *x, *y, *z, *sy2, *sz2; /* n_clusters each */
+  /* n_clusters each.  In a host frame (tpcfit_fit, tpcfit_submit) x may be
+   * NULL: the clusters then lie on their pad-row planes, x = the row table's
+   * float(row_x0 + row * row_pitch), derived on the device from `row` (4 B per
+   * cluster less to copy); device frames must carry x. */
+  const float *x, *y, *z, *sy2, *sz2;
   const uint8_t *row;             /* n_clusters */
   const uint8_t *sector;          /* n_tracks, may be NULL (informational only) */
   int32_t mem;                    /* TPCFIT_MEM_HOST or TPCFIT_MEM_DEVICE */

@@ -229,16 +229,24 @@ def _check_dtypes(obj, names):
 
 
 def _frame_struct(frame) -> tuple:
+    """The C frame of `frame`; a host frame may have x = None (clusters on
+    their pad-row planes: the library derives x from the rows)."""
     names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
-    arrs = [getattr(frame, k) for k in names]
-    _check_dtypes(frame, names)
+    present = tuple(k for k in names if getattr(frame, k, None) is not None)
+    if set(names) - set(present) - {"x"}:
+        raise ValueError(f"frame lacks {sorted(set(names) - set(present) - {'x'})}")
+    arrs = [getattr(frame, k) for k in present]
+    _check_dtypes(frame, present)
     mem = _mem_of(arrs)
-    nt = int(arrs[0].shape[0]) - 1
-    nc = int(arrs[1].shape[0])
-    for k, a in zip(names[1:], arrs[1:]):
-        if int(a.shape[0]) != nc:
-            raise ValueError(f"{k} has {a.shape[0]} entries, x has {nc}")
-    f = _Frame(nt, nc, _ptr(arrs[0]), *[_ptr(a) for a in arrs[1:]], 0, mem)
+    if "x" not in present and mem != MEM_HOST:
+        raise ValueError("x may be None only in a host frame")
+    nt = int(frame.offsets.shape[0]) - 1
+    nc = int(frame.y.shape[0])
+    for k in present[1:]:
+        if int(getattr(frame, k).shape[0]) != nc:
+            raise ValueError(f"{k} has {getattr(frame, k).shape[0]} entries, y has {nc}")
+    ptr = {k: _ptr(getattr(frame, k)) for k in present}
+    f = _Frame(nt, nc, ptr["offsets"], ptr.get("x"), ptr["y"], ptr["z"], ptr["sy2"], ptr["sz2"], ptr["row"], 0, mem)
     return f, mem, nt, nc
 
 

@@ -496,8 +496,10 @@ static int check_frame_shape(const tpcfit_frame *f, const tpcfit_result *r) {
   if (f->n_tracks < 0 || f->n_clusters < 0) return fail(TPCFIT_E_INVAL, "negative size");
   if (f->n_tracks > (int64_t)INT32_MAX - 64) return fail(TPCFIT_E_INVAL, "n_tracks above 2^31-64");
   if (!f->track_offsets) return fail(TPCFIT_E_INVAL, "track_offsets is NULL");
-  if (f->n_clusters > 0 && (!f->x || !f->y || !f->z || !f->sy2 || !f->sz2 || !f->row))
+  if (f->n_clusters > 0 && (!f->y || !f->z || !f->sy2 || !f->sz2 || !f->row))
     return fail(TPCFIT_E_INVAL, "cluster array is NULL");
+  if (f->n_clusters > 0 && !f->x && f->mem != TPCFIT_MEM_HOST)
+    return fail(TPCFIT_E_INVAL, "x may be NULL only in a host frame (clusters on their pad-row planes)");
   if (f->n_tracks > 0 && (!r->state || !r->cov || !r->x_ref || !r->chi2 || !r->ndf || !r->status))
     return fail(TPCFIT_E_INVAL, "result array is NULL");
   if (f->n_clusters > 0 && !r->accept) return fail(TPCFIT_E_INVAL, "accept is NULL");
@@ -655,6 +657,22 @@ static int validate_host_offsets(const tpcfit_frame *f) {
   return TPCFIT_OK;
 }
 
+// x of clusters on their pad-row planes: x[i] = row_x[row[i]] (host frames
+// whose x is NULL; the row table has kMaxRows entries, so every row byte
+// indexes it).
+__global__ void k_x_from_rows(const uint8_t *__restrict__ row, int64_t n, const float *__restrict__ row_x,
+                              float *__restrict__ x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = row_x[row[i]];
+}
+
+cudaError_t tpcfit::launch_x_from_rows(const uint8_t *row, int64_t n, const float *row_x, float *x, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_x_from_rows<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(row, n, row_x, x);
+  return cudaGetLastError();
+}
+
 // Chunk schedule of a host frame (host path and serving).  A call costs the
 // host->device copy of every input byte (the link is the bound) plus what no
 // copy overlaps: the fit and the result copy of the last chunk, and a setup
@@ -737,7 +755,7 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     CU(cudaStreamWaitEvent(h->h2d, S.free_ev, 0));
     CU(cudaMemcpyAsync(S.off, off + t0, (size_t)(cnt + 1) * 8, cudaMemcpyHostToDevice, h->h2d));
     tpcfit_frame cf = *f;
-    CU(copy_clusters_in(*f, c0, c1, ClusterArrays{S.x, S.y, S.z, S.sy2, S.sz2, S.row}, cf, h->h2d));
+    CU(copy_clusters_in(*f, c0, c1, ClusterArrays{S.x, S.y, S.z, S.sy2, S.sz2, S.row}, h->d_rowx, cf, h->h2d));
     CU(cudaEventRecord(h->ev_in[ci & 1], h->h2d));
     // fit
     CU(cudaStreamWaitEvent(h->stream, h->ev_in[ci & 1], 0));

@@ -62,9 +62,15 @@ struct ClusterArrays {
   uint8_t *row;
 };
 
+cudaError_t launch_x_from_rows(const uint8_t *row, int64_t n, const float *row_x, float *x, cudaStream_t st);
+
+// A NULL x in the host frame: the clusters lie on their pad-row planes, and
+// the staged x is filled on the device from the staged rows and the row table
+// `row_x` (device memory), over the row array's staged range.
 inline cudaError_t copy_clusters_in(const tpcfit_frame &f, int64_t c0, int64_t c1, const ClusterArrays &stage,
-                                    tpcfit_frame &view, cudaStream_t st) {
+                                    const float *row_x, tpcfit_frame &view, cudaStream_t st) {
   cudaError_t err = cudaSuccess;
+  int64_t row_a0 = c0, row_n = 0;
   auto one = [&](const void *src, void *dst, size_t elem) -> const void * {
     const uintptr_t base = reinterpret_cast<uintptr_t>(src);
     int64_t a0 = c0 - (int64_t)(((base + (uintptr_t)c0 * elem) & 255u) / elem);
@@ -74,14 +80,23 @@ inline cudaError_t copy_clusters_in(const tpcfit_frame &f, int64_t c0, int64_t c
     if (c1 > c0 && err == cudaSuccess)
       err = cudaMemcpyAsync(dst, static_cast<const char *>(src) + a0 * (int64_t)elem, (size_t)(a1 - a0) * elem,
                             cudaMemcpyHostToDevice, st);
+    if (elem == 1) {
+      row_a0 = a0;
+      row_n = a1 - a0;
+    }
     return static_cast<const char *>(dst) + (c0 - a0) * (int64_t)elem;
   };
-  view.x = static_cast<const float *>(one(f.x, stage.x, 4));
+  view.row = static_cast<const uint8_t *>(one(f.row, stage.row, 1));
+  if (f.x) {
+    view.x = static_cast<const float *>(one(f.x, stage.x, 4));
+  } else {
+    if (c1 > c0 && err == cudaSuccess) err = launch_x_from_rows(stage.row, row_n, row_x, stage.x, st);
+    view.x = stage.x + (c0 - row_a0);
+  }
   view.y = static_cast<const float *>(one(f.y, stage.y, 4));
   view.z = static_cast<const float *>(one(f.z, stage.z, 4));
   view.sy2 = static_cast<const float *>(one(f.sy2, stage.sy2, 4));
   view.sz2 = static_cast<const float *>(one(f.sz2, stage.sz2, 4));
-  view.row = static_cast<const uint8_t *>(one(f.row, stage.row, 1));
   view.n_clusters = c1 - c0;
   return err;
 }

@@ -46,6 +46,7 @@ ServeState *&handle_serve(tpcfit_handle *h);
 int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *dev_frame, tpcfit_result *dev_res, void *scratch_base,
                        int64_t off_base, cudaStream_t st, const int32_t **err_dev);
 int64_t handle_chunk_clusters(tpcfit_handle *h);
+const float *handle_rowx(tpcfit_handle *h);
 size_t serve_scratch_bytes(int64_t n_tracks);
 void serve_stop(tpcfit_handle *h);
 
@@ -188,7 +189,7 @@ static bool launch(ServeState *S, const Part &P, int si) {
   if (ok) {
     const ClusterArrays stage{const_cast<float *>(df.x), const_cast<float *>(df.y), const_cast<float *>(df.z),
                               const_cast<float *>(df.sy2), const_cast<float *>(df.sz2), const_cast<uint8_t *>(df.row)};
-    if (cudaError_t e = copy_clusters_in(F, c0, c1, stage, df, L.stream); e != cudaSuccess) {
+    if (cudaError_t e = copy_clusters_in(F, c0, c1, stage, handle_rowx(S->h), df, L.stream); e != cudaSuccess) {
       ok = false;
       if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: input copy failed: %s\n",
                                    (unsigned long long)P.ticket, cudaGetErrorString(e));

@@ -134,6 +134,35 @@ def test_host_chunk_schedules_and_unaligned_host_arrays_agree_with_device(T):
             assert np.array_equal(dev[k], got[k], equal_nan=k in ("state", "cov")), (chunk, shift, k)
 
 
+def test_host_frame_without_x_equals_with_x(T):
+    """Clusters on their pad-row planes: a host frame without x (the library
+    derives it on the device from the rows) gives the results of the same
+    frame with x bit for bit, in chunks of several sizes and through serving;
+    a device frame must carry x."""
+    f = tpcgen.generate("detector50k", n_tracks=7_003, seed=44)
+    assert np.array_equal(tpcgen.row_x_table()[f.row], f.x)  # the generator writes the row planes
+    dev = fit_gpu(T, f)
+    nox = types.SimpleNamespace(offsets=f.offsets, x=None, **{k: np.ascontiguousarray(getattr(f, k))
+                                                               for k in ("y", "z", "sy2", "sz2", "row")})
+    for chunk in (1_000, 100_000, 10_000_000):
+        with T.Fitter(host_chunk_clusters=chunk) as fx:
+            got = fx.fit(nox)
+        for k in dev:
+            assert np.array_equal(dev[k], got[k], equal_nan=k in ("state", "cov")), (chunk, k)
+    pinned = types.SimpleNamespace(offsets=torch.from_numpy(f.offsets).pin_memory(), x=None,
+                                   **{k: torch.from_numpy(np.ascontiguousarray(getattr(f, k))).pin_memory()
+                                      for k in ("y", "z", "sy2", "sz2", "row")})
+    with T.Fitter(host_chunk_clusters=200_000, max_slots=3) as fx:
+        r = T.alloc_result(f.n_tracks, f.n_clusters, pinned=True)
+        assert fx.wait(fx.submit(pinned, r), 60)[0] == T.DONE
+        for k in dev:
+            assert np.array_equal(dev[k], r[k].numpy(), equal_nan=k in ("state", "cov")), k
+        g = dev_frame(f)
+        g.x = None
+        with pytest.raises(ValueError):
+            fx.fit(g)
+
+
 def test_host_frame_of_empty_tracks(T):
     off = np.zeros(6, dtype=np.int64)
     empty = np.zeros(0, dtype=np.float32)
