@@ -755,10 +755,13 @@ static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
     CU(cudaStreamWaitEvent(h->h2d, S.free_ev, 0));
     CU(cudaMemcpyAsync(S.off, off + t0, (size_t)(cnt + 1) * 8, cudaMemcpyHostToDevice, h->h2d));
     tpcfit_frame cf = *f;
-    CU(copy_clusters_in(*f, c0, c1, ClusterArrays{S.x, S.y, S.z, S.sy2, S.sz2, S.row}, h->d_rowx, cf, h->h2d));
+    XFill xfill;  // a frame without x: its x is filled on the fit stream, after the copies
+    CU(copy_clusters_in(*f, c0, c1, ClusterArrays{S.x, S.y, S.z, S.sy2, S.sz2, S.row}, h->d_rowx, cf, h->h2d,
+                        &xfill));
     CU(cudaEventRecord(h->ev_in[ci & 1], h->h2d));
     // fit
     CU(cudaStreamWaitEvent(h->stream, h->ev_in[ci & 1], 0));
+    if (xfill.n > 0) CU(launch_x_from_rows(xfill.row, xfill.n, h->d_rowx, xfill.x, h->stream));
     CU(cudaMemsetAsync(h->scratch.hist, 0, 2 * kKeyBins * sizeof(uint32_t) + 16, h->stream));
     cf.n_tracks = cnt;
     cf.track_offsets = S.off;

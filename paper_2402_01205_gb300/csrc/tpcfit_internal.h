@@ -66,9 +66,19 @@ cudaError_t launch_x_from_rows(const uint8_t *row, int64_t n, const float *row_x
 
 // A NULL x in the host frame: the clusters lie on their pad-row planes, and
 // the staged x is filled on the device from the staged rows and the row table
-// `row_x` (device memory), over the row array's staged range.
+// `row_x` (device memory), over the row array's staged range: on `st` right
+// after the copies, or, when `fill` is given, by the caller (who launches
+// launch_x_from_rows(fill->row, fill->n, row_x, fill->x, ...) on a stream that
+// waits for the copies, so that the copy stream stays busy with copies).
+struct XFill {
+  const uint8_t *row = nullptr;
+  int64_t n = 0;
+  float *x = nullptr;
+};
+
 inline cudaError_t copy_clusters_in(const tpcfit_frame &f, int64_t c0, int64_t c1, const ClusterArrays &stage,
-                                    const float *row_x, tpcfit_frame &view, cudaStream_t st) {
+                                    const float *row_x, tpcfit_frame &view, cudaStream_t st,
+                                    XFill *fill = nullptr) {
   cudaError_t err = cudaSuccess;
   int64_t row_a0 = c0, row_n = 0;
   auto one = [&](const void *src, void *dst, size_t elem) -> const void * {
@@ -90,7 +100,14 @@ inline cudaError_t copy_clusters_in(const tpcfit_frame &f, int64_t c0, int64_t c
   if (f.x) {
     view.x = static_cast<const float *>(one(f.x, stage.x, 4));
   } else {
-    if (c1 > c0 && err == cudaSuccess) err = launch_x_from_rows(stage.row, row_n, row_x, stage.x, st);
+    const int64_t n_fill = c1 > c0 ? row_n : 0;
+    if (fill) {
+      fill->row = stage.row;
+      fill->n = n_fill;
+      fill->x = stage.x;
+    } else if (n_fill > 0 && err == cudaSuccess) {
+      err = launch_x_from_rows(stage.row, n_fill, row_x, stage.x, st);
+    }
     view.x = stage.x + (c0 - row_a0);
   }
   view.y = static_cast<const float *>(one(f.y, stage.y, 4));
