@@ -90,3 +90,24 @@ def test_binding_declares_the_signature_of_every_entry_point():
     assert not missing, missing
     for n in ("tpcfit_rans_bound", "tpcfit_now"):
         assert getattr(lib, n).restype in (ctypes.c_int64, ctypes.c_double), n
+
+
+def test_binding_marshals_host_frames_without_x():
+    """A host frame may leave x out (clusters on their pad-row planes): the C
+    frame then carries a NULL x and the cluster count of y; other arrays are
+    required."""
+    import types
+
+    import numpy as np
+
+    import paper_2402_01205_gb300 as T
+    import tpcgen
+    f = tpcgen.generate("sector1k", n_tracks=12)
+    arrays = {k: np.ascontiguousarray(getattr(f, k)) for k in ("y", "z", "sy2", "sz2", "row")}
+    c, mem, nt, nc = T._frame_struct(types.SimpleNamespace(offsets=f.offsets, x=None, **arrays))
+    assert c.x is None and c.y and mem == T.MEM_HOST and (nt, nc) == (f.n_tracks, f.n_clusters)
+    full, *_ = T._frame_struct(f)
+    assert full.x and full.n_clusters == c.n_clusters
+    bad = dict(arrays, z=None)
+    with pytest.raises(ValueError):
+        T._frame_struct(types.SimpleNamespace(offsets=f.offsets, x=None, **bad))
