@@ -44,7 +44,7 @@ class _Cfg(ctypes.Structure):
                 ("mass", ctypes.c_double), ("snp_max", ctypes.c_double), ("seed_cov", ctypes.c_double * 5),
                 ("min_clusters", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("row_x", ctypes.c_void_p),
                 ("restart_scale", ctypes.c_double), ("xrho", ctypes.c_double), ("eloss_za", ctypes.c_double),
-                ("eloss_i", ctypes.c_double), ("n_iterations", ctypes.c_int32)]
+                ("eloss_i", ctypes.c_double), ("n_iterations", ctypes.c_int32), ("reseed_pct", ctypes.c_int32)]
 
 
 class _Res(ctypes.Structure):
@@ -107,6 +107,7 @@ class FitConfig:
     eloss_za: float = 0.49555  # its Z/A (neon)
     eloss_i_ev: float = 137.0  # its mean excitation energy, eV (neon)
     iterations: int = 0        # refits seeded from the previous fit's state
+    reseed_pct: int = 50       # inward re-seed below this outward acceptance (percent of the clusters)
 
     def row_x(self) -> np.ndarray:
         return (self.row_x0 + np.arange(self.n_rows, dtype=np.float64) * self.row_pitch).astype(np.float32)
@@ -115,7 +116,7 @@ class FitConfig:
 def _cfg_struct(cfg: "FitConfig", rx: np.ndarray) -> _Cfg:
     return _Cfg(cfg.bz, cfg.chi2_max, cfg.xx0, cfg.mass, cfg.snp_max, (ctypes.c_double * 5)(*cfg.seed_cov),
                 cfg.min_clusters, cfg.n_rows, rx.ctypes.data, cfg.restart_scale, cfg.xrho, cfg.eloss_za,
-                cfg.eloss_i_ev * 1e-9, cfg.iterations)
+                cfg.eloss_i_ev * 1e-9, cfg.iterations, cfg.reseed_pct)
 
 
 def dedx(p: float, mass: float, za: float = 0.49555, i_ev: float = 137.0) -> float:

@@ -21,9 +21,9 @@
  *   |sinphi| limit 0.999; MS after the (possible) update at every crossed row;
  *   inward pass restarts from the outward state with a diagonal covariance:
  *   the outward variances times restart_scale (100), capped at the seed's;
- *   if the outward pass accepted fewer than 90 % of the clusters (a pass that
- *   lost the track for a stretch, typically after an outlier at the first
- *   cluster) it restarts instead from a fresh three-point seed at the
+ *   if the outward pass accepted fewer than reseed_pct % (50 %) of the
+ *   clusters (a pass that lost the track, typically after an outlier at the
+ *   first cluster) it restarts instead from a fresh three-point seed at the
  *   outermost cluster;
  *   outputs at the innermost cluster;
  *   optional mean energy loss in a thin layer at every crossed row, crossed
@@ -64,6 +64,7 @@ typedef struct {
   double eloss_za;      /* Z/A of its material */
   double eloss_i;       /* mean excitation energy of its material, GeV */
   int32_t n_iterations; /* refits seeded from the previous fit's state (0: none) */
+  int32_t reseed_pct;   /* the inward pass re-seeds when the outward pass accepted < reseed_pct % of the clusters */
 } orc_config;
 
 typedef struct {
@@ -376,8 +377,8 @@ refit:;
     if ((status = orc_eloss(p, C, c, 1.0)) != ST_OK) goto emit;
   }
 
-  /* ---- inward pass restart.  If the outward pass accepted at least 90 % of
-     the clusters: from the outward state with a diagonal covariance, the
+  /* ---- inward pass restart.  If the outward pass accepted at least
+     reseed_pct % of the clusters: from the outward state with a diagonal covariance, the
      outward variances inflated by restart_scale and capped at the seed's.
      Otherwise the outward pass is not trusted: a fresh three-point seed at the
      outermost cluster (circle through clusters n-1, n/2, 0, taken for motion
@@ -385,7 +386,7 @@ refit:;
   {
     int nacc_out = 0;
     for (int64_t k = a; k < e; ++k) nacc_out += o->accept[k] & 1;
-    if (10 * (int64_t)nacc_out < 9 * n) {
+    if (100 * (int64_t)nacc_out < (int64_t)c->reseed_pct * n) {
       double A[3] = {x[e - 1], y[e - 1], z[e - 1]}, B[3] = {x[a + n / 2], y[a + n / 2], z[a + n / 2]},
              D[3] = {x[a], y[a], z[a]};
       orc_seed(A, B, D, c->bz, p);
