@@ -27,7 +27,8 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 KB = 0.299792458e-2
-STATUS = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT", 6: "STOPPED"}
+STATUS = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT", 6: "STOPPED",
+          7: "DERAILED"}
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +45,8 @@ class _Cfg(ctypes.Structure):
                 ("mass", ctypes.c_double), ("snp_max", ctypes.c_double), ("seed_cov", ctypes.c_double * 5),
                 ("min_clusters", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("row_x", ctypes.c_void_p),
                 ("restart_scale", ctypes.c_double), ("xrho", ctypes.c_double), ("eloss_za", ctypes.c_double),
-                ("eloss_i", ctypes.c_double), ("n_iterations", ctypes.c_int32), ("reseed_pct", ctypes.c_int32)]
+                ("eloss_i", ctypes.c_double), ("n_iterations", ctypes.c_int32), ("reseed_pct", ctypes.c_int32),
+                ("derail_pct", ctypes.c_int32)]
 
 
 class _Res(ctypes.Structure):
@@ -85,6 +87,9 @@ def _load():
             [ctypes.c_void_p] * 6 + [ctypes.c_int64] + [ctypes.c_void_p] * 10 + [ctypes.c_int]
         lib.oracle_follow.restype = ctypes.c_int
         lib.oracle_residuals.restype = ctypes.c_int
+        lib.oracle_smooth.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 7 + \
+            [ctypes.POINTER(_Res), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_smooth.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -108,6 +113,7 @@ class FitConfig:
     eloss_i_ev: float = 137.0  # its mean excitation energy, eV (neon)
     iterations: int = 0        # refits seeded from the previous fit's state
     reseed_pct: int = 50       # inward re-seed below this outward acceptance (percent of the clusters)
+    derail_pct: int = 80       # a fit whose inward pass accepted fewer (percent) is DERAILED
 
     def row_x(self) -> np.ndarray:
         return (self.row_x0 + np.arange(self.n_rows, dtype=np.float64) * self.row_pitch).astype(np.float32)
@@ -116,7 +122,7 @@ class FitConfig:
 def _cfg_struct(cfg: "FitConfig", rx: np.ndarray) -> _Cfg:
     return _Cfg(cfg.bz, cfg.chi2_max, cfg.xx0, cfg.mass, cfg.snp_max, (ctypes.c_double * 5)(*cfg.seed_cov),
                 cfg.min_clusters, cfg.n_rows, rx.ctypes.data, cfg.restart_scale, cfg.xrho, cfg.eloss_za,
-                cfg.eloss_i_ev * 1e-9, cfg.iterations, cfg.reseed_pct)
+                cfg.eloss_i_ev * 1e-9, cfg.iterations, cfg.reseed_pct, cfg.derail_pct)
 
 
 def dedx(p: float, mass: float, za: float = 0.49555, i_ev: float = 137.0) -> float:
@@ -163,6 +169,36 @@ def fit(frame, cfg: Optional[FitConfig] = None, threads: Optional[int] = None, d
     if rc != 0:
         raise ValueError("oracle_fit: malformed track offsets")
     out["threads"] = min(th, max(nt, 1))
+    return out
+
+
+def smooth(frame, cfg: Optional[FitConfig] = None, threads: Optional[int] = None) -> dict:
+    """Two-filter smoother (oracle_smooth): the track outputs of the smoothed
+    fit (state and covariance at the innermost cluster, chi2, ndf, status,
+    accept flags), the smoothed state ``sm_state`` (nc, 5) and packed
+    covariance ``sm_cov`` (nc, 15) at every cluster, and the backward
+    filter's starting state ``state_out_t`` and covariance diagonal
+    ``restart_t`` per track."""
+    lib = _load()
+    cfg = cfg or FitConfig()
+    if cfg.xrho > 0 or cfg.iterations > 0:
+        raise ValueError("the smoother takes neither energy loss nor seed iteration")
+    off = np.ascontiguousarray(frame.offsets, dtype=np.int64)
+    arrs = [np.ascontiguousarray(getattr(frame, k), dtype=np.float32) for k in ("x", "y", "z", "sy2", "sz2")]
+    row = np.ascontiguousarray(frame.row, dtype=np.uint8)
+    nt, nc = off.shape[0] - 1, int(arrs[0].shape[0])
+    rx = cfg.row_x()
+    c = _cfg_struct(cfg, rx)
+    out = dict(state=np.zeros((nt, 5)), cov=np.zeros((nt, 15)), x_ref=np.zeros(nt), chi2=np.zeros(nt),
+               ndf=np.zeros(nt, np.int32), status=np.zeros(nt, np.int32), accept=np.zeros(nc, np.uint8),
+               sm_state=np.zeros((nc, 5)), sm_cov=np.zeros((nc, 15)),
+               state_out_t=np.full((nt, 5), np.nan), restart_t=np.full((nt, 5), np.nan))
+    r = _Res(*[out[k].ctypes.data if k in out else None for k, _ in _Res._fields_])
+    th = threads if threads else (os.cpu_count() or 1)
+    rc = lib.oracle_smooth(ctypes.byref(c), nt, nc, off.ctypes.data, *[a.ctypes.data for a in arrs],
+                           row.ctypes.data, ctypes.byref(r), out["sm_state"].ctypes.data, out["sm_cov"].ctypes.data, th)
+    if rc != 0:
+        raise ValueError("oracle_smooth: malformed track offsets")
     return out
 
 

@@ -33,8 +33,10 @@
  *   (seed covariance), restart and inward pass, n_iterations times.
  * Status rule: clusters are validated when the outward pass reaches them, so the
  * first offending cluster decides; NaN never trips a numerical limit (it flows
- * to that cluster), and a completed fit with a non-finite state or covariance
- * is marked NONFINITE.
+ * to that cluster), a completed fit with a non-finite state or covariance
+ * is marked NONFINITE, and a completed fit whose last inward pass accepted
+ * fewer than derail_pct % (80 %) of the track's clusters is marked DERAILED
+ * (the pass lost the track for a stretch: its estimate does not describe it).
  */
 #include <math.h>
 #include <pthread.h>
@@ -47,7 +49,7 @@
 #define ORC_K 0.307075e-3     /* 4 pi N_A r_e^2 m_e c^2, GeV cm^2 / mol */
 
 enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5,
-       ST_STOPPED = 6 };
+       ST_STOPPED = 6, ST_DERAILED = 7 };
 
 typedef struct {
   double bz;            /* Tesla */
@@ -65,6 +67,7 @@ typedef struct {
   double eloss_i;       /* mean excitation energy of its material, GeV */
   int32_t n_iterations; /* refits seeded from the previous fit's state (0: none) */
   int32_t reseed_pct;   /* the inward pass re-seeds when the outward pass accepted < reseed_pct % of the clusters */
+  int32_t derail_pct;   /* a completed fit whose inward pass accepted < derail_pct % of the clusters is DERAILED */
 } orc_config;
 
 typedef struct {
@@ -454,6 +457,8 @@ refit:;
     }
     goto refit;
   }
+  /* a completed fit that kept fewer than derail_pct % of its clusters lost the track */
+  if (status == ST_OK && 100 * (int64_t)nacc_in < (int64_t)c->derail_pct * n) status = ST_DERAILED;
 
 emit:
   for (int i = 0; i < 5; ++i) o->state[5 * t + i] = p[i];
@@ -501,6 +506,240 @@ int oracle_fit(const orc_config *c, int64_t nt, int64_t nc, const int64_t *off, 
     jobs[i] = jj;
     if (nth == 1) worker(&jobs[i]);
     else pthread_create(&th[i], NULL, worker, &jobs[i]);
+  }
+  if (nth > 1) for (int i = 0; i < nth; ++i) pthread_join(th[i], NULL);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Two-filter smoother (fit variant): the state at every cluster from all of
+ * the track's clusters.  Model (the fit's outward reading): the particle
+ * moves outward; at each crossed row it is first measured (if the row has a
+ * cluster) and then scattered, x_{r+1} = f(x_r + w_r).
+ *  - forward filter: the outward pass of fit_track; at cluster k it records
+ *    the prediction (p-, C-) before the update (clusters 0..k-1 and the seed
+ *    prior at cluster 0);
+ *  - backward filter: starts at the outermost cluster as the inward pass of
+ *    fit_track does (the forward state with the diagonal restart covariance,
+ *    or the fresh reversed seed when the forward filter accepted fewer than
+ *    reseed_pct % of the clusters), so its prior carries about 1 % of the
+ *    forward information (the restart inflates the variances 100-fold);
+ *    moving
+ *    inward it propagates to each crossed row, adds that row's scattering
+ *    (the kink lies outward of the row's measurement in the model above),
+ *    and then updates with the row's cluster: after the update at cluster k
+ *    it holds (p+, C+) from clusters k..n-1 and its own seed prior;
+ *  - the two estimates of the state arriving at cluster k are independent
+ *    and combine as p = p- + K (p+ - p-), C = C- - K C-, K = C- (C- + C+)^-1.
+ * Track outputs: the smoothed state and covariance at cluster 0; chi2, ndf
+ * and accept bit 1 from the backward filter; bit 0 from the forward filter;
+ * status as for fit_track (DERAILED when the backward filter kept fewer than
+ * derail_pct % of the clusters).  No energy loss, no seed iteration.
+ * ------------------------------------------------------------------------- */
+static int solve5(const double A[25], const double B[25], double X[25]) {
+  /* X = A^-1 B for a symmetric positive definite A, by Gauss-Jordan
+     elimination with partial pivoting; returns 0, or -1 if A is singular */
+  double M[5][10];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) { M[i][j] = A[i * 5 + j]; M[i][5 + j] = B[i * 5 + j]; }
+  for (int c = 0; c < 5; ++c) {
+    int pr = c;
+    for (int i = c + 1; i < 5; ++i) if (fabs(M[i][c]) > fabs(M[pr][c])) pr = i;
+    if (!(fabs(M[pr][c]) > 0.0)) return -1;
+    if (pr != c) for (int j = 0; j < 10; ++j) { double t = M[c][j]; M[c][j] = M[pr][j]; M[pr][j] = t; }
+    double d = M[c][c];
+    for (int j = 0; j < 10; ++j) M[c][j] /= d;
+    for (int i = 0; i < 5; ++i) {
+      if (i == c) continue;
+      double f = M[i][c];
+      for (int j = 0; j < 10; ++j) M[i][j] -= f * M[c][j];
+    }
+  }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) X[i * 5 + j] = M[i][5 + j];
+  return 0;
+}
+
+static void smooth_track(const orc_config *c, int64_t t, const int64_t *off, const float *x, const float *y,
+                         const float *z, const float *sy2, const float *sz2, const uint8_t *row, const orc_result *o,
+                         double *sm_state, double *sm_cov) {
+  int64_t a = off[t], e = off[t + 1];
+  int64_t n = e - a;
+  double p[5] = {0, 0, 0, 0, 0}, C[25], F[25], pn[5];
+  int status = ST_OK;
+  double chi2_in = 0.0;
+  int nacc_in = 0;
+  double *fp = NULL, *fC = NULL; /* forward predictions at each cluster */
+  for (int64_t k = a; k < e; ++k) {
+    o->accept[k] = 0;
+    for (int i = 0; i < 5; ++i) sm_state[5 * k + i] = NAN;
+    for (int i = 0; i < 15; ++i) sm_cov[15 * k + i] = NAN;
+  }
+  seed_cov(c, C);
+  double xref = (n > 0) ? (double)x[a] : 0.0;
+  if (n < c->min_clusters || n < 3) { status = ST_TOO_FEW; goto emit; }
+  {
+    double A[3] = {x[a], y[a], z[a]}, B[3] = {x[a + n / 2], y[a + n / 2], z[a + n / 2]},
+           D[3] = {x[e - 1], y[e - 1], z[e - 1]};
+    orc_seed(A, B, D, c->bz, p);
+  }
+  if (fabs(p[2]) >= c->snp_max) { status = ST_SNP_LIMIT; goto emit; }
+  fp = malloc((size_t)n * 5 * sizeof(double));
+  fC = malloc((size_t)n * 25 * sizeof(double));
+  if (!fp || !fC) { status = ST_NONFINITE; goto emit; }
+  /* ---- forward filter (the outward pass), predictions recorded ---- */
+  double xcur = x[a];
+  for (int64_t k = a; k < e; ++k) {
+    if (row[k] >= c->n_rows || (k > a && row[k] <= row[k - 1])) { status = ST_BAD_INPUT; goto emit; }
+    if (!finite_cluster(x, y, z, sy2, sz2, k)) { status = ST_NONFINITE; goto emit; }
+    if (!(sy2[k] > 0.0f) || !(sz2[k] > 0.0f)) { status = ST_BAD_INPUT; goto emit; }
+    if (k > a) {
+      for (int r = row[k - 1] + 1; r < row[k]; ++r) {
+        double xr = c->row_x[r];
+        if ((status = orc_propagate(p, xcur, xr, c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+        memcpy(p, pn, sizeof(pn));
+        cov_transport(C, F);
+        xcur = xr;
+        orc_ms_noise(p, C, c->xx0, c->mass);
+      }
+    }
+    if ((status = orc_propagate(p, xcur, x[k], c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+    memcpy(p, pn, sizeof(pn));
+    cov_transport(C, F);
+    xcur = x[k];
+    memcpy(fp + 5 * (k - a), p, 5 * sizeof(double));
+    memcpy(fC + 25 * (k - a), C, 25 * sizeof(double));
+    double chi2;
+    int acc;
+    if ((status = orc_update(p, C, y[k], z[k], sy2[k], sz2[k], c->chi2_max, &chi2, &acc)) != ST_OK) goto emit;
+    if (acc) o->accept[k] |= 1;
+    orc_ms_noise(p, C, c->xx0, c->mass);
+  }
+  /* ---- backward filter: from the forward state (or a fresh reversed seed) with the seed covariance ---- */
+  {
+    int nacc_out = 0;
+    for (int64_t k = a; k < e; ++k) nacc_out += o->accept[k] & 1;
+    if (100 * (int64_t)nacc_out < (int64_t)c->reseed_pct * n) {
+      double A[3] = {x[e - 1], y[e - 1], z[e - 1]}, B[3] = {x[a + n / 2], y[a + n / 2], z[a + n / 2]},
+             D[3] = {x[a], y[a], z[a]};
+      orc_seed(A, B, D, c->bz, p);
+      p[2] = -p[2];
+      p[3] = -p[3];
+      p[4] = -p[4];
+      seed_cov(c, C);
+    } else {
+      double d[5];
+      for (int i = 0; i < 5; ++i) {
+        d[i] = c->restart_scale * C[i * 5 + i];
+        if (!(d[i] <= c->seed_cov[i])) d[i] = c->seed_cov[i];
+      }
+      for (int i = 0; i < 25; ++i) C[i] = 0.0;
+      for (int i = 0; i < 5; ++i) C[i * 5 + i] = d[i];
+    }
+    if (o->state_out_t) for (int i = 0; i < 5; ++i) o->state_out_t[5 * t + i] = p[i];
+    if (o->restart_t) for (int i = 0; i < 5; ++i) o->restart_t[5 * t + i] = C[i * 5 + i];
+  }
+  for (int64_t k = e - 1; k >= a; --k) {
+    if (k < e - 1) {
+      /* rows crossed without a cluster between cluster k+1 and cluster k */
+      for (int r = row[k + 1] - 1; r > row[k]; --r) {
+        double xr = c->row_x[r];
+        if ((status = orc_propagate(p, xcur, xr, c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+        memcpy(p, pn, sizeof(pn));
+        cov_transport(C, F);
+        xcur = xr;
+        orc_ms_noise(p, C, c->xx0, c->mass);
+      }
+      if ((status = orc_propagate(p, xcur, x[k], c->bz, c->snp_max, pn, F)) != ST_OK) goto emit;
+      memcpy(p, pn, sizeof(pn));
+      cov_transport(C, F);
+      xcur = x[k];
+      orc_ms_noise(p, C, c->xx0, c->mass); /* the kink of row k lies outward of its measurement */
+    }
+    double chi2;
+    int acc;
+    if ((status = orc_update(p, C, y[k], z[k], sy2[k], sz2[k], c->chi2_max, &chi2, &acc)) != ST_OK) goto emit;
+    if (acc) { o->accept[k] |= 2; chi2_in += chi2; ++nacc_in; }
+    /* combine with the forward prediction at cluster k */
+    {
+      const double *pm = fp + 5 * (k - a), *Cm = fC + 25 * (k - a);
+      double S[25], K[25], Kt[25], ps[5], Cs[25];
+      for (int i = 0; i < 25; ++i) S[i] = Cm[i] + C[i];
+      /* K^T = S^-1 Cm (S and Cm symmetric), so K = Cm S^-1 */
+      if (solve5(S, Cm, Kt) != 0) { status = ST_NOT_PD; goto emit; }
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) K[i * 5 + j] = Kt[j * 5 + i];
+      for (int i = 0; i < 5; ++i) {
+        double v = pm[i];
+        for (int j = 0; j < 5; ++j) v += K[i * 5 + j] * (p[j] - pm[j]);
+        ps[i] = v;
+      }
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+          double v = Cm[i * 5 + j];
+          for (int m = 0; m < 5; ++m) v -= K[i * 5 + m] * Cm[m * 5 + j];
+          Cs[i * 5 + j] = v;
+        }
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < i; ++j) { double m = 0.5 * (Cs[i * 5 + j] + Cs[j * 5 + i]); Cs[i * 5 + j] = Cs[j * 5 + i] = m; }
+      for (int i = 0; i < 5; ++i) sm_state[5 * k + i] = ps[i];
+      pack_cov(Cs, sm_cov + 15 * k);
+      if (k == a) { memcpy(p, ps, sizeof(ps)); memcpy(C, Cs, sizeof(Cs)); } /* the track output */
+    }
+  }
+  for (int i = 0; i < 25; ++i)
+    if (!isfinite(C[i]) || (i < 5 && !isfinite(p[i]))) { status = ST_NONFINITE; break; }
+  if (status == ST_OK && 100 * (int64_t)nacc_in < (int64_t)c->derail_pct * n) status = ST_DERAILED;
+emit:
+  free(fp);
+  free(fC);
+  for (int i = 0; i < 5; ++i) o->state[5 * t + i] = p[i];
+  pack_cov(C, o->cov + 15 * t);
+  o->x_ref[t] = xref;
+  o->chi2[t] = chi2_in;
+  o->ndf[t] = 2 * nacc_in - 5;
+  o->status[t] = status;
+}
+
+typedef struct {
+  const orc_config *c;
+  int64_t nt;
+  const int64_t *off;
+  const float *x, *y, *z, *sy2, *sz2;
+  const uint8_t *row;
+  const orc_result *o;
+  double *sm_state, *sm_cov;
+  int tid, nth;
+} smooth_job;
+
+static void *smooth_worker(void *arg) {
+  smooth_job *j = (smooth_job *)arg;
+  for (int64_t t = j->tid; t < j->nt; t += j->nth)
+    smooth_track(j->c, t, j->off, j->x, j->y, j->z, j->sy2, j->sz2, j->row, j->o, j->sm_state, j->sm_cov);
+  return NULL;
+}
+
+/* Frame-level entry of the smoother: track outputs in *o (accept flags
+ * included), smoothed state (nc*5) and covariance (nc*15, packed) at every
+ * cluster (NaN where the fit did not complete).  Returns 0, or -1 on
+ * malformed offsets. */
+int oracle_smooth(const orc_config *c, int64_t nt, int64_t nc, const int64_t *off, const float *x, const float *y,
+                  const float *z, const float *sy2, const float *sz2, const uint8_t *row, const orc_result *o,
+                  double *sm_state, double *sm_cov, int n_threads) {
+  if (nt < 0 || nc < 0 || !off) return -1;
+  if (off[0] != 0 || off[nt] != nc) return -1;
+  for (int64_t t = 0; t < nt; ++t)
+    if (off[t + 1] < off[t]) return -1;
+  int nth = n_threads > 0 ? n_threads : 1;
+  if (nth > 512) nth = 512;
+  if ((int64_t)nth > nt) nth = nt > 0 ? (int)nt : 1;
+  pthread_t th[512];
+  smooth_job jobs[512];
+  for (int i = 0; i < nth; ++i) {
+    smooth_job jj = {c, nt, off, x, y, z, sy2, sz2, row, o, sm_state, sm_cov, i, nth};
+    jobs[i] = jj;
+    if (nth == 1) smooth_worker(&jobs[i]);
+    else pthread_create(&th[i], NULL, smooth_worker, &jobs[i]);
   }
   if (nth > 1) for (int i = 0; i < nth; ++i) pthread_join(th[i], NULL);
   return 0;
