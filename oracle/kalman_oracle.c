@@ -530,7 +530,11 @@ int oracle_fit(const orc_config *c, int64_t nt, int64_t nc, const int64_t *off, 
  *    and then updates with the row's cluster: after the update at cluster k
  *    it holds (p+, C+) from clusters k..n-1 and its own seed prior;
  *  - the two estimates of the state arriving at cluster k are independent
- *    and combine as p = p- + K (p+ - p-), C = C- - K C-, K = C- (C- + C+)^-1.
+ *    and combine as p = p- + K (p+ - p-), C = C- - K C-, K = C- (C- + C+)^-1;
+ *    when the forward filter lost the track (it accepted fewer than
+ *    reseed_pct % of the clusters, so that the backward filter re-seeds) its
+ *    predictions carry no valid information and the smoothed state is the
+ *    backward filter's.
  * Track outputs: the smoothed state and covariance at cluster 0; chi2, ndf
  * and accept bit 1 from the backward filter; bit 0 from the forward filter;
  * status as for fit_track (DERAILED when the backward filter kept fewer than
@@ -616,10 +620,12 @@ static void smooth_track(const orc_config *c, int64_t t, const int64_t *off, con
     orc_ms_noise(p, C, c->xx0, c->mass);
   }
   /* ---- backward filter: from the forward state (or a fresh reversed seed) with the seed covariance ---- */
+  int fw_valid = 1;
   {
     int nacc_out = 0;
     for (int64_t k = a; k < e; ++k) nacc_out += o->accept[k] & 1;
     if (100 * (int64_t)nacc_out < (int64_t)c->reseed_pct * n) {
+      fw_valid = 0;
       double A[3] = {x[e - 1], y[e - 1], z[e - 1]}, B[3] = {x[a + n / 2], y[a + n / 2], z[a + n / 2]},
              D[3] = {x[a], y[a], z[a]};
       orc_seed(A, B, D, c->bz, p);
@@ -661,7 +667,10 @@ static void smooth_track(const orc_config *c, int64_t t, const int64_t *off, con
     if ((status = orc_update(p, C, y[k], z[k], sy2[k], sz2[k], c->chi2_max, &chi2, &acc)) != ST_OK) goto emit;
     if (acc) { o->accept[k] |= 2; chi2_in += chi2; ++nacc_in; }
     /* combine with the forward prediction at cluster k */
-    {
+    if (!fw_valid) {
+      for (int i = 0; i < 5; ++i) sm_state[5 * k + i] = p[i];
+      pack_cov(C, sm_cov + 15 * k);
+    } else {
       const double *pm = fp + 5 * (k - a), *Cm = fC + 25 * (k - a);
       double S[25], K[25], Kt[25], ps[5], Cs[25];
       for (int i = 0; i < 25; ++i) S[i] = Cm[i] + C[i];

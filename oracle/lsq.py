@@ -74,3 +74,45 @@ def fit_inward(x, y, z, sy2, sz2, p_out, P0, bz: float, p_start=None, iters: int
             break
     _, A = jac(p)
     return p, np.linalg.inv(A.T @ A)
+
+
+def fit_two_priors(x, y, z, sy2, sz2, s_first, P_first, s_last, P_last, bz: float, p_start=None, iters: int = 50,
+                   k_ref: int = 0):
+    """Gauss-Newton minimum of
+      sum_i r_i^T V_i^-1 r_i + (p(x_0) - s_first)^T P_first^-1 (p(x_0) - s_first)
+                             + (p(x_last) - s_last)^T P_last^-1 (p(x_last) - s_last)
+    over the state at x[k_ref] (the objective of a two-filter smoother whose
+    forward filter starts from (s_first, P_first) at the innermost cluster
+    and whose backward filter starts from (s_last, P_last) at the outermost
+    one; both priors diagonal); returns (p_ref, cov_ref) at x[k_ref]."""
+    x = np.asarray(x, float)
+    Lf = np.diag(1.0 / np.sqrt(np.diag(P_first)))
+    Ll = np.diag(1.0 / np.sqrt(np.diag(P_last)))
+    wy, wz = 1.0 / np.sqrt(np.asarray(sy2, float)), 1.0 / np.sqrt(np.asarray(sz2, float))
+    s_first, s_last = np.asarray(s_first, float), np.asarray(s_last, float)
+
+    def resid(p):
+        pred = np.array([transport(p, x[k_ref], X, bz) for X in x])
+        r_meas = np.concatenate([(np.asarray(y) - pred[:, 0]) * wy, (np.asarray(z) - pred[:, 1]) * wz])
+        return np.concatenate([r_meas, Lf @ (pred[0] - s_first), Ll @ (pred[-1] - s_last)])
+
+    steps = np.array([1e-4, 1e-4, 1e-7, 1e-7, 1e-5])
+
+    def jac(p):
+        r0 = resid(p)
+        A = np.empty((r0.shape[0], 5))
+        for j in range(5):
+            dp = np.zeros(5)
+            dp[j] = steps[j]
+            A[:, j] = (resid(p + dp) - resid(p - dp)) / (2 * steps[j])
+        return r0, A
+
+    p = np.array(p_start if p_start is not None else s_first, float)
+    for _ in range(iters):
+        r0, A = jac(p)
+        step = -np.linalg.solve(A.T @ A, A.T @ r0)
+        p = p + step
+        if np.all(np.abs(step) <= 1e-14 * (1 + np.abs(p))):
+            break
+    _, A = jac(p)
+    return p, np.linalg.inv(A.T @ A)

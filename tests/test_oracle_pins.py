@@ -773,3 +773,28 @@ def test_smoother_on_noise_free_helices_and_its_track_outputs():
     assert np.array_equal(r["state"], r["sm_state"][a]) and np.array_equal(r["cov"], r["sm_cov"][a])
     nacc = np.add.reduceat((r["accept"] >> 1) & 1, a).astype(np.int64)
     assert np.array_equal(r["ndf"], 2 * nacc - 5) and r["chi2"].max() < 0.05
+
+
+def test_smoother_ignores_a_forward_filter_that_lost_the_track():
+    """An outlier at the innermost cluster makes the forward (outward) filter
+    lose most tracks.  Its predictions then carry no valid information: the
+    smoothed state is the backward filter's, and against the generator's truth
+    the smoothed states keep unit pulls at every cluster (combining the lost
+    filter's predictions instead gives pulls of 6-8 sigma)."""
+    f = tpcgen.generate("detector50k", n_tracks=5000, truth=True, seed=29, p_outlier=0.0)
+    rng = np.random.default_rng(7)
+    first = f.offsets[:-1]
+    y, z = f.y.copy(), f.z.copy()
+    y[first] += rng.choice([-1, 1], f.n_tracks) * rng.uniform(1.5, 2.0, f.n_tracks)
+    z[first] += rng.choice([-1, 1], f.n_tracks) * rng.uniform(1.5, 2.0, f.n_tracks)
+    g = tpcgen.Frame(f.offsets, f.x, y, z, f.sy2, f.sz2, f.row, f.sector, f.truth)
+    r = oracle.smooth(g, _cfg())
+    n = np.diff(g.offsets)
+    lost = (r["status"] == 0) & (np.add.reduceat(r["accept"] & 1, first) < 0.5 * n)
+    assert lost.mean() > 0.9
+    sel = np.repeat(lost, n)
+    sel[first] = False  # the displaced clusters themselves
+    C = oracle.unpack_cov(r["sm_cov"][sel])
+    pull = (r["sm_state"][sel] - f.truth[sel]) / np.sqrt(np.diagonal(C, axis1=1, axis2=2))
+    assert np.all(np.abs(pull.mean(0)) < 0.05)
+    assert np.all(np.sqrt(np.mean(np.minimum(pull ** 2, 100), axis=0)) < 1.25)
