@@ -61,6 +61,9 @@ extern "C" {
 #define TPCFIT_TRACK_NONFINITE 4  /* non-finite cluster value, or non-finite fitted state */
 #define TPCFIT_TRACK_BAD_INPUT 5  /* rows not ascending, row >= n_rows, variance <= 0, bad offsets */
 #define TPCFIT_TRACK_STOPPED 6    /* energy loss: one row would change p^2 by more than 50 % */
+#define TPCFIT_TRACK_DERAILED 7   /* the fit completed, but its inward pass accepted fewer than 80 % of
+                                     the track's clusters: it lost the track for a stretch, and its state
+                                     and covariance (written as for OK) do not describe it */
 
 /* ticket states for tpcfit_poll */
 #define TPCFIT_PENDING 0
@@ -108,7 +111,12 @@ typedef struct tpcfit_config {
    * flags and ndf are the last pass's; a failing pass ends the fit with its
    * status.  Each iteration costs about one more fit. */
   int32_t fit_iterations;
-  int32_t reserved[1];
+  /* Inward re-seed: when the outward pass accepted fewer than reseed_pct %
+   * of a track's clusters, the inward pass starts from a fresh three-point
+   * seed at the outermost cluster (circle through the last, middle and first
+   * cluster, reversed) with seed_cov, instead of from the outward state with
+   * the inflated restart covariance.  0-100; the default is 50. */
+  int32_t reseed_pct;
   int64_t host_chunk_clusters; /* host frames: chunk scale C (16M clusters); chunks shrink from up to 4C at the
                                  start of the frame to C/4 at its end (two device staging buffers of the
                                  largest chunk); serving splits frames into parts of about C */
@@ -162,6 +170,22 @@ typedef struct tpcfit_result {
    * tpcfit_fit_async, batches and serving; not by tpcfit_fit_noalloc. */
   int16_t *res_y;           /* n_clusters */
   int16_t *res_z;           /* n_clusters */
+  /* optional: the two-filter smoother (a fit variant).  When both are set,
+   * the fit runs as a smoother: the outward pass is the forward filter; the
+   * backward filter starts as the inward pass does (restart from the outward
+   * state, or the reversed seed) but adds each row's scattering before the
+   * row's update (the kink follows the measurement in outward motion); at
+   * every cluster the two independent estimates of the state arriving there
+   * are combined.  smoothed_state[5k..5k+4] = (y, z, sinphi, tanlambda, q/pT)
+   * at cluster k's x, smoothed_cov[15k..15k+14] its packed covariance (NaN
+   * where the fit did not complete).  The track outputs above are then the
+   * smoothed state and covariance at x_ref (cluster 0), with chi2, ndf, the
+   * inward accept bit and the status of the backward filter.  Device frames
+   * and results of tpcfit_fit, tpcfit_fit_async and batches only (a host
+   * frame is TPCFIT_E_INVAL; serving ignores them); not with energy loss or
+   * seed iteration (TPCFIT_E_INVAL).  NULL = the plain fit. */
+  float *smoothed_state;    /* n_clusters*5 */
+  float *smoothed_cov;      /* n_clusters*15 */
 } tpcfit_result;
 
 /* Kernel timings of the last completed fit on a handle (CUDA events on the

@@ -19,8 +19,10 @@ extern "C" {
 
 /* Largest frame tpcfit_fit_noalloc accepts.  The scratch for this many tracks
  * (about 1.6 MB: seeds, sort permutation and histogram, work counter, error
- * word, pad-row table) is a static device array that every GPU which loads the
- * library holds until the process exits. */
+ * word, pad-row table) is a static device array.  A device holds it from the
+ * moment the library's device code is loaded there until the process exits;
+ * with the CUDA runtime's lazy module loading (the default) that is the first
+ * call on that device. */
 #define TPCFIT_NOALLOC_MAX_TRACKS 65536
 
 /* Fit one DEVICE frame into DEVICE results, like tpcfit_fit, without creating
@@ -32,6 +34,21 @@ extern "C" {
  *
  * Set-up: the first call on each device looks up the device address of the
  * static scratch array; make that first call before any stream capture.
+ * That first call is also where the CUDA driver, loading the library's
+ * device code on the device, places the static array (and the kernels): a
+ * driver-side allocation of about 1.6 MB plus code, which can fail if another
+ * allocator has already taken all of the device memory (the kernels, too,
+ * are loaded on their first launch).  A caller that must not allocate at
+ * all in its steady state makes one call on each device during its set-up,
+ * before that state begins, with a small frame and the configuration (and
+ * residual outputs) it will use; later calls allocate nothing.
+ *
+ * Device: the call makes cfg->device current while it runs and gives the
+ * calling thread its previous current device back before it returns.
+ *
+ * Residual codes: when res->res_y or res->res_z is set, they are written as
+ * by tpcfit_fit (steps cfg->res_step_y_cm, cfg->res_step_z_cm), by one more
+ * kernel that needs no scratch.
  *
  * Sharing: all calls on a device share the one scratch array, which keeps the
  * last call's contents; every call clears what must start at zero.  Calls that
@@ -41,8 +58,9 @@ extern "C" {
  * Returns TPCFIT_OK, TPCFIT_E_INVAL (NULL pointers, host memory, a frame with
  * more than TPCFIT_NOALLOC_MAX_TRACKS tracks, parameters out of range, or
  * malformed offsets), TPCFIT_E_NODEV (device cannot be selected) or
- * TPCFIT_E_CUDA (a launch, copy or wait failed).  Per-track results and
- * statuses are as for tpcfit_fit. */
+ * TPCFIT_E_CUDA (a launch, copy or wait failed), with the detail in
+ * tpcfit_last_error_message().  Per-track results and statuses are as for
+ * tpcfit_fit. */
 int tpcfit_fit_noalloc(const tpcfit_config *cfg, const tpcfit_frame *frame, tpcfit_result *res, void *stream);
 
 #ifdef __cplusplus

@@ -30,7 +30,8 @@ __all__ = ["TpcfitError", "Config", "default_config", "create", "destroy", "fit"
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_NOTFOUND, E_NODEV = 0, -1, -2, -3, -4, -5, -6, -7
 MEM_HOST, MEM_DEVICE = 0, 1
 PENDING, DONE, FAILED = 0, 1, 2
-STATUS_NAMES = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT", 6: "STOPPED"}
+STATUS_NAMES = {0: "OK", 1: "TOO_FEW", 2: "SNP_LIMIT", 3: "NOT_PD", 4: "NONFINITE", 5: "BAD_INPUT", 6: "STOPPED",
+                7: "DERAILED"}
 
 
 class TpcfitError(RuntimeError):
@@ -48,7 +49,7 @@ class Config(ctypes.Structure):
         ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32), ("block_threads", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32), ("sort_tracks", ctypes.c_int32), ("res_step_y_cm", ctypes.c_float),
         ("res_step_z_cm", ctypes.c_float), ("xrho_per_row", ctypes.c_float), ("eloss_z_over_a", ctypes.c_float),
-        ("eloss_i_ev", ctypes.c_float), ("fit_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+        ("eloss_i_ev", ctypes.c_float), ("fit_iterations", ctypes.c_int32), ("reseed_pct", ctypes.c_int32),
         ("host_chunk_clusters", ctypes.c_int64),
     ]
 
@@ -65,7 +66,7 @@ class _Result(ctypes.Structure):
                 ("chi2", ctypes.c_void_p), ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p),
                 ("accept", ctypes.c_void_p), ("mem", ctypes.c_int32), ("chi2_out_cluster", ctypes.c_void_p),
                 ("chi2_in_cluster", ctypes.c_void_p), ("restart_state", ctypes.c_void_p), ("res_y", ctypes.c_void_p),
-                ("res_z", ctypes.c_void_p)]
+                ("res_z", ctypes.c_void_p), ("smoothed_state", ctypes.c_void_p), ("smoothed_cov", ctypes.c_void_p)]
 
 
 class _Timing(ctypes.Structure):
@@ -250,10 +251,13 @@ def _frame_struct(frame) -> tuple:
     return f, mem, nt, nc
 
 
-def alloc_result(n_tracks: int, n_clusters: int, device=None, pinned: bool = False, residuals: bool = False) -> dict:
+def alloc_result(n_tracks: int, n_clusters: int, device=None, pinned: bool = False, residuals: bool = False,
+                 smoothed: bool = False) -> dict:
     """Result buffers: torch tensors on ``device`` (CUDA) or numpy arrays on the
     host (pinned torch tensors with ``pinned``).  ``residuals`` adds the int16
-    track-model compression residual codes ``res_y``, ``res_z``."""
+    track-model compression residual codes ``res_y``, ``res_z``; ``smoothed``
+    the two-filter smoother's per-cluster ``smoothed_state`` (n_clusters, 5)
+    and ``smoothed_cov`` (n_clusters, 15), which select the smoother."""
     if device is not None or pinned:
         import torch
         kw = dict(device=device) if device is not None else dict(pin_memory=True)
@@ -264,6 +268,8 @@ def alloc_result(n_tracks: int, n_clusters: int, device=None, pinned: bool = Fal
                    accept=mk((n_clusters,), torch.uint8))
         if residuals:
             out.update(res_y=mk((n_clusters,), torch.int16), res_z=mk((n_clusters,), torch.int16))
+        if smoothed:
+            out.update(smoothed_state=mk((n_clusters, 5), torch.float32), smoothed_cov=mk((n_clusters, 15), torch.float32))
         return out
     out = dict(state=np.empty((n_tracks, 5), np.float32), cov=np.empty((n_tracks, 15), np.float32),
                x_ref=np.empty(n_tracks, np.float32), chi2=np.empty(n_tracks, np.float64),
@@ -271,14 +277,37 @@ def alloc_result(n_tracks: int, n_clusters: int, device=None, pinned: bool = Fal
                accept=np.empty(n_clusters, np.uint8))
     if residuals:
         out.update(res_y=np.empty(n_clusters, np.int16), res_z=np.empty(n_clusters, np.int16))
+    if smoothed:
+        out.update(smoothed_state=np.empty((n_clusters, 5), np.float32),
+                   smoothed_cov=np.empty((n_clusters, 15), np.float32))
     return out
 
 
-def _result_struct(res: dict) -> tuple:
+# Elements per track (or per cluster) of each result array.
+_RES_TRACK = {"state": 5, "cov": 15, "x_ref": 1, "chi2": 1, "ndf": 1, "status": 1, "restart_state": 5}
+_RES_CLUSTER = {"accept": 1, "res_y": 1, "res_z": 1, "chi2_out_cluster": 1, "chi2_in_cluster": 1, "smoothed_state": 5,
+                "smoothed_cov": 15}
+
+
+def _numel(a) -> int:
+    return int(a.numel()) if _is_torch(a) else int(a.size)
+
+
+def _result_struct(res: dict, nt: int, nc: int) -> tuple:
+    """The C result of `res` for a frame of nt tracks and nc clusters: every
+    buffer must hold exactly its frame's number of elements (a result of
+    another frame would be written past its end)."""
     names = ("state", "cov", "x_ref", "chi2", "ndf", "status", "accept")
     arrs = [res[k] for k in names]
     mem = _mem_of(arrs)
-    extra = [_ptr(res.get(k)) for k in ("chi2_out_cluster", "chi2_in_cluster", "restart_state", "res_y", "res_z")]
+    for k, a in res.items():
+        if a is None or (k not in _RES_TRACK and k not in _RES_CLUSTER):
+            continue
+        want = _RES_TRACK[k] * nt if k in _RES_TRACK else _RES_CLUSTER[k] * nc
+        if _numel(a) != want:
+            raise ValueError(f"result {k} has {_numel(a)} elements, the frame needs {want}")
+    extra = [_ptr(res.get(k)) for k in ("chi2_out_cluster", "chi2_in_cluster", "restart_state", "res_y", "res_z",
+                                         "smoothed_state", "smoothed_cov")]
     for k in ("res_y", "res_z"):
         if res.get(k) is not None:
             dt = str(res[k].dtype).replace("torch.", "")
@@ -300,16 +329,16 @@ def destroy(handle: int) -> None:
 
 
 def fit(handle: int, frame, res: dict) -> dict:
-    f, _, _, _ = _frame_struct(frame)
-    r, _ = _result_struct(res)
+    f, _, nt, nc = _frame_struct(frame)
+    r, _ = _result_struct(res, nt, nc)
     _check(_load().tpcfit_fit(handle, ctypes.byref(f), ctypes.byref(r)))
     return res
 
 
 def fit_async(handle: int, frame, res: dict, stream=None) -> dict:
     """Enqueue on a torch.cuda.Stream (or raw cudaStream_t int, or None)."""
-    f, _, _, _ = _frame_struct(frame)
-    r, _ = _result_struct(res)
+    f, _, nt, nc = _frame_struct(frame)
+    r, _ = _result_struct(res, nt, nc)
     s = getattr(stream, "cuda_stream", stream)
     _check(_load().tpcfit_fit_async(handle, ctypes.byref(f), ctypes.byref(r), s))
     return res
@@ -320,8 +349,8 @@ def sync(handle: int, timeout_s: float = -1.0) -> None:
 
 
 def submit(handle: int, frame, res: dict) -> int:
-    f, _, _, _ = _frame_struct(frame)
-    r, _ = _result_struct(res)
+    f, _, nt, nc = _frame_struct(frame)
+    r, _ = _result_struct(res, nt, nc)
     t = ctypes.c_uint64()
     _check(_load().tpcfit_submit(handle, ctypes.byref(f), ctypes.byref(r), ctypes.byref(t)))
     return t.value
@@ -368,18 +397,16 @@ def fit_noalloc(frame, res: dict, config: Optional[Config] = None, stream=None) 
     fn = lib.tpcfit_fit_noalloc
     fn.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_Frame), ctypes.POINTER(_Result), ctypes.c_void_p]
     fn.restype = ctypes.c_int
-    f, _, _, _ = _frame_struct(frame)
-    r, _ = _result_struct(res)
+    f, _, nt, nc = _frame_struct(frame)
+    r, _ = _result_struct(res, nt, nc)
     s = getattr(stream, "cuda_stream", stream)
-    rc = fn(ctypes.byref(config) if config is not None else None, ctypes.byref(f), ctypes.byref(r), s)
-    if rc < 0:
-        raise TpcfitError(rc, strerror(rc))
+    _check(fn(ctypes.byref(config) if config is not None else None, ctypes.byref(f), ctypes.byref(r), s))
     return res
 
 
 def batch_create(handle: int, frame, res: dict) -> int:
-    f, _, _, _ = _frame_struct(frame)
-    r, _ = _result_struct(res)
+    f, _, nt, nc = _frame_struct(frame)
+    r, _ = _result_struct(res, nt, nc)
     b = ctypes.c_void_p()
     _check(_load().tpcfit_batch_create(handle, ctypes.byref(f), ctypes.byref(r), ctypes.byref(b)))
     return b.value
@@ -520,8 +547,8 @@ class EventViews:
             reb[t0 + e:t1 + e + 1] = off[t0:t1 + 1] - off[t0]
         self.rebased = torch.from_numpy(reb).to(frame.x.device)
         self.frame, self.res = frame, res
-        fs, _, _, _ = _frame_struct(frame)
-        rs, _ = _result_struct(res)
+        fs, _, nt, nc = _frame_struct(frame)
+        rs, _ = _result_struct(res, nt, nc)
         if fs.mem != MEM_DEVICE or rs.mem != MEM_DEVICE:
             raise ValueError("EventViews takes a device frame and device results")
         self.frames, self.results = [], []

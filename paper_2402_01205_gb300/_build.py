@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtpcfit.so")
-SOURCES = ["fit_kernels.cu", "track_kernels.cu", "tpcfit_api.cu", "tpcfit_serve.cu", "probe.cu", "tpcfit_noalloc.cu", "tpcfit_rans.cu", "tpcfit_follow.cu"]
+SOURCES = ["fit_kernels.cu", "smooth_kernels.cu", "track_kernels.cu", "tpcfit_api.cu", "tpcfit_serve.cu", "probe.cu",
+           "tpcfit_noalloc.cu", "tpcfit_rans.cu", "tpcfit_follow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -12,7 +12,7 @@
 namespace tpcfit {
 
 enum { ST_OK = 0, ST_TOO_FEW = 1, ST_SNP_LIMIT = 2, ST_NOT_PD = 3, ST_NONFINITE = 4, ST_BAD_INPUT = 5,
-       ST_STOPPED = 6 };
+       ST_STOPPED = 6, ST_DERAILED = 7 };
 
 // ---------------------------------------------------------------------------
 // binary32 -> binary64 widening with integer operations (IEEE 754: the
@@ -55,6 +55,17 @@ __device__ __forceinline__ bool le0_finite64(double x) {
   split64(x, hi, lo);
   return (int32_t)hi < 0 || (hi | lo) == 0u;
 }
+// binary64 -> binary32 narrowing with integer operations, rounding toward
+// zero (relative error below 2^-23), for a positive x whose magnitude lies in
+// the normal binary32 range; `other` for any x outside it (zero, negative,
+// subnormal or too large as a binary32, non-finite).
+__device__ __forceinline__ float narrow_pos_or(double x, float other) {
+  uint32_t hi, lo;
+  split64(x, hi, lo);
+  // biased binary64 exponent in [897, 1150] <=> binary32 exponent in [1, 254]; sign bit clear
+  const bool in_range = hi - (897u << 20) < (254u << 20);
+  return in_range ? __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29)) : other;
+}
 // x <= g for a finite x and a positive finite g given as (ghi, glo).
 __device__ __forceinline__ bool le_finite64(double x, uint32_t ghi, uint32_t glo) {
   uint32_t hi, lo;
@@ -89,11 +100,27 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 //  - variances of tanlambda and q/pT: compensated sums c[9] + c9l, c[14] + c14l
 //    (transport leaves them unchanged; after a restart they shrink by orders of
 //    magnitude through many small decrements)
+//  - variance of sinphi and its covariance with q/pT: compensated sums
+//    c[5] + c5l, c[12] + c12l.  On a curved track sinphi and q/pT become
+//    almost fully correlated, and binary32 storage of these two entries
+//    alone (every other step in FP64) moves the fitted covariance of a track
+//    that was lost and found again in the outward pass by up to 1.2e-4 of
+//    its diagonal; with them compensated, by less than 2e-5.
 struct Trk {
   float dy, dz, sp, spl, tl0, dtl, w0, dw;
   float ya, za;
   float c[15];  // covariance, packed lower triangle
-  float c9l, c14l;
+  float c9l, c14l, c5l, c12l, c3l;
+  __device__ __forceinline__ void clear_comp() { c9l = c14l = c5l = c12l = c3l = 0.f; }
+  // the covariance with the compensation terms added in (binary32)
+  __device__ __forceinline__ void fold_comp() {
+    c[3] += c3l;
+    c[5] += c5l;
+    c[9] += c9l;
+    c[12] += c12l;
+    c[14] += c14l;
+    clear_comp();
+  }
   __device__ __forceinline__ float tl() const { return tl0 + dtl; }
   __device__ __forceinline__ float w() const { return w0 + dw; }
   __device__ __forceinline__ float snp() const { return sp + spl; }
@@ -168,19 +195,21 @@ __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_m
   const float n32 = fmaf(Jsw, c[13], c[8]);
   const float n40 = fmaf(Jys, c[12], fmaf(Jyw, c[14], c[10]));
   const float n41 = fmaf(Jzs, c[12], fmaf(Jzt, c[13], fmaf(Jzw, c[14], c[11])));
-  const float n42 = fmaf(Jsw, c[14], c[12]);
+  // compensated C_sw' = C_sw + Jsw C_ww and C_ss' = C_ss + Jsw (2 C_sw + Jsw C_ww)
+  const float dsw = Jsw * (c[14] + T.c14l);
+  const float dss = Jsw * fmaf(2.0f, c[12], dsw);
   c[0] = fmaf(Jys, FC02, fmaf(Jyw, FC04, FC00));
   c[1] = fmaf(Jys, FC12, fmaf(Jyw, FC14, FC10));
   c[2] = fmaf(Jzs, FC12, fmaf(Jzt, FC13, fmaf(Jzw, FC14, FC11)));
-  c[3] = fmaf(Jys, FC22, fmaf(Jyw, FC24, FC20));
+  two_sum(c[3], fmaf(Jys, FC22, fmaf(Jyw, FC24, fmaf(Jsw, c[10], T.c3l))), c[3], T.c3l);
   c[4] = fmaf(Jzs, FC22, fmaf(Jzt, FC23, fmaf(Jzw, FC24, FC21)));
-  c[5] = fmaf(Jsw, FC24, FC22);
+  fast_two_sum(c[5], dss + T.c5l, c[5], T.c5l);  // a variance plus a smaller change
   c[6] = n30;
   c[7] = n31;
   c[8] = n32;
   c[10] = n40;
   c[11] = n41;
-  c[12] = n42;
+  two_sum(c[12], dsw + T.c12l, c[12], T.c12l);
   // c[9], c[13], c[14] unchanged
   return true;
 }
@@ -196,7 +225,7 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   const float eps = xx0 * (tt * rsqrtf(tt * cs2));  // xx0 sqrt(tt / cs2)
   const float lg = fmaf(0.038f, __logf(eps * ib2), 1.0f);
   const float th2 = (0.0136f * 0.0136f) * pinv2 * ib2 * eps * lg * lg;
-  T.c[5] = fmaf(th2, cs2 * tt, T.c[5]);
+  fast_two_sum(T.c[5], fmaf(th2, cs2 * tt, T.c5l), T.c[5], T.c5l);
   fast_two_sum(T.c[9], fmaf(th2, tt * tt, T.c9l), T.c[9], T.c9l);
   fast_two_sum(T.c[14], fmaf(th2, w * w * t * t, T.c14l), T.c[14], T.c14l);
   T.c[13] = fmaf(th2, tt * w * t, T.c[13]);
@@ -253,6 +282,7 @@ __device__ __forceinline__ bool eloss(Trk &T, float xrho, float kza, float a_coe
   T.c[10] *= k;
   T.c[11] *= k;
   T.c[12] *= k;
+  T.c12l *= k;
   T.c[13] *= k;
   T.c[14] *= k2;
   T.c14l *= k2;
@@ -289,13 +319,16 @@ __device__ __forceinline__ void quad_form2(float S00, float S10, float S11, floa
 }
 
 // Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: the
-// determinant of S, and where the chi2 value is needed (inward pass,
-// diagnostics) the reciprocal of det (Newton step from an FP32 seed), chi2 =
-// q / det and (by the caller) the chi2 sum; otherwise the gate is decided in
-// FP64 as q - chi2_max det <= 0.  The quadratic form q = r^T adj(S) r enters
-// as the exact binary64 sum of its two binary32 parts.  Non-finite innovation
-// matrices or residuals give chi2 = NaN and a rejected cluster, as in FP64.
-// Returns the status (OK / NOT_PD).
+// inversion of S -- its determinant, and where the chi2 value is needed
+// (inward pass, diagnostics) the reciprocal of det (Newton step from an FP32
+// seed), chi2 = q / det and (by the caller) the chi2 sum; otherwise the gate
+// is decided in FP64 as q - chi2_max det <= 0.  The quadratic form
+// q = r^T adj(S) r enters as the exact binary64 sum of its two binary32
+// parts.  The gain's S^-1 = adj(S) / det takes its 1/det from the FP64
+// determinant (narrowed to binary32 by integer operations), so that the
+// cancellation in det of a strongly correlated S does not reach the gain.
+// Non-finite innovation matrices or residuals give chi2 = NaN and a rejected
+// cluster, as in FP64.  Returns the status (OK / NOT_PD).
 __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, double gate, uint32_t gate_hi,
                                       uint32_t gate_lo, bool want_chi2, bool &acc, double &chi2) {
   float *c = T.c;
@@ -305,11 +338,11 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
   float qh, ql;
   quad_form2(S00, S10, S11, r0, r1, qh, ql);
   const bool fin = fabsf((S00 + S11) + (S10 + qh)) < INFINITY;
-  const float det32 = fmaf(S00, S11, -(S10 * S10));
-  const float i32 = __fdividef(1.0f, det32);  // FP32 seed of 1/det, and the gain's 1/det
   // ---- FP64 island ----
   const double s00 = widen_pos(S00), s11 = widen_pos(S11), s10 = widen(S10);
-  const double det = fma(s00, s11, -(s10 * s10));
+  const double det = fma(s00, s11, -(s10 * s10));  // exact products of the binary32 S: rounded once
+  // the gain's 1/det and the FP32 seed of the FP64 reciprocal, from the FP64 determinant
+  const float i32 = __fdividef(1.0f, narrow_pos_or(det, fmaf(S00, S11, -(S10 * S10))));
   const double qhd = widen(qh), qld = widen(ql);
   if (want_chi2) {
     const double y0 = widen_pos(i32);
@@ -360,15 +393,16 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
       h0[j] = c[col0[j]];
       h1[j] = c[col1[j]];
     }
+    T.c3l = 0.f;  // C'(2,0) below is a fresh product
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       c[col0[i]] = K0[i] * vy;  // C'(i,0)
       if (i >= 1) c[col1[i]] = K1[i] * vz;  // C'(i,1)
     }
-    c[5] = fmaf(-K0[2], h0[2], fmaf(-K1[2], h1[2], c[5]));
+    fast_two_sum(c[5], T.c5l - fmaf(K0[2], h0[2], K1[2] * h1[2]), c[5], T.c5l);
     c[8] = fmaf(-K0[3], h0[2], fmaf(-K1[3], h1[2], c[8]));
     fast_two_sum(c[9], T.c9l - fmaf(K0[3], h0[3], K1[3] * h1[3]), c[9], T.c9l);
-    c[12] = fmaf(-K0[4], h0[2], fmaf(-K1[4], h1[2], c[12]));
+    two_sum(c[12], T.c12l - fmaf(K0[4], h0[2], K1[4] * h1[2]), c[12], T.c12l);
     c[13] = fmaf(-K0[4], h0[3], fmaf(-K1[4], h1[3], c[13]));
     fast_two_sum(c[14], T.c14l - fmaf(K0[4], h0[4], K1[4] * h1[4]), c[14], T.c14l);
   } else {
@@ -377,6 +411,48 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
   }
   T.ya = yc;
   T.za = zc;
+  return ST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Seed: circle through three clusters (a, b, c) in the (x, y) plane; state at a.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float asin_over_u_f(float u) {
+  const float u2 = u * u;
+  if (fabsf(u) < 0.1f) return 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
+  return asinf(u) / u;
+}
+
+static __device__ __noinline__ void seed3(float xa, float ya, float za, float xb, float yb, float xc, float yc, float zc, float b,
+                      float p[5]) {
+  const float abx = xb - xa, aby = yb - ya, acx = xc - xa, acy = yc - ya, bcx = xc - xb, bcy = yc - yb;
+  const float cross = abx * acy - aby * acx;
+  const float lab = sqrtf(abx * abx + aby * aby), lac = sqrtf(acx * acx + acy * acy),
+              lbc = sqrtf(bcx * bcx + bcy * bcy);
+  const float kappa = 2.0f * cross / (lab * lac * lbc);
+  float u = 0.5f * kappa * lac;
+  u = fminf(1.0f, fmaxf(-1.0f, u));
+  const float phi = atan2f(acy, acx) - asinf(u);
+  const float s_ac = lac * asin_over_u_f(u);
+  p[0] = ya;
+  p[1] = za;
+  p[2] = sinf(phi);
+  p[3] = (zc - za) / s_ac;
+  p[4] = kappa / b;  // q/pT = -kappa/(kB Bz) = kappa / b
+}
+
+__device__ __forceinline__ bool finite5(float a, float b, float c, float d, float e) {
+  return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e);
+}
+
+// Validation of a cluster when the outward pass reaches it (before any
+// propagation towards it): row inside the geometry and above the previous
+// one, finite values, positive variances.
+__device__ __forceinline__ int check_cluster(int r, int rprev, int n_rows, float x, float y, float z, float vy,
+                                             float vz) {
+  if (r >= n_rows || r <= rprev) return ST_BAD_INPUT;
+  if (!finite5(x, y, z, vy, vz)) return ST_NONFINITE;
+  if (!(vy > 0.f) || !(vz > 0.f)) return ST_BAD_INPUT;
   return ST_OK;
 }
 

@@ -48,6 +48,9 @@ constexpr int kBitWords = kMaxRows / 32;  // outward accept bits of one track (<
 constexpr int kChunk = 4;                 // clusters per staged chunk (per lane)
 constexpr int kStageBufs = 3;             // chunk buffers per lane: a ring, chunk c in buffer c % 3
 constexpr int kStageArrays = 5;           // x, y, z, sy2, sz2
+// A completed fit whose (last) inward pass accepted fewer than this percentage
+// of the track's clusters lost the track for a stretch: status DERAILED.
+constexpr int kDerailPct = 80;
 // dynamic shared memory of k_fit: row table, outward accept bits, staged clusters
 constexpr size_t kSmemRowx = kMaxRows * sizeof(float);
 template <int BLOCK> __host__ __device__ constexpr size_t smem_bits() { return (size_t)(BLOCK / 32) * kBitWords * 32 * sizeof(uint32_t); }
@@ -66,33 +69,6 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool val
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-// ---------------------------------------------------------------------------
-// Seed: circle through three clusters (a, b, c) in the (x, y) plane; state at a.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float asin_over_u_f(float u) {
-  const float u2 = u * u;
-  if (fabsf(u) < 0.1f) return 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
-  return asinf(u) / u;
-}
-
-__device__ __noinline__ void seed3(float xa, float ya, float za, float xb, float yb, float xc, float yc, float zc, float b,
-                      float p[5]) {
-  const float abx = xb - xa, aby = yb - ya, acx = xc - xa, acy = yc - ya, bcx = xc - xb, bcy = yc - yb;
-  const float cross = abx * acy - aby * acx;
-  const float lab = sqrtf(abx * abx + aby * aby), lac = sqrtf(acx * acx + acy * acy),
-              lbc = sqrtf(bcx * bcx + bcy * bcy);
-  const float kappa = 2.0f * cross / (lab * lac * lbc);
-  float u = 0.5f * kappa * lac;
-  u = fminf(1.0f, fmaxf(-1.0f, u));
-  const float phi = atan2f(acy, acx) - asinf(u);
-  const float s_ac = lac * asin_over_u_f(u);
-  p[0] = ya;
-  p[1] = za;
-  p[2] = sinf(phi);
-  p[3] = (zc - za) / s_ac;
-  p[4] = kappa / b;  // q/pT = -kappa/(kB Bz) = kappa / b
-}
-
 // ---------------------------------------------------------------------------
 // k_prepare: per-track offset checks, status preset, seed, key histogram.
 // ---------------------------------------------------------------------------
@@ -177,24 +153,9 @@ __global__ void __launch_bounds__(256) k_sort_scatter(FitArgs A) {
   if (t < A.n_tracks) A.perm[s_base[key] + rank] = (int32_t)t;
 }
 
-__device__ __forceinline__ bool finite5(float a, float b, float c, float d, float e) {
-  return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e);
-}
-
 // ---------------------------------------------------------------------------
 // k_fit: persistent warps over the (sorted) track list.
 // ---------------------------------------------------------------------------
-// Validation of a cluster when the outward pass reaches it (before any
-// propagation towards it): row inside the geometry and above the previous
-// one, finite values, positive variances.
-__device__ __forceinline__ int check_cluster(int r, int rprev, int n_rows, float x, float y, float z, float vy,
-                                             float vz) {
-  if (r >= n_rows || r <= rprev) return ST_BAD_INPUT;
-  if (!finite5(x, y, z, vy, vz)) return ST_NONFINITE;
-  if (!(vy > 0.f) || !(vz > 0.f)) return ST_BAD_INPUT;
-  return ST_OK;
-}
-
 struct Clu {
   float x, y, z, vy, vz;
   int r;
@@ -291,8 +252,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   T.c[5] = A.seed_cov[2];
   T.c[9] = A.seed_cov[3];
   T.c[14] = A.seed_cov[4];
-  T.c9l = 0.f;
-  T.c14l = 0.f;
+  T.clear_comp();
   int st = st0;
   double chi2sum = 0.0;
   int nacc = 0;
@@ -380,8 +340,8 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         // ---------------- restart ----------------
         if (st == ST_OK) {
           // cand holds the outermost cluster n-1
-          if (10 * nacc_out < 9 * n) {
-            // the outward pass accepted fewer than 90 % of the clusters: re-seed
+          if (100 * nacc_out < A.reseed_pct * n) {
+            // the outward pass accepted fewer than reseed_pct % of the clusters: re-seed
             // at the outermost cluster (circle through clusters n-1, n/2, 0 for
             // motion towards cluster 0, reversed) with the seed covariance
             float p[5];
@@ -408,7 +368,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             // inward restart: diagonal, outward variances inflated, capped at the seed's
             const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
             const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
-            const float d2 = fminf(A.restart_scale * T.c[5], A.seed_cov[2]);
+            const float d2 = fminf(A.restart_scale * (T.c[5] + T.c5l), A.seed_cov[2]);
             const float d3 = fminf(A.restart_scale * (T.c[9] + T.c9l), A.seed_cov[3]);
             const float d4 = fminf(A.restart_scale * (T.c[14] + T.c14l), A.seed_cov[4]);
 #pragma unroll
@@ -419,8 +379,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             T.c[9] = d3;
             T.c[14] = d4;
           }
-          T.c9l = 0.f;
-          T.c14l = 0.f;
+          T.clear_comp();
           if (A.restart_state) {
             float *rs = A.restart_state + 5 * t;
             rs[0] = T.ya + T.dy;
@@ -490,8 +449,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         T.c[5] = A.seed_cov[2];
         T.c[9] = A.seed_cov[3];
         T.c[14] = A.seed_cov[4];
-        T.c9l = 0.f;
-        T.c14l = 0.f;
+        T.clear_comp();
 #pragma unroll
         for (int w = 0; w < kBitWords; ++w) bits[32 * w] = 0u;
         done = 0;
@@ -501,6 +459,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       }  // passes
       cp_async_wait_all();  // no copy may land in the column after this track
       if (st == ST_OK && !state_finite(T)) st = ST_NONFINITE;
+      if (st == ST_OK && 100 * nacc < kDerailPct * n) st = ST_DERAILED;  // the last inward pass lost the track
     }
     // accept bytes not written by the inward pass (failed or unfitted tracks): outward bits only
     for (int64_t k = a; k < e - done; ++k) {
@@ -520,8 +479,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   ps[3] = T.tl();
   ps[4] = T.w();
   float *pc = A.cov + 15 * t;
-  T.c[9] += T.c9l;
-  T.c[14] += T.c14l;
+  T.fold_comp();
 #pragma unroll
   for (int i = 0; i < 15; ++i) pc[i] = T.c[i];
   A.chi2[t] = chi2sum;

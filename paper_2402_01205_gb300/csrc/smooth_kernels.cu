@@ -1,0 +1,405 @@
+// Two-filter smoother of the track fit (a fit variant): the state and
+// covariance at every cluster of a track from all of its clusters.
+//
+// The paper's TPC chain stores clusters as residuals to their track (Sec. 5,
+// track-model compression) and names no smoothing method; the smoother here
+// is the textbook two-filter form (Fraser and Potter 1969; Fruhwirth 1987 for
+// track fitting), in the scattering model of the fit's outward pass: the
+// particle moves outward and, at each crossed pad row, is first measured (if
+// the row has a cluster) and then scattered.
+//
+//  1. forward filter = the fit's outward pass.  Before its update at cluster
+//     k the predicted state (p-, C-) (clusters 0..k-1 and the seed prior) is
+//     written into the caller's smoothed-output slots of cluster k;
+//  2. backward filter = the inward pass, started as the fit starts it (the
+//     outward state with the inflated diagonal restart covariance, or the
+//     reversed three-point seed), except that at each crossed row it adds the
+//     row's scattering before the row's update (the kink follows the
+//     measurement in outward motion);
+//  3. after its update at cluster k it holds (p+, C+) from clusters k..n-1
+//     and combines them with the stored prediction of the same state:
+//       S = C- + C+,  K = C- S^-1,  p = p- + K (p+ - p-),  C = K C+,
+//     and overwrites the slots of cluster k with the smoothed state.  When
+//     the forward filter lost the track (it accepted fewer than reseed_pct %
+//     of the clusters, so that the backward filter re-seeds) its predictions
+//     carry no valid information: the smoothed state is the backward
+//     filter's.
+//
+// The track outputs are the smoothed state and covariance at cluster 0; chi2,
+// ndf, the inward accept bit and the status come from the backward filter as
+// in the fit.
+//
+// Precision: the filters are the fit's (FP32 with the FP64 innovation island).
+// The 5x5 combination is FP32: S is scaled to unit diagonal (its correlation
+// matrix) before a Cholesky factorisation, and C = K C+ is formed as a
+// product, not as the difference C- - K C-, which cancels wherever one filter
+// knows far more than the other (near the ends of the track).
+//
+// One thread per track on the persistent grid of the fit (same sort, same
+// work counter); clusters are read directly from global memory (no staging
+// ring: a variant, not the benchmark path).
+
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdint.h>
+
+#include "fit_device.cuh"
+#include "tpcfit_internal.h"
+
+namespace tpcfit {
+
+namespace {
+
+constexpr int kSmoothBlock = 128;
+constexpr int kSmoothDerailPct = 80;  // as the fit: DERAILED below 80 % inward acceptance
+
+// absolute state of a track
+__device__ __forceinline__ void state_of(const Trk &T, float p[5]) {
+  p[0] = T.ya + T.dy;
+  p[1] = T.za + T.dz;
+  p[2] = T.snp();
+  p[3] = T.tl();
+  p[4] = T.w();
+}
+
+// packed covariance with the compensation terms added in
+__device__ __forceinline__ void cov_of(const Trk &T, float c[15]) {
+#pragma unroll
+  for (int i = 0; i < 15; ++i) c[i] = T.c[i];
+  c[3] += T.c3l;
+  c[5] += T.c5l;
+  c[9] += T.c9l;
+  c[12] += T.c12l;
+  c[14] += T.c14l;
+}
+
+__device__ __forceinline__ int pk(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+// Two-filter combination of the prediction (pm, cm) with the filtered state
+// (pp, cp) of the same plane (packed covariances).  Returns false when S is
+// not positive definite (the outputs are then unchanged).
+__device__ __forceinline__ bool combine(const float pm[5], const float cm[15], const float pp[5], const float cp[15],
+                                        float ps[5], float cs[15]) {
+  float S[15], d[5];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) S[i] = cm[i] + cp[i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float v = S[pk(i, i)];
+    if (!(v > 0.0f)) return false;
+    d[i] = rsqrtf(v);
+  }
+  // L L^T = D S D (unit diagonal), lower triangle packed in place
+  float L[15];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) L[pk(i, j)] = S[pk(i, j)] * d[i] * d[j];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    float s = L[pk(j, j)];
+#pragma unroll
+    for (int m = 0; m < j; ++m) s = fmaf(-L[pk(j, m)], L[pk(j, m)], s);
+    if (!(s > 0.0f)) return false;
+    const float r = rsqrtf(s);
+    L[pk(j, j)] = s * r;  // sqrt(s)
+#pragma unroll
+    for (int i = j + 1; i < 5; ++i) {
+      float t = L[pk(i, j)];
+#pragma unroll
+      for (int m = 0; m < j; ++m) t = fmaf(-L[pk(i, m)], L[pk(j, m)], t);
+      L[pk(i, j)] = t * r;
+    }
+  }
+  // X = S^-1 C- = D (L L^T)^-1 D C-, column by column; K = C- S^-1 = X^T
+  float X[5][5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    float v[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] = d[i] * cm[pk(i, c)];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {  // L y = v
+      float t = v[i];
+#pragma unroll
+      for (int m = 0; m < i; ++m) t = fmaf(-L[pk(i, m)], v[m], t);
+      v[i] = t / L[pk(i, i)];
+    }
+#pragma unroll
+    for (int i = 4; i >= 0; --i) {  // L^T x = y
+      float t = v[i];
+#pragma unroll
+      for (int m = i + 1; m < 5; ++m) t = fmaf(-L[pk(m, i)], v[m], t);
+      v[i] = t / L[pk(i, i)];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) X[i][c] = d[i] * v[i];
+  }
+  // p = p- + K (p+ - p-), K[i][m] = X[m][i]
+  float dp[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) dp[m] = pp[m] - pm[m];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float t = pm[i];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) t = fmaf(X[m][i], dp[m], t);
+    ps[i] = t;
+  }
+  // C = K C+ (symmetric in exact arithmetic: averaged with its transpose)
+  float KC[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      float t = 0.0f;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) t = fmaf(X[m][i], cp[pk(m, j)], t);
+      KC[i][j] = t;
+    }
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) cs[pk(i, j)] = 0.5f * (KC[i][j] + KC[j][i]);
+  return true;
+}
+
+__device__ __forceinline__ void store5(float *dst, const float v[5]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dst[i] = v[i];
+}
+__device__ __forceinline__ void store15(float *dst, const float v[15]) {
+#pragma unroll
+  for (int i = 0; i < 15; ++i) dst[i] = v[i];
+}
+
+__device__ void seed_cov_of(const FitArgs &A, Trk &T) {
+#pragma unroll
+  for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+  T.c[0] = A.seed_cov[0];
+  T.c[2] = A.seed_cov[1];
+  T.c[5] = A.seed_cov[2];
+  T.c[9] = A.seed_cov[3];
+  T.c[14] = A.seed_cov[4];
+  T.clear_comp();
+}
+
+__device__ void smooth_track(const FitArgs &A, int64_t t) {
+  const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
+  const int st0 = A.status[t];
+  const float *sd = A.seed + 5 * t;
+  const float qnan = __int_as_float(0x7fc00000);
+  Trk T;
+  T.sp = sd[2];
+  T.spl = 0.f;
+  T.tl0 = sd[3];
+  T.dtl = 0.f;
+  T.w0 = sd[4];
+  T.dw = 0.f;
+  T.dy = 0.f;
+  T.dz = 0.f;
+  T.ya = 0.f;
+  T.za = 0.f;
+  seed_cov_of(A, T);
+  int st = st0;
+  double chi2sum = 0.0;
+  int nacc = 0;
+  float xref = 0.f;
+  float out_p[5], out_c[15];
+  int64_t smoothed_from = e;  // clusters [smoothed_from, e) hold smoothed values
+  if (st0 != ST_BAD_INPUT) {  // BAD_INPUT here = offsets out of range: touch nothing of the frame
+    const int n = (int)(e - a);
+    if (n > 0) {
+      T.ya = A.y[a];
+      T.za = A.z[a];
+      xref = A.x[a];
+    }
+    state_of(T, out_p);  // the outputs of a track that is not fitted
+    cov_of(T, out_c);
+    float xcur = xref;
+    int64_t fw_done = a;  // clusters the forward filter updated with
+    if (st0 == ST_OK) {
+      uint32_t gate_hi, gate_lo;
+      split64(A.chi2_max_d, gate_hi, gate_lo);
+      // ---------------- forward filter (outward pass) ----------------
+      int nacc_out = 0, rprev = -1;
+      int64_t k = a;
+      int rk = A.row[k];
+      st = check_cluster(rk, rprev, A.n_rows, A.x[k], A.y[k], A.z[k], A.sy2[k], A.sz2[k]);
+      for (int r = rk; st == ST_OK; ++r) {
+        const bool has = (rk == r);
+        const float xt = has ? A.x[k] : A.row_x[r];
+        if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
+        xcur = xt;
+        if (has) {
+          float pm[5], cm[15];
+          state_of(T, pm);
+          cov_of(T, cm);
+          store5(A.sm_state + 5 * k, pm);
+          store15(A.sm_cov + 15 * k, cm);
+          bool acc;
+          double chi2;
+          const int ust = update(T, A.y[k], A.z[k], A.sy2[k], A.sz2[k], A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
+          if (ust != ST_OK) { st = ust; break; }
+          A.accept[k] = acc ? 1u : 0u;
+          nacc_out += acc ? 1 : 0;
+          ++fw_done;
+          rprev = rk;
+          if (++k < e) {
+            rk = A.row[k];
+            const int vs = check_cluster(rk, rprev, A.n_rows, A.x[k], A.y[k], A.z[k], A.sy2[k], A.sz2[k]);
+            if (vs != ST_OK) { st = vs; break; }
+          }
+        }
+        if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
+        if (k == e) break;
+      }
+      if (st == ST_OK) {
+        // ---------------- restart, as the fit's inward pass ----------------
+        const bool fw_valid = 100 * nacc_out >= A.reseed_pct * n;
+        if (!fw_valid) {
+          float p[5];
+          const int64_t m = a + n / 2;
+          seed3(A.x[e - 1], A.y[e - 1], A.z[e - 1], A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
+          T.sp = -p[2];
+          T.spl = 0.f;
+          T.tl0 = -p[3];
+          T.dtl = 0.f;
+          T.w0 = -p[4];
+          T.dw = 0.f;
+          T.ya = A.y[e - 1];
+          T.za = A.z[e - 1];
+          T.dy = 0.f;
+          T.dz = 0.f;
+          seed_cov_of(A, T);
+        } else {
+          const float d0 = fminf(A.restart_scale * T.c[0], A.seed_cov[0]);
+          const float d1 = fminf(A.restart_scale * T.c[2], A.seed_cov[1]);
+          const float d2 = fminf(A.restart_scale * (T.c[5] + T.c5l), A.seed_cov[2]);
+          const float d3 = fminf(A.restart_scale * (T.c[9] + T.c9l), A.seed_cov[3]);
+          const float d4 = fminf(A.restart_scale * (T.c[14] + T.c14l), A.seed_cov[4]);
+#pragma unroll
+          for (int i = 0; i < 15; ++i) T.c[i] = 0.f;
+          T.c[0] = d0;
+          T.c[2] = d1;
+          T.c[5] = d2;
+          T.c[9] = d3;
+          T.c[14] = d4;
+          T.clear_comp();
+        }
+        // ---------------- backward filter and combination ----------------
+        k = e - 1;
+        rk = A.row[k];
+        for (int r = rk, step = 0;; --r, ++step) {
+          const bool has = (rk == r);
+          const float xt = has ? A.x[k] : A.row_x[r];
+          if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
+          xcur = xt;
+          if (step > 0 && A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);  // the row's kink lies beyond its measurement
+          if (has) {
+            bool acc;
+            double chi2;
+            const int ust = update(T, A.y[k], A.z[k], A.sy2[k], A.sz2[k], A.chi2_max_d, gate_hi, gate_lo, true, acc,
+                                   chi2);
+            if (ust != ST_OK) { st = ust; break; }
+            chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
+            nacc += acc ? 1 : 0;
+            A.accept[k] = (uint8_t)(A.accept[k] | (acc ? 2u : 0u));
+            float pp[5], cp[15], ps[5], cs[15];
+            state_of(T, pp);
+            cov_of(T, cp);
+            if (fw_valid) {
+              float pm[5], cm[15];
+#pragma unroll
+              for (int i = 0; i < 5; ++i) pm[i] = A.sm_state[5 * k + i];
+#pragma unroll
+              for (int i = 0; i < 15; ++i) cm[i] = A.sm_cov[15 * k + i];
+              if (!combine(pm, cm, pp, cp, ps, cs)) { st = ST_NOT_PD; break; }
+            } else {
+              store5(ps, pp);
+              store15(cs, cp);
+            }
+            store5(A.sm_state + 5 * k, ps);
+            store15(A.sm_cov + 15 * k, cs);
+            smoothed_from = k;
+            if (k == a) {
+              store5(out_p, ps);
+              store15(out_c, cs);
+            }
+            if (--k < a) break;
+            rk = A.row[k];
+          }
+        }
+        if (st == ST_OK) {
+          bool fin = true;
+#pragma unroll
+          for (int i = 0; i < 5; ++i) fin = fin && isfinite(out_p[i]);
+#pragma unroll
+          for (int i = 0; i < 15; ++i) fin = fin && isfinite(out_c[i]);
+          if (!fin) st = ST_NONFINITE;
+        }
+        if (st == ST_OK && 100 * nacc < kSmoothDerailPct * n) st = ST_DERAILED;
+      }
+      if (st != ST_OK && st != ST_DERAILED) {  // a failed fit: the state where it stopped
+        state_of(T, out_p);
+        cov_of(T, out_c);
+      }
+    }
+    // accept bytes the forward filter did not reach; clusters without a smoothed state
+    for (int64_t q = fw_done; q < e; ++q) A.accept[q] = 0u;
+    for (int64_t q = a; q < smoothed_from; ++q) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) A.sm_state[5 * q + i] = qnan;
+#pragma unroll
+      for (int i = 0; i < 15; ++i) A.sm_cov[15 * q + i] = qnan;
+      if (q >= fw_done) continue;
+      A.accept[q] = (uint8_t)(A.accept[q] & 1u);  // forward bit only
+    }
+  }
+  if (st0 == ST_BAD_INPUT) {
+    state_of(T, out_p);
+    cov_of(T, out_c);
+  }
+  A.x_ref[t] = xref;
+  store5(A.state + 5 * t, out_p);
+  store15(A.cov + 15 * t, out_c);
+  A.chi2[t] = chi2sum;
+  A.ndf[t] = 2 * nacc - 5;
+  A.status[t] = st;
+}
+
+__global__ void __launch_bounds__(kSmoothBlock) k_smooth(FitArgs A) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(A.work, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= (unsigned long long)A.n_tracks) break;
+    const int64_t i = (int64_t)base + lane;
+    if (i < A.n_tracks) smooth_track(A, A.perm ? (int64_t)A.perm[i] : i);
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+int smooth_grid() {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_smooth, kSmoothBlock, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int per_sm = occ < 4 ? (occ > 0 ? occ : 1) : 4;  // up to 512 tracks per SM, as the fit
+  return sms * per_sm;
+}
+
+cudaError_t launch_smooth(const FitArgs &a, int grid, cudaStream_t stream) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  if (!a.sm_state || !a.sm_cov || grid <= 0) return cudaErrorInvalidValue;
+  k_smooth<<<grid, kSmoothBlock, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tpcfit

@@ -61,6 +61,10 @@ extern "C" const char *tpcfit_strerror(int code) {
 
 extern "C" const char *tpcfit_last_error_message(void) { return g_errmsg; }
 
+namespace tpcfit {
+int set_error_message(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace tpcfit
+
 extern "C" double tpcfit_now(void) {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -261,6 +265,7 @@ extern "C" void tpcfit_default_config(tpcfit_config *c) {
   c->seed_cov[3] = 0.01f;
   c->seed_cov[4] = 1.0f;
   c->restart_scale = 100.0f;
+  c->reseed_pct = 50;
   c->min_clusters = 10;
   c->n_rows = 152;
   c->row_x0_cm = 85.0f;
@@ -400,6 +405,8 @@ FitArgs make_args(tpcfit_handle *h, const tpcfit_frame *f, const tpcfit_result *
   a.chi2_out_c = r->chi2_out_cluster;
   a.chi2_in_c = r->chi2_in_cluster;
   a.restart_state = r->restart_state;
+  a.sm_state = r->smoothed_state;
+  a.sm_cov = r->smoothed_cov;
   a.res_y = r->res_y;
   a.res_z = r->res_z;
   a.res_inv_step_y = 1.0f / c.res_step_y_cm;
@@ -462,7 +469,8 @@ int run_sequence(tpcfit_handle *h, const FitArgs &a, cudaStream_t st, Scratch &s
   if (timed) CU(cudaEventRecord(h->ring[slot].ev[1], st));
   CU(launch_sort(a, st, &l));
   if (timed) CU(cudaEventRecord(h->ring[slot].ev[2], st));
-  CU(launch_fit(a, h->fit_grid, h->fit_block, st));
+  if (a.sm_state) CU(launch_smooth(a, smooth_grid(), st));
+  else CU(launch_fit(a, h->fit_grid, h->fit_block, st));
   l += 1;
   if (a.res_y || a.res_z) {
     CU(launch_residuals(a, st));
@@ -506,6 +514,16 @@ static int check_frame_shape(const tpcfit_frame *f, const tpcfit_result *r) {
   if ((f->mem != TPCFIT_MEM_HOST && f->mem != TPCFIT_MEM_DEVICE) ||
       (r->mem != TPCFIT_MEM_HOST && r->mem != TPCFIT_MEM_DEVICE))
     return fail(TPCFIT_E_INVAL, "mem must be TPCFIT_MEM_HOST or TPCFIT_MEM_DEVICE");
+  if (!r->smoothed_state != !r->smoothed_cov)
+    return fail(TPCFIT_E_INVAL, "the smoother writes both smoothed_state and smoothed_cov");
+  return TPCFIT_OK;
+}
+
+// The smoother variant (smoothed outputs requested) takes neither energy loss
+// nor seed iteration.
+static int check_smoother(const tpcfit_handle *h, const tpcfit_result *r) {
+  if (r->smoothed_state && (h->cfg.xrho_per_row > 0.0f || h->cfg.fit_iterations > 0))
+    return fail(TPCFIT_E_INVAL, "the smoother takes neither energy loss nor seed iteration");
   return TPCFIT_OK;
 }
 
@@ -567,6 +585,7 @@ extern "C" int tpcfit_batch_create(tpcfit_handle *h, const tpcfit_frame *f, tpcf
   if (!h || !out) return fail(TPCFIT_E_INVAL, "handle or out is NULL");
   int rc = check_frame_shape(f, r);
   if (rc) return rc;
+  if ((rc = check_smoother(h, r))) return rc;
   if (f->mem != TPCFIT_MEM_DEVICE || r->mem != TPCFIT_MEM_DEVICE)
     return fail(TPCFIT_E_INVAL, "a batch takes a device frame and device results");
   CU(cudaSetDevice(h->device));
@@ -595,12 +614,14 @@ extern "C" int tpcfit_batch_create(tpcfit_handle *h, const tpcfit_frame *f, tpcf
   // set the kernel attributes before capture (no such calls inside it)
   fit_blocks_per_sm(h->fit_block);
   FitArgs a = make_args(h, f, r, b->scratch, 0);
+  const int sgrid = a.sm_state ? smooth_grid() : 0;
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bail(fail(TPCFIT_E_CUDA, "begin capture: %s", cudaGetErrorString(e)));
   int l = 0;
   if ((e = cudaMemsetAsync(b->scratch.hist, 0, b->scratch.small_bytes, b->stream)) != cudaSuccess ||
       (e = launch_prepare(a, b->stream)) != cudaSuccess || (e = launch_sort(a, b->stream, &l)) != cudaSuccess ||
-      (e = launch_fit(a, h->fit_grid, h->fit_block, b->stream)) != cudaSuccess ||
+      (e = (a.sm_state ? launch_smooth(a, sgrid, b->stream) : launch_fit(a, h->fit_grid, h->fit_block, b->stream))) !=
+          cudaSuccess ||
       (e = launch_residuals(a, b->stream)) != cudaSuccess ||
       (e = cudaMemcpyAsync(b->h_err, b->scratch.err, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream)) !=
           cudaSuccess)
@@ -725,6 +746,8 @@ int64_t tpcfit::chunk_cuts(const int64_t *off, int64_t nt, int64_t nc_all, int64
 static int fit_host(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r) {
   if (r->chi2_out_cluster || r->chi2_in_cluster || r->restart_state)
     return fail(TPCFIT_E_INVAL, "diagnostic outputs need a device frame and device results");
+  if (r->smoothed_state || r->smoothed_cov)
+    return fail(TPCFIT_E_INVAL, "smoothed outputs need a device frame and device results");
   const int64_t *off = f->track_offsets;
   const int64_t nt = f->n_tracks;
   int rc = TPCFIT_OK;
@@ -808,6 +831,7 @@ extern "C" int tpcfit_fit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result
   if (!h) return fail(TPCFIT_E_INVAL, "handle is NULL");
   int rc = check_frame_shape(f, r);
   if (rc) return rc;
+  if ((rc = check_smoother(h, r))) return rc;
   std::lock_guard<std::mutex> lk(h->mu);
   CU(cudaSetDevice(h->device));
   if (f->n_tracks == 0) return TPCFIT_OK;
@@ -823,6 +847,7 @@ extern "C" int tpcfit_fit_async(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_
   if (!h) return fail(TPCFIT_E_INVAL, "handle is NULL");
   int rc = check_frame_shape(f, r);
   if (rc) return rc;
+  if ((rc = check_smoother(h, r))) return rc;
   if (f->mem != TPCFIT_MEM_DEVICE || r->mem != TPCFIT_MEM_DEVICE)
     return fail(TPCFIT_E_INVAL, "tpcfit_fit_async takes device frames and device results");
   std::lock_guard<std::mutex> lk(h->mu);

@@ -26,6 +26,7 @@ struct FitArgs {
   uint8_t *accept;
   double *chi2_out_c, *chi2_in_c;  // optional per-cluster chi2 (nullptr: not written)
   float *restart_state;            // optional inward restart state (nullptr: not written)
+  float *sm_state, *sm_cov;        // smoother variant: per-cluster smoothed state / packed covariance (nullptr: fit)
   int16_t *res_y, *res_z;          // optional residual codes (nullptr: not written)
   float res_inv_step_y, res_inv_step_z;
   // scratch (device)
@@ -43,6 +44,7 @@ struct FitArgs {
   float xrho;                    // energy-loss layer per row (g/cm^2); 0 = none
   float el_kza, el_a, el_ratio;  // K Z/A (GeV cm^2/g), 2 m_e / I, m_e / M
   int32_t n_iter;                // seed iterations: refits seeded from the fitted state
+  int32_t reseed_pct;            // inward re-seed below this outward acceptance (percent)
   float seed_cov[5];
   int32_t min_clusters, n_rows;
 };
@@ -139,6 +141,7 @@ inline void fit_params(FitArgs &a, const tpcfit_config &c) {
   a.el_a = (float)(2.0 * me / (iev * 1e-9));
   a.el_ratio = c.mass_gev > 0.0f ? (float)(me / (double)c.mass_gev) : 0.0f;
   a.n_iter = c.fit_iterations;
+  a.reseed_pct = c.reseed_pct;
   for (int i = 0; i < 5; ++i) a.seed_cov[i] = c.seed_cov[i];
   a.min_clusters = c.min_clusters;
   a.n_rows = c.n_rows;
@@ -150,6 +153,7 @@ inline const char *check_variant_params(const tpcfit_config &c) {
     return "energy-loss parameters must be >= 0";
   if (c.xrho_per_row > 0.0f && !(c.mass_gev > 0.0f)) return "energy loss needs mass_gev > 0";
   if (c.fit_iterations < 0 || c.fit_iterations > 16) return "fit_iterations must be in [0, 16]";
+  if (c.reseed_pct < 0 || c.reseed_pct > 100) return "reseed_pct must be in [0, 100]";
   return nullptr;
 }
 
@@ -189,11 +193,18 @@ __host__ __device__ inline int follow_zbin(float z, float z_max, int nz) {
 
 cudaError_t launch_follow(const FollowArgs &a, cudaStream_t stream);
 
+// Record `msg` as the calling thread's tpcfit_last_error_message; returns code.
+int set_error_message(int code, const char *msg);
+
 // Launch helpers (all asynchronous on `stream`); each returns the CUDA error
 // of its launch.
 cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream);
 cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches);
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream);
+// the two-filter smoother variant in place of the fit (a.sm_state, a.sm_cov set),
+// on a persistent grid of smooth_grid() blocks (0 if the device cannot be queried)
+int smooth_grid();
+cudaError_t launch_smooth(const FitArgs &a, int grid, cudaStream_t stream);
 // track-model compression residual codes (nothing when a.res_y and a.res_z are null)
 cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream);
 // Occupancy-derived resident blocks per SM for the fit kernel at `block` threads.

@@ -43,7 +43,9 @@ constexpr size_t kScratchBytes = kPermOff + a256((size_t)TPCFIT_NOALLOC_MAX_TRAC
 
 }  // namespace
 
-// The scratch array: every GPU that loads the library holds it until exit.
+// The scratch array.  The CUDA runtime loads it with the library's device code
+// on a device (at the first launch or symbol lookup there: lazily, by default)
+// and keeps it until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
@@ -52,14 +54,34 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void *g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
-// Error codes only: this entry point keeps no message state.
-int fail(int code, const char *) { return code; }
+// The code, with `msg` as the thread's tpcfit_last_error_message.
+int fail(int code, const char *msg) { return set_error_message(code, msg); }
 
-// Pad-row plane positions, float-rounded from double, written into the scratch.
+// Pad-row plane positions, float-rounded from double, written into the
+// scratch: the product and the sum each rounded on its own (no fused
+// multiply-add), as the handle path computes the same table on the host.
 __global__ void k_noalloc_rowx(float *rowx, double x0, double pitch) {
   const int r = threadIdx.x;
-  if (r < kMaxRows) rowx[r] = (float)(x0 + (double)r * pitch);
+  if (r < kMaxRows) rowx[r] = (float)__dadd_rn(x0, __dmul_rn((double)r, pitch));
 }
+
+// Makes `device` current for the lifetime of the guard and gives the
+// caller's thread its previous device back on every return.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    ok = cudaSetDevice(device) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 // Per-device set-up, once per device with that device current: the host needs
 // the array's device address to hand it to the kernels.
@@ -105,10 +127,12 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   if (cfg.block_threads != 0 && cfg.block_threads != 128 && cfg.block_threads != 256)
     return fail(TPCFIT_E_INVAL, "block_threads must be 0, 128 or 256");
   if (cfg.blocks_per_sm < 0) return fail(TPCFIT_E_INVAL, "blocks_per_sm < 0");
-  if (cudaSetDevice(cfg.device) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(TPCFIT_E_NODEV, "cannot select the CUDA device");
-  }
+  if (r->smoothed_state || r->smoothed_cov)
+    return fail(TPCFIT_E_INVAL, "tpcfit_fit_noalloc does not run the smoother (use tpcfit_fit)");
+  if ((r->res_y || r->res_z) && !(cfg.res_step_y_cm > 0.0f && cfg.res_step_z_cm > 0.0f))
+    return fail(TPCFIT_E_INVAL, "residual steps must be > 0");
+  DeviceGuard dev(cfg.device);
+  if (!dev.ok) return fail(TPCFIT_E_NODEV, "cannot select the CUDA device");
   void *base = nullptr;
   int rc = setup(cfg.device, &base);
   if (rc) return rc;
@@ -128,7 +152,10 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   a.chi2_out_c = r->chi2_out_cluster;
   a.chi2_in_c = r->chi2_in_cluster;
   a.restart_state = r->restart_state;
-  a.res_y = a.res_z = nullptr;  // residuals are not written by this entry point
+  a.res_y = r->res_y;  // optional residual codes: one more kernel, no scratch
+  a.res_z = r->res_z;
+  a.res_inv_step_y = 1.0f / cfg.res_step_y_cm;
+  a.res_inv_step_z = 1.0f / cfg.res_step_z_cm;
   a.hist = reinterpret_cast<uint32_t *>(sc + kHistOff);
   a.work = reinterpret_cast<unsigned long long *>(sc + kWorkOff);
   a.frame_error = reinterpret_cast<int32_t *>(sc + kErrOff);
@@ -151,6 +178,7 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   if ((e = launch_prepare(a, st)) != cudaSuccess) goto cuda_fail;
   if ((e = launch_sort(a, st, nullptr)) != cudaSuccess) goto cuda_fail;
   if ((e = launch_fit(a, sms * bps, block, st)) != cudaSuccess) goto cuda_fail;
+  if ((e = launch_residuals(a, st)) != cudaSuccess) goto cuda_fail;
   {
     int32_t err_host = 0;
     if ((e = cudaMemcpyAsync(&err_host, a.frame_error, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -161,5 +189,6 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   return TPCFIT_OK;
 cuda_fail:
   cudaGetLastError();
-  return e == cudaSuccess ? TPCFIT_OK : TPCFIT_E_CUDA;
+  if (e == cudaSuccess) return TPCFIT_OK;
+  return fail(TPCFIT_E_CUDA, cudaGetErrorString(e));
 }

@@ -148,6 +148,7 @@ static void carve(void *mem, int64_t nt, int64_t nc, bool want_ry, bool want_rz,
   dr->mem = TPCFIT_MEM_DEVICE;
   dr->chi2_out_cluster = dr->chi2_in_cluster = nullptr;
   dr->restart_state = nullptr;
+  dr->smoothed_state = dr->smoothed_cov = nullptr;
   *scratch = p;
 }
 

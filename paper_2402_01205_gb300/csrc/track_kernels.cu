@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
   T.c[5] = A.seed_cov[2];
   T.c[9] = A.seed_cov[3];
   T.c[14] = A.seed_cov[4];
-  T.c9l = T.c14l = 0.f;
+  T.clear_comp();
   uint32_t gate_hi, gate_lo;
   split64(A.chi2_max_d, gate_hi, gate_lo);
   const int r0 = A.seed_row[s], sec = A.seed_sector[s];

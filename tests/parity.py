@@ -1,7 +1,12 @@
 """GPU-vs-oracle comparison with the tolerances of the fit's precision split.
 
 Tolerances of the parity bar:
-  state      |dp_i| / sqrt(C_ii oracle) < 1e-3
+  state      |dp_i| / max(sqrt(C_ii oracle), 1000 ulp32(p_i)) < 1e-3, where
+             ulp32(p_i) is the spacing of binary32 numbers at the oracle's
+             p_i: the library reports the state in binary32, which cannot
+             come closer to p_i than half that spacing (this floor binds
+             only when sigma_i < 1000 ulp32(p_i), e.g. sigma_z < 0.015 cm at
+             |z| = 250 cm)
   covariance |dC_ij| / sqrt(C_ii C_jj)  < 1e-4   (normalised by the diagonal)
   chi2       |dchi2| <= 1e-4 * max(chi2, 1)
   ndf, status, accept bytes: identical, except that a track whose accept flag
@@ -52,7 +57,9 @@ class ParityReport:
 
 
 def compare(offsets, gpu: dict, orc: dict, chi2_max: float = 16.0, track_ids=None) -> ParityReport:
-    """``orc`` must come from oracle.fit(..., diagnostics=True) on the same frame."""
+    """``orc`` comes from oracle.fit(..., diagnostics=True) on the same frame.
+    Without the diagnostics (no per-cluster chi2) every accept difference
+    counts as a mismatch: the gate window cannot be checked."""
     off = _np(offsets).astype(np.int64)
     g = {k: _np(v) for k, v in gpu.items()}
     nt = off.shape[0] - 1
@@ -71,6 +78,9 @@ def compare(offsets, gpu: dict, orc: dict, chi2_max: float = 16.0, track_ids=Non
             continue
         # first differing decision in processing order: outward (ascending), then inward (descending)
         dout, din = (d & 1) != 0, (d & 2) != 0
+        if "chi2_out_c" not in orc:
+            rep.accept_mismatch.append(int(t))
+            continue
         if dout.any():
             k, c = a + int(np.argmax(dout)), orc["chi2_out_c"]
         else:
@@ -86,7 +96,8 @@ def compare(offsets, gpu: dict, orc: dict, chi2_max: float = 16.0, track_ids=Non
     import oracle
     C = oracle.unpack_cov(orc["cov"][keep])
     sig = np.sqrt(np.diagonal(C, axis1=1, axis2=2))
-    ds = np.abs(g["state"][keep].astype(np.float64) - orc["state"][keep]) / sig
+    ulp32 = np.spacing(np.abs(orc["state"][keep]).astype(np.float32)).astype(np.float64)
+    ds = np.abs(g["state"][keep].astype(np.float64) - orc["state"][keep]) / np.maximum(sig, 1000.0 * ulp32)
     Cg = oracle.unpack_cov(g["cov"][keep].astype(np.float64))
     dc = np.abs(Cg - C) / (sig[:, :, None] * sig[:, None, :])
     dchi = np.abs(g["chi2"][keep] - orc["chi2"][keep]) / np.maximum(orc["chi2"][keep], 1.0)
@@ -97,3 +108,25 @@ def compare(offsets, gpu: dict, orc: dict, chi2_max: float = 16.0, track_ids=Non
     rep.worst = dict(state_track=int(keep[np.argmax(ds.max(1))]), cov_track=int(keep[np.argmax(dc.max((1, 2)))]),
                      chi2_track=int(keep[np.argmax(dchi)]))
     return rep
+
+
+def compare_smoothed(offsets, status_ok, gpu_state, gpu_cov, orc_state, orc_cov) -> dict:
+    """Per-cluster smoothed states of the tracks ``status_ok`` (bool per track)
+    against the oracle's, with the bars of ``compare``: state over the
+    oracle's sigma (with the binary32 floor), covariance over the square roots
+    of the oracle's diagonal."""
+    import oracle
+    off = _np(offsets).astype(np.int64)
+    ok = np.repeat(np.asarray(status_ok, bool), np.diff(off))
+    gs, gc = _np(gpu_state).reshape(-1, 5)[ok].astype(np.float64), _np(gpu_cov).reshape(-1, 15)[ok].astype(np.float64)
+    os_, oc = np.asarray(orc_state)[ok], np.asarray(orc_cov)[ok]
+    C = oracle.unpack_cov(oc)
+    sig = np.sqrt(np.diagonal(C, axis1=1, axis2=2))
+    ulp32 = np.spacing(np.abs(os_).astype(np.float32)).astype(np.float64)
+    ds = np.abs(gs - os_) / np.maximum(sig, 1000.0 * ulp32)
+    dc = np.abs(oracle.unpack_cov(gc) - C) / (sig[:, :, None] * sig[:, None, :])
+    return {"clusters": int(ok.sum()), "max_state": float(ds.max()) if ds.size else 0.0,
+            "max_cov": float(dc.max()) if dc.size else 0.0,
+            "q999_state": float(np.quantile(ds.max(1), 0.999)) if ds.size else 0.0,
+            "q999_cov": float(np.quantile(dc.max((1, 2)), 0.999)) if dc.size else 0.0,
+            "finite": bool(np.isfinite(gs).all() and np.isfinite(gc).all())}

@@ -111,3 +111,27 @@ def test_binding_marshals_host_frames_without_x():
     bad = dict(arrays, z=None)
     with pytest.raises(ValueError):
         T._frame_struct(types.SimpleNamespace(offsets=f.offsets, x=None, **bad))
+
+
+def test_results_of_another_frame_are_rejected_before_any_launch():
+    """Every result buffer is checked against the frame it is for (state and
+    cov per track, accept and residual codes per cluster): a result sized for
+    a smaller frame raises ValueError in the binding, so no kernel or copy
+    ever writes past it.  Handle 0 is never reached."""
+    import numpy as np
+
+    import paper_2402_01205_gb300 as T
+    import tpcgen
+    f = tpcgen.generate("sector1k", n_tracks=40)
+    small = tpcgen.generate("sector1k", n_tracks=39)
+    good = T.alloc_result(f.n_tracks, f.n_clusters, residuals=True)
+    T._result_struct(good, f.n_tracks, f.n_clusters)  # the right sizes pass
+    for k in ("state", "cov", "chi2", "status", "accept", "res_y"):
+        res = dict(good)
+        res[k] = T.alloc_result(small.n_tracks, small.n_clusters, residuals=True)[k]
+        for call in (lambda: T.fit(0, f, res), lambda: T.submit(0, f, res), lambda: T.fit_noalloc(f, res)):
+            with pytest.raises(ValueError, match=k):
+                call()
+    res = dict(good, restart_state=np.empty((f.n_tracks - 1, 5), np.float32))
+    with pytest.raises(ValueError, match="restart_state"):
+        T.fit(0, f, res)

@@ -83,6 +83,45 @@ def test_parity_pbpb_spectrum_200k(T):
     check(f, gpu, orc)
 
 
+def test_parity_detector_50k_unequal_variances(T):
+    """Per-cluster measurement variances: sy2 and sz2 drawn independently,
+    log-uniform in [0.002, 0.05] cm^2, the noise drawn with them (V =
+    diag(sy2, sz2) read from each cluster)."""
+    f = tpcgen.generate("detector50k", seed=7, var_mode=1)
+    assert (f.sy2 != f.sz2).mean() > 0.99
+    check(f, fit_gpu(T, f), oracle.fit(f, orc_cfg(5e-4), diagnostics=True))
+
+
+def test_parity_pbpb_spectrum_200k_unequal_variances(T):
+    f = tpcgen.generate("pbpb2m", n_tracks=200_003, seed=9, var_mode=1)
+    check(f, fit_gpu(T, f), oracle.fit(f, orc_cfg(5e-4), diagnostics=True))
+
+
+def test_parity_strongly_correlated_innovation_matrices(T):
+    """Steep (tan lambda up to 2), soft (pT 0.2-0.5 GeV/c) tracks with small
+    cluster variances (1e-4 to 1e-2 cm^2): the predicted covariance dominates
+    S and correlates y with z through the direction, |corr(S)| reaches 0.992,
+    so det S cancels to 1.5 % of S00 S11 and the gain sees that cancellation.
+    With sigma_z down to 0.01 cm at |z| up to 250 cm, the binary32 spacing of
+    the output z (1.5e-5 cm) is itself near 1e-3 sigma: the state bar's
+    float32 floor (tests/parity.py) matters here."""
+    f = tpcgen.generate("detector50k", n_tracks=30_011, seed=8, var_mode=1, var_lo=1e-4, var_hi=1e-2,
+                        tgl_max=2.0, pt_max=0.5)
+    check(f, fit_gpu(T, f), oracle.fit(f, orc_cfg(5e-4), diagnostics=True))
+
+
+def test_parity_sees_swapped_variances(T):
+    """The comparison is sensitive to which variance belongs to which axis:
+    the GPU fit of the same clusters with sy2 and sz2 exchanged fails parity
+    against the oracle's fit of the frame as generated."""
+    f = tpcgen.generate("detector50k", n_tracks=5_000, seed=10, var_mode=1)
+    swapped = tpcgen.Frame(f.offsets, f.x, f.y, f.z, f.sz2, f.sy2, f.row, f.sector)
+    orc = oracle.fit(f, orc_cfg(5e-4), diagnostics=True)
+    rep = compare(f.offsets, fit_gpu(T, swapped), orc)
+    assert not rep.ok and rep.max_state > 0.1, rep.summary()
+    check(f, fit_gpu(T, f), orc)  # and the unswapped frame passes
+
+
 def test_parity_full_size_pbpb_frame_sampled(T):
     """2,000,000 tracks fitted whole (benchmark launch); oracle on 8 blocks of 2,500 tracks."""
     f = tpcgen.generate("pbpb2m")

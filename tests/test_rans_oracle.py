@@ -30,6 +30,32 @@ def test_hand_derived_example():
     assert len(p["payload"]) == 128 + 2 * want["words"][0][0] and len(p["esc"]) == want["escapes"][0][0]
 
 
+def test_hand_derived_example_with_a_renormalisation_word():
+    """Four rare symbols in one lane drive its state past f * 2^20 at the
+    last step encoded: the 16-bit word and the state after it are derived by
+    hand in the fixture."""
+    want = {}
+    for ln in open(os.path.join(os.path.dirname(__file__), "golden", "rans_hand_renorm.txt")):
+        if ln.strip() and not ln.startswith("#"):
+            k, *v = ln.split()
+            want.setdefault(k, []).append([int(t) for t in v])
+    c = np.zeros(want["n"][0][0], np.int16)
+    c[want["input_ones"][0]] = 1
+    blob = rans.encode(c)
+    p = rans.parse(blob)
+    for s, fq in want["freq"]:
+        assert p["f"][s] == fq
+    states = struct.unpack_from("<32I", p["payload"], 0)
+    for lane, x in want["state"]:
+        assert states[lane] == x
+    nw = want["words"][0][0]
+    assert len(p["payload"]) == 128 + 2 * nw
+    words = struct.unpack_from("<%dH" % nw, p["payload"], 128)
+    for i, w in want["word"]:
+        assert words[i] == w
+    assert np.array_equal(rans.decode(blob), c)
+
+
 @pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 127, 128, 129, 1000])
 def test_round_trip_partial_segments(n):
     rng = np.random.default_rng(n)

@@ -81,6 +81,25 @@ def test_noalloc_rejects_frames_above_the_limit(T):
     with pytest.raises(T.TpcfitError) as ei:
         T.fit_noalloc(dev_frame(f), T.alloc_result(f.n_tracks, f.n_clusters, device="cuda"))
     assert ei.value.code == T.E_INVAL
+    assert "TPCFIT_NOALLOC_MAX_TRACKS" in str(ei.value)  # the detail of tpcfit_last_error_message
+    assert torch.cuda.current_device() == 0  # the caller's device is current again
+
+
+def test_noalloc_writes_the_residual_codes_of_fit(T):
+    """Residual codes requested from the allocation-free call are those of
+    tpcfit_fit on the same frame (same kernels, same inputs: bit for bit)."""
+    f = tpcgen.generate("detector50k", n_tracks=9_001, seed=36)
+    d = dev_frame(f)
+    with T.Fitter() as fx:
+        ref = T.alloc_result(f.n_tracks, f.n_clusters, device="cuda", residuals=True)
+        fx.fit(d, ref)
+        ref = host(ref)
+    for _ in range(2):
+        out = T.alloc_result(f.n_tracks, f.n_clusters, device="cuda", residuals=True)
+        T.fit_noalloc(d, out)
+        got = host(out)
+        assert_same_fit(got, ref)
+        assert np.array_equal(got["res_y"], ref["res_y"]) and np.array_equal(got["res_z"], ref["res_z"])
 
 
 def test_noalloc_with_energy_loss_equals_fit(T):

@@ -55,6 +55,7 @@ class _Config(ctypes.Structure):
         ("max_attempts", ctypes.c_int32), ("n_threads", ctypes.c_int32),
         ("track_id_offset", ctypes.c_int64),
         ("xrho", ctypes.c_double), ("eloss_za", ctypes.c_double), ("eloss_i_ev", ctypes.c_double),
+        ("var_mode", ctypes.c_int32), ("var_lo", ctypes.c_double), ("var_hi", ctypes.c_double),
     ]
 
 
@@ -89,6 +90,7 @@ BASE = dict(
     sector_half_angle=math.radians(10.0), vtx_sigma=0.01, tgl_max=0.9, z_max=250.0,
     snp_max=0.99, min_clusters=10, max_attempts=1000,
     xrho=0.0, eloss_za=0.49555, eloss_i_ev=137.0,  # no energy loss unless xrho > 0 (neon material)
+    var_mode=0, var_lo=0.002, var_hi=0.05,  # var_mode 1: per-cluster sy2, sz2 log-uniform in [var_lo, var_hi]
 )
 PRESETS = {
     # single sector, 1,000 tracks, no scattering / dropout / outliers

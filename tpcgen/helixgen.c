@@ -51,6 +51,8 @@ typedef struct {
   double xrho;              /* g/cm^2 of material per crossed row (mean energy loss); 0 = none */
   double eloss_za;          /* its Z/A */
   double eloss_i_ev;        /* its mean excitation energy, eV */
+  int32_t var_mode;         /* 0: every cluster has sigma_y^2, sigma_z^2; 1: per-cluster variances */
+  double var_lo, var_hi;    /* var_mode 1: sy2 and sz2 drawn independently, log-uniform in [var_lo, var_hi] cm^2 */
 } tpcgen_config;
 
 typedef struct {
@@ -171,8 +173,15 @@ static int gen_one(const tpcgen_config *c, rng_t *r, int64_t base, const tpcgen_
 
     int dropped = (c->p_drop > 0) && (u01(r) < c->p_drop);
     if (!dropped) {
-      double ny = c->sigma_y > 0 ? c->sigma_y * gauss(r) : 0.0;
-      double nz = c->sigma_z > 0 ? c->sigma_z * gauss(r) : 0.0;
+      /* measurement variances of this cluster, and noise drawn with them */
+      double vy = c->sigma_y * c->sigma_y, vz = c->sigma_z * c->sigma_z;
+      if (c->var_mode == 1) {
+        const double lr = log(c->var_hi / c->var_lo);
+        vy = (double)(float)(c->var_lo * exp(u01(r) * lr));
+        vz = (double)(float)(c->var_lo * exp(u01(r) * lr));
+      }
+      double ny = vy > 0 ? sqrt(vy) * gauss(r) : 0.0;
+      double nz = vz > 0 ? sqrt(vz) * gauss(r) : 0.0;
       int outl = (c->p_outlier > 0) && (u01(r) < c->p_outlier);
       if (outl) {
         ny += (2.0 * u01(r) - 1.0) * c->outlier_half;
@@ -183,8 +192,8 @@ static int gen_one(const tpcgen_config *c, rng_t *r, int64_t base, const tpcgen_
         o->x[k] = (float)X;
         o->y[k] = (float)(best_y + ny);
         o->z[k] = (float)(zq + nz);
-        o->sy2[k] = (float)(c->sigma_y * c->sigma_y > 0 ? c->sigma_y * c->sigma_y : 1e-6);
-        o->sz2[k] = (float)(c->sigma_z * c->sigma_z > 0 ? c->sigma_z * c->sigma_z : 1e-6);
+        o->sy2[k] = (float)(vy > 0 ? vy : 1e-6);
+        o->sz2[k] = (float)(vz > 0 ? vz : 1e-6);
         o->row[k] = (uint8_t)i;
         if (o->truth) {
           double *tr = o->truth + 5 * k;
