@@ -54,6 +54,8 @@ WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT
                         "arrival schedule; 120 GB HBM budget, 8 slots"}
 # fit parameters of a workload beyond the defaults (library / oracle names)
 FIT_PARAMS = {"pbpb2m_eloss": ({"xrho_per_row": 0.0145}, {"xrho": 0.0145})}
+# the metric of the benchmark, the same string in both arms
+METRIC = "clusters/s and tracks/s fitted on 1 GB300 at stated FP64-oracle error; p50/p99 frame latency"
 FP64_PER_CLUSTER = 11         # FP64 lane-instructions per cluster: 4 (outward update) + 7 (inward update + sum)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
@@ -164,42 +166,50 @@ def profiled_counters(n_clusters: int, launch: tuple, variant: str = ""):
     return out, note
 
 
+FP64_NOMINAL_OPS = 0.625e12  # GB300 nominal FP64 rate (1.25 TFLOP/s), as FP64 lane-ops (an FMA counts once) per s
+
+
 def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz, variant: str = "", passes: int = 1):
-    """Roofline of the fit kernel.  Primary: instruction issue (the unit that
-    binds), achieved = ncu warp instructions per launch / mean launch time,
-    peak = 4 per SM per clock at the sampled SM clock.  Beside it the
-    algorithmic roofs: FP64 lane-instructions (11 per cluster) against the
-    live FP64 FMA probe, FP32 flops against 2x the FP32 FMA probe, HBM bytes
-    (22 per cluster + 108 per track) against the measured copy bandwidth."""
+    """Roofline of the fit kernel against its binding algorithmic roof.
+
+    The fit's algorithmic work per cluster is 11 FP64 lane-operations (the
+    innovation-matrix determinant, the outward gate, the inward reciprocal,
+    chi2 and its sum; a lane-operation = one lane of one FP64 instruction,
+    an FMA counting once), about 725 FP32 flops, and 22 bytes of HBM
+    traffic (+108 per track).  On GB300 the FP64 roof binds: the kernel
+    cannot beat 11 lane-ops per cluster at the FP64 pipe's rate.  So
+    ``achieved`` = FP64 lane-ops per launch / mean launch time, ``peak`` =
+    the FP64 FMA rate measured live in the same run (one lane-op per FMA),
+    and beside it the FP32 and HBM fractions and the instruction-issue
+    roof (from the ncu counters committed for this kernel and launch)."""
     peaks, peak_src = measured_peaks()
     c, note = profiled_counters(nc, launch, variant)
     fp64 = FP64_PER_CLUSTER * passes * nc_fit / fit_s  # each seed iteration repeats both passes
     hbm = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
-    sub = {
-        "fp64": {"achieved_tinst_s": fp64 / 1e12, "peak_tinst_s": probe["fp64_fma_per_s"] / 1e12,
-                 "frac": fp64 / probe["fp64_fma_per_s"], "lane_inst_per_cluster": FP64_PER_CLUSTER,
-                 "peak_source": "measured live: FP64 FMA chain probe (tpcfit_probe_fma_rates)"},
-        "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks["hbm_gbs"], "frac": hbm * 1e9 / (peaks["hbm_gbs"] * 1e9),
+    beside = {
+        "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks["hbm_gbs"], "frac": hbm / peaks["hbm_gbs"],
                 "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
     }
     if c and "fp32_flop_per_cluster" in c:
         f32 = c["fp32_flop_per_cluster"] * passes * nc_fit / fit_s
-        sub["fp32"] = {"achieved_tflops": f32 / 1e12, "peak_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
-                       "frac": f32 / (2 * probe["fp32_fma_per_s"]), "flop_per_cluster": c["fp32_flop_per_cluster"],
-                       "peak_source": "2 x measured live FP32 FMA chain probe"}
-    issue_peak = ISSUE_PER_SM_CLK * sms * (sm_mhz or 2070.0) * 1e6
+        beside["fp32"] = {"achieved_tflops": f32 / 1e12, "peak_tflops": 2 * probe["fp32_fma_per_s"] / 1e12,
+                          "frac": f32 / (2 * probe["fp32_fma_per_s"]), "flop_per_cluster": c["fp32_flop_per_cluster"],
+                          "peak_source": "2 x measured live FP32 FMA chain probe"}
     if c:
+        issue_peak = ISSUE_PER_SM_CLK * sms * (sm_mhz or 2070.0) * 1e6
         ach = c["warp_inst"] / fit_s
-        roof = {"bound": "alu", "kernel": "k_fit", "unit": "G warp-inst/s (instruction issue)",
-                "achieved": ach / 1e9, "peak": issue_peak / 1e9, "frac": ach / issue_peak,
-                "peak_source": f"{ISSUE_PER_SM_CLK} issue slots per SM per clock x {sms} SMs x sampled SM clock",
-                "traffic": c["dram_bytes"], "traffic_note": note,
-                "warp_inst_per_cluster": c["warp_inst"] / nc, "active_lanes_per_inst": c["thread_inst"] / c["warp_inst"]}
-    else:
-        roof = {"bound": "alu", "kernel": "k_fit", "unit": "Tinst/s (FP64 pipe, one lane-instruction = 1)",
-                "achieved": fp64 / 1e12, "peak": probe["fp64_fma_per_s"] / 1e12,
-                "frac": fp64 / probe["fp64_fma_per_s"], "traffic": None, "traffic_note": note}
-    roof.update({"fit_ms_avg": fit_s * 1e3, "algorithmic": sub})
+        beside["issue"] = {"achieved_ginst_s": ach / 1e9, "peak_ginst_s": issue_peak / 1e9, "frac": ach / issue_peak,
+                           "peak_source": f"{ISSUE_PER_SM_CLK} issue slots per SM per clock x {sms} SMs x sampled "
+                                          "SM clock", "warp_inst_per_cluster": c["warp_inst"] / nc,
+                           "active_lanes_per_inst": c["thread_inst"] / c["warp_inst"]}
+    roof = {"bound": "alu", "kernel": "k_fit", "unit": "T FP64 lane-ops/s",
+            "achieved": fp64 / 1e12, "peak": probe["fp64_fma_per_s"] / 1e12, "frac": fp64 / probe["fp64_fma_per_s"],
+            "binding": "fp64", "lane_ops_per_cluster": FP64_PER_CLUSTER,
+            "peak_source": "measured live in this run: FP64 FMA chain probe (tpcfit_probe_fma_rates); the "
+                           "driver-measured peaks hold no FP64 figure",
+            "frac_of_nominal": fp64 / FP64_NOMINAL_OPS,
+            "traffic": c["dram_bytes"] if c else None, "traffic_note": note,
+            "fit_ms_avg": fit_s * 1e3, "beside": beside}
     return roof
 
 
@@ -228,7 +238,8 @@ def link_rates(nbytes: int = 1 << 30, reps: int = 3) -> dict:
 def cpu_baseline(frame, seconds_target: float = 15.0, workload: str = "pbpb2m", iterations: int = 0):
     """Time the FP64 oracle with every host core on a bounded sample of the
     frame: the whole frame when a 20k-track probe predicts <= ~2x the target,
-    else the first tracks sized for about `seconds_target` seconds."""
+    else the first tracks sized for about `seconds_target` seconds.  Returns
+    the baseline record and the oracle's fit of the sample (its first tracks)."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
@@ -246,7 +257,50 @@ def cpu_baseline(frame, seconds_target: float = 15.0, workload: str = "pbpb2m", 
     what = "the whole frame" if sub.n_tracks == frame.n_tracks else f"the first {sub.n_tracks} tracks of the frame"
     return {"value": sub.n_clusters / dt, "unit": "clusters/s", "cores": int(r["threads"]), "kind": "oracle",
             "sample": f"{what} ({sub.n_tracks} tracks, {sub.n_clusters} clusters), FP64 C oracle, {dt:.1f} s, "
-                      f"one pthread per host core", "tracks_per_s": sub.n_tracks / dt}
+                      f"one pthread per host core", "tracks_per_s": sub.n_tracks / dt}, r
+
+
+def parity_block(frame, gpu: dict, orc: dict, workload: str = "pbpb2m", iterations: int = 0) -> dict:
+    """The GPU fit of the benchmark frame against the FP64 oracle's fit of the
+    same tracks (the cpu_baseline run), element by element with the bars of
+    tests/parity.py.  Tracks whose accept flags differ are refitted by the
+    oracle with per-cluster chi2, so that flips within the gate window are
+    told apart from real mismatches."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from parity import GATE_WINDOW, TOL_CHI2, TOL_COV, TOL_STATE, compare
+    nt = orc["status"].shape[0]
+    a, e = int(frame.offsets[0]), int(frame.offsets[nt])
+    g = {k: np.asarray(gpu[k][:nt]) for k in ("state", "cov", "chi2", "ndf", "status")}
+    g["accept"] = np.asarray(gpu["accept"][a:e])
+    off = frame.offsets[:nt + 1] - a
+    rep = compare(off, g, orc)
+    cfg = oracle.FitConfig(iterations=iterations, **FIT_PARAMS.get(workload, ({}, {}))[1])
+    flips = list(rep.accept_mismatch)
+    rep.accept_mismatch = []
+    gate_excluded = rep.n_gate_excluded
+    for t in flips:
+        sub = frame.subset(t, t + 1)
+        o1 = oracle.fit(sub, cfg, diagnostics=True, threads=1)
+        ka, kb = int(off[t]), int(off[t + 1])
+        g1 = {k: g[k][t:t + 1] for k in ("state", "cov", "chi2", "ndf", "status")}
+        g1["accept"] = g["accept"][ka:kb]
+        r1 = compare(sub.offsets, g1, o1)
+        gate_excluded += r1.n_gate_excluded
+        if r1.accept_mismatch:
+            rep.accept_mismatch.append(t)
+    st, cnt = np.unique(g["status"], return_counts=True)
+    ok = (not rep.status_mismatch and not rep.accept_mismatch and rep.ndf_mismatch == 0
+          and rep.max_state < TOL_STATE and rep.max_cov < TOL_COV and rep.max_chi2 < TOL_CHI2)
+    return {"oracle": "FP64 C oracle fit of the same tracks in this run", "tracks": int(nt),
+            "compared": int(rep.n_compared),
+            "gate_excluded": int(gate_excluded), "status_mismatch": len(rep.status_mismatch),
+            "accept_mismatch": len(rep.accept_mismatch), "ndf_mismatch": int(rep.ndf_mismatch),
+            "max_state_over_sigma": rep.max_state, "max_cov_over_sqrt_diag": rep.max_cov,
+            "max_chi2_rel": rep.max_chi2,
+            "bars": {"state_over_sigma": TOL_STATE, "cov_over_sqrt_diag": TOL_COV, "chi2_rel": TOL_CHI2,
+                     "gate_window_rel": GATE_WINDOW},
+            "status_counts": {str(int(s)): int(c) for s, c in zip(st, cnt)}, "ok": bool(ok)}
 
 
 def run_reference(args, ws, rank):
@@ -275,7 +329,7 @@ def run_reference(args, ws, rank):
     dt = time.perf_counter() - t0
     value = frame.n_clusters * args.steps / dt
     line = {
-        "impl": "reference", "metric": "clusters/s fitted (FP64 oracle on host cores)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "clusters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -296,25 +350,31 @@ def gpu_index(local: int) -> int:
 
 
 def reduce_max(dist, torch, x: float) -> float:
-    if not dist:
-        return x
-    t = torch.tensor([x], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    """Max over the ranks (timing only; the data path has no collective)."""
+    from paper_2402_01205_gb300 import replicas
+    return replicas.max_over_ranks(x, device="cuda") if dist else x
 
 
 def reduce_sum(dist, torch, x: float) -> float:
-    if not dist:
-        return x
-    t = torch.tensor([x], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t)
-    return float(t.item())
+    from paper_2402_01205_gb300 import replicas
+    return replicas.sum_over_ranks(x, device="cuda") if dist else x
 
 
-def run_events(args, ws, rank, local, T, torch, dist, probe):
-    """Batched uneven events: the autotuned batch graph vs one launch per event."""
+def frame_seed(rank: int, ws: int) -> int:
+    """The seed of the frame this rank fits: one independent time frame per
+    rank, frames dealt round robin over the ranks (the paper's distribution of
+    time frames over GPUs without GPU intercommunication, Sec. 6)."""
+    from paper_2402_01205_gb300 import replicas
+    mine = replicas.shard_round_robin(ws, rank, ws)
+    return mine[0]
+
+
+def run_events(args, ws, rank, local, T, torch, dist, probe, leg: bool = False):
+    """Batched uneven events: the autotuned batch graph vs one launch per event.
+    As a leg of the default run (``leg``): fewer steps, no end-to-end or CPU
+    arm, and a compact record returned instead of a printed line."""
     from paper_2402_01205_gb300 import autotune
-    frame, ev = tpcgen.event_batch(n_events=args.n_events, seed=rank)
+    frame, ev = tpcgen.event_batch(n_events=args.n_events, seed=frame_seed(rank, ws))
     nt, nc = frame.n_tracks, frame.n_clusters
     names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
 
@@ -329,7 +389,7 @@ def run_events(args, ws, rank, local, T, torch, dist, probe):
     entry = autotune.lookup(table, props.name, props.multi_processor_count, nt)
     tuned_now = entry is None
     if tuned_now:
-        entry = autotune.tune(T, dev, reps=3, device=local)
+        entry = autotune.tune(T, dev, reps=1 if leg else 3, device=local)
         if args.tune_table and rank == 0:
             autotune.save(args.tune_table, autotune.table_key(props.name, props.multi_processor_count, nt), entry)
     cfg = autotune.config_for(entry)
@@ -395,6 +455,22 @@ def run_events(args, ws, rank, local, T, torch, dist, probe):
     fit_s = tm["fit_ms_sum"] / max(tm["n_timed"], 1) * 1e-3
     roofline = fit_roofline(nc, nt, nc_fit, fit_s, (tm["fit_grid"], tm["fit_block"]), probe,
                             props.multi_processor_count, clk.get("sm_mhz"))
+    if leg:
+        sizes = np.diff(ev)
+        out = {"workload": "events4096", "description": WORKLOADS["events4096"], "n_events": len(sizes),
+               "n_tracks": nt, "n_clusters": nc, "tracks_per_event_median": float(np.median(sizes)),
+               "batch": {"clusters_per_s": value, "tracks_per_s": nt_all * args.steps / (ms * 1e-3),
+                         "ms_per_step": ms / args.steps, "steps": args.steps,
+                         "launch": "tpcfit_batch graph replay (one captured launch sequence per step)"},
+               "per_event": {"clusters_per_s": nc_all * args.per_event_steps / (ms_pe * 1e-3),
+                             "ms_per_step": ms_pe / args.per_event_steps, "steps": args.per_event_steps,
+                             "launch": "tpcfit_fit_async per event, one stream"},
+               "speedup_of_batch": (ms_pe / args.per_event_steps) / (ms / args.steps),
+               "results_identical_to_batch": bool(same), "autotuned": cfg, "autotune_ms": entry["ms"],
+               "autotune_candidates": entry.get("all"), "fit_roofline_frac": roofline["frac"], "clocks": clk}
+        batch.close()
+        fx.close()
+        return out
     e2e = None
     if args.e2e_steps > 0:
         host = F()
@@ -418,7 +494,7 @@ def run_events(args, ws, rank, local, T, torch, dist, probe):
                "path": "tpcfit_fit of the concatenated events, TPCFIT_MEM_HOST pinned, chunked overlap"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(frame, workload=args.workload)
+        cpu, _ = cpu_baseline(frame, workload=args.workload)
     if rank == 0:
         sizes = np.diff(ev)
         line = {
@@ -482,8 +558,11 @@ def percentile(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
 
 
-def run_serving(args, ws, rank, local, T, torch, dist, probe):
-    """Served frames (tpcfit_submit/poll) vs sequential plain fits (tpcfit_fit)."""
+def run_serving(args, ws, rank, local, T, torch, dist, probe, leg: bool = False):
+    """Served frames (tpcfit_submit/poll) vs sequential plain fits (tpcfit_fit).
+    As a leg of the default run (``leg``): the Poisson window only (served,
+    then the same schedule as sequential plain fits), a compact record
+    returned instead of a printed line."""
     big, wins = serving_pool(rank, args.serve_pool)
     names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
 
@@ -580,10 +659,31 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe):
         out["h2d_floor_ms"] = 1e3 * (21 * f.n_clusters + 8 * f.n_tracks) / 211e9
         return out
 
-    by_size = sorted(range(len(frames)), key=lambda k: frames[k].n_clusters)
-    unloaded_lat = {"largest": unloaded(frames[by_size[-1]]), "median": unloaded(frames[by_size[len(by_size) // 2]])}
     ncl = np.array([frames[k].n_clusters for k in pick], dtype=np.float64)
     ntr = np.array([frames[k].n_tracks for k in pick], dtype=np.float64)
+
+    def summary(lat, span, cl, tr):
+        ms = [x * 1e3 for x in lat]
+        return {"p50_ms": percentile(ms, 50), "p90_ms": percentile(ms, 90), "p99_ms": percentile(ms, 99),
+                "p999_ms": percentile(ms, 99.9), "max_ms": max(ms),
+                "mean_ms": float(np.mean(ms)), "clusters_per_s": cl / span, "tracks_per_s": tr / span,
+                "frames": len(lat), "span_s": span}
+
+    if leg:
+        clocks = ClockSampler(gpu_index(local))
+        clocks.start()
+        lat_s, span_s = served(arrivals)
+        clk = clocks.stop()
+        lat_q, span_q = sequential(arrivals)
+        return {"workload": "serving", "description": WORKLOADS["serving"], "rate_hz": args.serve_rate,
+                "seconds": args.serve_seconds, "frames_submitted": n_req, "pool_frames": len(frames),
+                "clusters_per_frame_median": float(np.median(ncl)), "clusters_per_frame_max": float(ncl.max()),
+                "hbm_budget_bytes": budget, "max_slots": 8,
+                "latency": "arrival on the seeded schedule to results in pinned host memory",
+                "served": summary(lat_s, span_s, ncl.sum(), ntr.sum()),
+                "sequential_plain_fit": summary(lat_q, span_q, ncl.sum(), ntr.sum()), "clocks": clk}
+    by_size = sorted(range(len(frames)), key=lambda k: frames[k].n_clusters)
+    unloaded_lat = {"largest": unloaded(frames[by_size[-1]]), "median": unloaded(frames[by_size[len(by_size) // 2]])}
     if dist:
         dist.barrier()
     clocks = ClockSampler(gpu_index(local))
@@ -622,16 +722,9 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe):
     roofline["over"] = f"one device-resident fit of each of the {len(frames)} pool frames"
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(big)
+        cpu, _ = cpu_baseline(big)
     sustained = float(ncl.sum()) / span_s
     value = reduce_sum(dist, torch, sustained)
-
-    def summary(lat, span, cl, tr):
-        ms = [x * 1e3 for x in lat]
-        return {"p50_ms": percentile(ms, 50), "p90_ms": percentile(ms, 90), "p99_ms": percentile(ms, 99),
-                "p999_ms": percentile(ms, 99.9), "max_ms": max(ms),
-                "mean_ms": float(np.mean(ms)), "clusters_per_s": cl / span, "tracks_per_s": tr / span,
-                "frames": len(lat), "span_s": span}
 
     if rank == 0:
         line = {
@@ -803,6 +896,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: length of the arrival schedule")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="serving: frames/s")
     ap.add_argument("--serve-pool", type=int, default=64, help="serving: distinct frames in the replayed pool")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="pbpb2m: leave out the batched-events and serving legs of the default line")
+    ap.add_argument("--leg-serve-seconds", type=float, default=10.0, help="serving leg: length of the arrival schedule")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -826,7 +922,7 @@ def main():
     if args.workload == "tracking":
         return run_tracking(args, ws, rank, local, T, torch, dist, probe)
     kw = {} if args.n_tracks is None else {"n_tracks": args.n_tracks}
-    frame = tpcgen.generate(args.workload, seed=rank, **kw)
+    frame = tpcgen.generate(args.workload, seed=frame_seed(rank, ws), **kw)
     nt, nc = frame.n_tracks, frame.n_clusters
     names = ("offsets", "x", "y", "z", "sy2", "sz2", "row")
 
@@ -862,15 +958,8 @@ def main():
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     tm = fx.timing()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([float(nc)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tot)
-        nc_all = float(tot.item())
-    else:
-        nc_all = float(nc)
+    ms = reduce_max(dist, torch, ms)
+    nc_all = reduce_sum(dist, torch, float(nc))
     value = nc_all * args.steps / (ms * 1e-3)
     status = res["status"].cpu().numpy()
     ok = status == 0
@@ -936,6 +1025,27 @@ def main():
                  "median of %d calls per stream" % args.rans_steps}
         del outs, dec
     del res_r
+    # the two-filter smoother variant (per-cluster smoothed states, 80 B per cluster written)
+    smoother = None
+    if args.workload == "pbpb2m" and args.fit_iterations == 0:
+        res_s = T.alloc_result(nt, nc, device=torch.device("cuda", local), smoothed=True)
+        fx.fit_async(dev, res_s, stream=stream)
+        fx.sync()
+        fx.reset_timing()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_sm = 3
+        s0.record(stream)
+        for _ in range(n_sm):
+            fx.fit_async(dev, res_s, stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms_sm = reduce_max(dist, torch, s0.elapsed_time(s1))
+        tm_s = fx.timing()
+        smoother = {"value": nc_all * n_sm / (ms_sm * 1e-3), "unit": "clusters/s", "steps": n_sm,
+                    "ms_per_step": ms_sm / n_sm, "kernel_ms": tm_s["fit_ms_sum"] / max(tm_s["n_timed"], 1),
+                    "what": "two-filter smoother: forward predictions stored, backward filter, 5x5 combination at "
+                            "every cluster; smoothed state and covariance written per cluster (80 B)"}
+        del res_s
     # end to end through the C-ABI: pinned host frame in, pinned host results out
     e2e = None
     if args.e2e_steps > 0:
@@ -956,11 +1066,7 @@ def main():
             fx.fit(host, hres)
             _ = float(hres["chi2"][0])  # the step's result read on the host
             step_ms.append(round(1e3 * (time.perf_counter() - ts), 3))
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = reduce_max(dist, torch, time.perf_counter() - t0)
         h2d_b, d2h_b = int(21 * nc + 8 * (nt + 1)), int(100 * nt + nc)
         # the same frame without x: its clusters lie on the pad-row planes, and
         # the library derives x from the rows on the device (17 B per cluster copied)
@@ -994,12 +1100,25 @@ def main():
             "step_ms": nox_ms, "h2d_bytes_per_step": int(17 * nc + 8 * (nt + 1)), "d2h_bytes_per_step": d2h_b,
             "what": "the same frame passed without x (its clusters lie on the pad-row planes: x derived on the device "
                     "from the rows)", "results_identical_to_e2e": nox_same}
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(frame, workload=args.workload, iterations=args.fit_iterations)
+        gpu_host = {k: res[k].cpu().numpy() for k in ("state", "cov", "chi2", "ndf", "status", "accept")}
+        cpu, orc = cpu_baseline(frame, workload=args.workload, iterations=args.fit_iterations)
+        parity = parity_block(frame, gpu_host, orc, args.workload, args.fit_iterations)
+        del gpu_host, orc
+    # the other two workloads of the metric, shortened, on this GPU after the timed steps
+    legs = {}
+    if ws == 1 and not args.no_legs and args.workload == "pbpb2m":
+        import copy
+        la = copy.copy(args)
+        la.steps, la.warmup, la.per_event_steps, la.e2e_steps, la.n_events = 5, 2, 1, 0, 4096
+        la.serve_seconds, la.tune_table = args.leg_serve_seconds, None
+        legs["events4096"] = run_events(la, ws, rank, local, T, torch, None, probe, leg=True)
+        legs["serving"] = run_serving(la, ws, rank, local, T, torch, None, probe, leg=True)
     if rank == 0:
+        srv = legs.get("serving", {}).get("served", {})
         line = {
-            "metric": "clusters/s fitted on 1 GB300 (FP32 fit, FP64 innovation inverse and chi2)",
+            "metric": METRIC,
             "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
@@ -1009,8 +1128,17 @@ def main():
                        "parallelism": f"replicas x{ws}", "fit_grid": tm["fit_grid"], "fit_block": tm["fit_block"],
                        "fit_regs": tm["fit_regs"]},
             "tracks_per_s": nt * ws * args.steps / (ms * 1e-3),
+            "metrics": {"clusters_per_s": value, "tracks_per_s": nt * ws * args.steps / (ms * 1e-3),
+                        "oracle_error": None if parity is None else {
+                            k: parity[k] for k in ("max_state_over_sigma", "max_cov_over_sqrt_diag", "max_chi2_rel",
+                                                   "ok")},
+                        "p50_ms": srv.get("p50_ms"), "p99_ms": srv.get("p99_ms"),
+                        "latency_from": "the serving leg (Poisson arrivals, served frames)" if srv else None},
+            "parity": parity,
             "roofline": roofline,
+            "legs": legs or None,
             "with_residuals": with_residuals,
+            "smoother": smoother,
             "rans": codec,
             "cpu_baseline": cpu,
             "e2e": e2e,

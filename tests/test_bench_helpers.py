@@ -37,20 +37,25 @@ def test_roofline_fractions(monkeypatch):
         "test"))
     nc, nt, t = 1_000_000, 10_000, 1e-3
     r = bench.fit_roofline(nc, nt, nc, t, (304, 256), PROBE, 152, 2000.0)
-    assert r["bound"] == "alu" and r["peak"] == pytest.approx(4 * 152 * 2000e6 / 1e9)
-    assert r["achieved"] == pytest.approx(40.0 * nc / t / 1e9) and r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    alg = r["algorithmic"]
-    assert alg["fp64"]["frac"] == pytest.approx(bench.FP64_PER_CLUSTER * nc / t / 5.0e11)
-    assert alg["fp32"]["frac"] == pytest.approx(700.0 * nc / t / 8.0e13)
+    # the binding roof: FP64 lane-operations against the live FP64 FMA rate
+    assert r["bound"] == "alu" and r["binding"] == "fp64" and r["peak"] == pytest.approx(5.0e11 / 1e12)
+    assert r["achieved"] == pytest.approx(bench.FP64_PER_CLUSTER * nc / t / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["frac_of_nominal"] == pytest.approx(bench.FP64_PER_CLUSTER * nc / t / bench.FP64_NOMINAL_OPS)
+    side = r["beside"]
+    assert side["fp32"]["frac"] == pytest.approx(700.0 * nc / t / 8.0e13)
     peaks, _ = bench.measured_peaks()
-    assert alg["hbm"]["frac"] == pytest.approx((22 * nc + 108 * nt) / t / 1e9 / peaks["hbm_gbs"])
-    assert r["traffic"] == 64.0 * nc and r["active_lanes_per_inst"] == pytest.approx(28)
+    assert side["hbm"]["frac"] == pytest.approx((22 * nc + 108 * nt) / t / 1e9 / peaks["hbm_gbs"])
+    assert side["issue"]["peak_ginst_s"] == pytest.approx(4 * 152 * 2000e6 / 1e9)
+    assert side["issue"]["frac"] == pytest.approx(40.0 * nc / t / (4 * 152 * 2000e6))
+    assert r["traffic"] == 64.0 * nc and side["issue"]["active_lanes_per_inst"] == pytest.approx(28)
 
 
-def test_roofline_without_counters_falls_back_to_the_fp64_pipe(monkeypatch):
+def test_roofline_without_counters_keeps_the_fp64_roof(monkeypatch):
     monkeypatch.setattr(bench, "profiled_counters", lambda n, l, v="": (None, "no record"))
     r = bench.fit_roofline(1000, 10, 1000, 1e-6, (1, 1), PROBE, 152, None)
     assert "FP64" in r["unit"] and r["traffic"] is None and r["frac"] == pytest.approx(11 * 1000 / 1e-6 / 5e11)
+    assert "issue" not in r["beside"] and "fp32" not in r["beside"]
 
 
 def test_serving_pool_windows():
@@ -64,3 +69,12 @@ def test_serving_pool_windows():
         # the window holds the wanted clusters, up to one track, unless the pool ran out
         assert got >= min(c, off[-1] - off[t0]) and got - c < 400
     assert bench.percentile([1.0, 2.0, 3.0, 4.0], 50) == pytest.approx(2.5)
+
+
+def test_ranks_take_their_frames_from_the_replica_shards():
+    """Under torchrun each rank fits one independent frame, dealt round robin
+    by the replica helpers: distinct seeds, every rank one frame."""
+    for ws in (1, 2, 4, 8):
+        seeds = [bench.frame_seed(r, ws) for r in range(ws)]
+        assert sorted(seeds) == list(range(ws))
+    assert bench.reduce_max(None, None, 3.5) == 3.5 and bench.reduce_sum(None, None, 2.0) == 2.0
