@@ -73,20 +73,33 @@ __device__ __forceinline__ bool le_finite64(double x, uint32_t ghi, uint32_t glo
   return (int32_t)hi < (int32_t)ghi || (hi == ghi && lo <= glo);
 }
 
-// Error-free sum of two binary32 numbers (Knuth's TwoSum): a + b = s + e
-// exactly.  The error-free transformations use the _rn intrinsics, which the
-// compiler never contracts into a fused multiply-add: the proofs need each
-// sum and product rounded on its own.
+// ---------------------------------------------------------------------------
+// FP32 arithmetic of the fit, every operation rounded as written: vmul and
+// vadd are never contracted into a fused multiply-add (vfma is one), so the
+// error-free transformations below hold and the results do not depend on the
+// compiler's contraction choices.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Error-free sum of two binary32 numbers (Knuth's TwoSum): a + b = s + e exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  s = vadd(a, b);
+  const float bb = vsub(s, a);
+  e = vadd(vsub(a, vsub(s, bb)), vsub(b, bb));
 }
 // Dekker's Fast2Sum: the same when |a| >= |b| (a variance plus a smaller
 // increment, or minus a smaller decrement).
 __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
+  s = vadd(a, b);
+  e = vsub(b, vsub(s, a));
+}
+// Error-free product of two binary32 numbers: a * b = p + e exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = vmul(a, b);
+  e = vfma(a, b, -p);
 }
 
 // ---------------------------------------------------------------------------
@@ -114,102 +127,101 @@ struct Trk {
   __device__ __forceinline__ void clear_comp() { c9l = c14l = c5l = c12l = c3l = 0.f; }
   // the covariance with the compensation terms added in (binary32)
   __device__ __forceinline__ void fold_comp() {
-    c[3] += c3l;
-    c[5] += c5l;
-    c[9] += c9l;
-    c[12] += c12l;
-    c[14] += c14l;
+    c[3] = vadd(c[3], c3l);
+    c[5] = vadd(c[5], c5l);
+    c[9] = vadd(c[9], c9l);
+    c[12] = vadd(c[12], c12l);
+    c[14] = vadd(c[14], c14l);
     clear_comp();
   }
-  __device__ __forceinline__ float tl() const { return tl0 + dtl; }
-  __device__ __forceinline__ float w() const { return w0 + dw; }
-  __device__ __forceinline__ float snp() const { return sp + spl; }
+  __device__ __forceinline__ float tl() const { return vadd(tl0, dtl); }
+  __device__ __forceinline__ float w() const { return vadd(w0, dw); }
+  __device__ __forceinline__ float snp() const { return vadd(sp, spl); }
 };
 
 // Exact helix transport x1 -> x1+dx with Jacobian applied to the covariance.
-// Returns false on the |sinphi| limit (NaN passes).
+// Returns false on the |sinphi| limit (NaN passes), with T unchanged.
 __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_max) {
   const float tl = T.tl();
-  const float C = b * T.w();
-  const float s1 = T.snp(), s2 = fmaf(C, dx, s1);
+  const float C = vmul(b, T.w());
+  const float s1 = T.snp(), s2 = vfma(C, dx, s1);
   if (fabsf(s1) >= snp_max || fabsf(s2) >= snp_max) return false;
-  const float q1 = fmaf(-s1, s1, 1.0f), q2 = fmaf(-s2, s2, 1.0f);
+  const float q1 = vfma(-s1, s1, 1.0f), q2 = vfma(-s2, s2, 1.0f);
   const float ic1 = rsqrtf(q1), ic2 = rsqrtf(q2);
-  const float c1 = q1 * ic1, c2 = q2 * ic2;  // cos phi at both planes
-  const float iB = __fdividef(1.0f, c1 + c2);
-  const float Tn = (s1 + s2) * iB;           // tangent of the chord direction
-  const float kk2 = fmaf(Tn, Tn, 1.0f);
+  const float c1 = vmul(q1, ic1), c2 = vmul(q2, ic2);  // cos phi at both planes
+  const float iB = __fdividef(1.0f, vadd(c1, c2));
+  const float Tn = vmul(vadd(s1, s2), iB);             // tangent of the chord direction
+  const float kk2 = vfma(Tn, Tn, 1.0f);
   const float ik = rsqrtf(kk2);
-  const float L = dx * (kk2 * ik);           // signed chord
-  const float u = 0.5f * C * L;
-  const float u2 = u * u;
+  const float L = vmul(dx, vmul(kk2, ik));             // signed chord
+  const float u = vmul(vmul(0.5f, C), L);
+  const float u2 = vmul(u, u);
+  // arc / chord g = asin(u)/u and h = (g' / u) / 2 = (1/sqrt(1-u^2) - g) / (2 u^2):
+  // series for |u| < 0.1, else the functions themselves
   float g, h;
   if (fabsf(u) < 0.1f) {
-    g = 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
-    h = 1.0f / 6.0f + u2 * (3.0f / 20.0f + u2 * (15.0f / 112.0f + u2 * (35.0f / 288.0f)));
+    g = vfma(u2, vfma(u2, vfma(u2, 5.0f / 112.0f, 3.0f / 40.0f), 1.0f / 6.0f), 1.0f);
+    h = vfma(u2, vfma(u2, vfma(u2, 35.0f / 288.0f, 15.0f / 112.0f), 3.0f / 20.0f), 1.0f / 6.0f);
   } else {
     g = asinf(u) / u;
     h = (rsqrtf(1.0f - u2) - g) / (2.0f * u2);
   }
-  const float sT = L * g;                    // signed transverse arc length
-  T.dy = fmaf(dx, Tn, T.dy);
-  T.dz = fmaf(tl, sT, T.dz);
+  const float sT = vmul(L, g);                         // signed transverse arc length
+  T.dy = vfma(dx, Tn, T.dy);
+  T.dz = vfma(tl, sT, T.dz);
   {  // sinphi += C dx, compensated
     float hi, e;
-    two_sum(T.sp, C * dx, hi, e);
+    two_sum(T.sp, vmul(C, dx), hi, e);
     T.sp = hi;
-    T.spl += e;
+    T.spl = vadd(T.spl, e);
   }
   // Jacobian
-  const float Q = fmaf(c1, c2, fmaf(s1, s2, 1.0f)) * iB * iB;
-  const float dTds = Q * (ic1 + ic2);
-  const float bdx = b * dx;
-  const float dTdw = Q * ic2 * bdx;
-  const float Jys = dx * dTds, Jyw = dx * dTdw;
-  const float dsdL = rsqrtf(fmaf(-u, u, 1.0f));
-  const float dLdT = dx * Tn * ik;
-  const float dsdC = L * L * u * h;
-  const float a1 = dsdL * dLdT;
-  const float Jzs = tl * a1 * dTds;
+  const float Q = vmul(vmul(vfma(c1, c2, vfma(s1, s2, 1.0f)), iB), iB);
+  const float dTds = vmul(Q, vadd(ic1, ic2));
+  const float bdx = vmul(b, dx);
+  const float dTdw = vmul(vmul(Q, ic2), bdx);
+  const float Jys = vmul(dx, dTds), Jyw = vmul(dx, dTdw);
+  const float dsdL = rsqrtf(vfma(-u, u, 1.0f));
+  const float dLdT = vmul(vmul(dx, Tn), ik);
+  const float dsdC = vmul(vmul(vmul(L, L), u), h);
+  const float a1 = vmul(dsdL, dLdT);
+  const float Jzs = vmul(vmul(tl, a1), dTds);
   const float Jzt = sT;
-  const float Jzw = tl * fmaf(a1, dTdw, dsdC * b);
+  const float Jzw = vmul(tl, vfma(a1, dTdw, vmul(dsdC, b)));
   const float Jsw = bdx;
   float *c = T.c;
   // F C (rows 0..2 differ from C), entries needed by F C F^T
-  const float FC00 = fmaf(Jys, c[3], fmaf(Jyw, c[10], c[0]));
-  const float FC02 = fmaf(Jys, c[5], fmaf(Jyw, c[12], c[3]));
-  const float FC04 = fmaf(Jys, c[12], fmaf(Jyw, c[14], c[10]));
-  const float FC10 = fmaf(Jzs, c[3], fmaf(Jzt, c[6], fmaf(Jzw, c[10], c[1])));
-  const float FC11 = fmaf(Jzs, c[4], fmaf(Jzt, c[7], fmaf(Jzw, c[11], c[2])));
-  const float FC12 = fmaf(Jzs, c[5], fmaf(Jzt, c[8], fmaf(Jzw, c[12], c[4])));
-  const float FC13 = fmaf(Jzs, c[8], fmaf(Jzt, c[9], fmaf(Jzw, c[13], c[7])));
-  const float FC14 = fmaf(Jzs, c[12], fmaf(Jzt, c[13], fmaf(Jzw, c[14], c[11])));
-  const float FC20 = fmaf(Jsw, c[10], c[3]);
-  const float FC21 = fmaf(Jsw, c[11], c[4]);
-  const float FC22 = fmaf(Jsw, c[12], c[5]);
-  const float FC23 = fmaf(Jsw, c[13], c[8]);
-  const float FC24 = fmaf(Jsw, c[14], c[12]);
-  // (F C) F^T, lower triangle; rows 3 and 4 of F C equal those of C
-  const float n30 = fmaf(Jys, c[8], fmaf(Jyw, c[13], c[6]));
-  const float n31 = fmaf(Jzs, c[8], fmaf(Jzt, c[9], fmaf(Jzw, c[13], c[7])));
-  const float n32 = fmaf(Jsw, c[13], c[8]);
-  const float n40 = fmaf(Jys, c[12], fmaf(Jyw, c[14], c[10]));
-  const float n41 = fmaf(Jzs, c[12], fmaf(Jzt, c[13], fmaf(Jzw, c[14], c[11])));
+  const float FC00 = vfma(Jys, c[3], vfma(Jyw, c[10], c[0]));
+  const float FC02 = vfma(Jys, c[5], vfma(Jyw, c[12], c[3]));
+  const float FC04 = vfma(Jys, c[12], vfma(Jyw, c[14], c[10]));
+  const float FC10 = vfma(Jzs, c[3], vfma(Jzt, c[6], vfma(Jzw, c[10], c[1])));
+  const float FC11 = vfma(Jzs, c[4], vfma(Jzt, c[7], vfma(Jzw, c[11], c[2])));
+  const float FC12 = vfma(Jzs, c[5], vfma(Jzt, c[8], vfma(Jzw, c[12], c[4])));
+  const float FC13 = vfma(Jzs, c[8], vfma(Jzt, c[9], vfma(Jzw, c[13], c[7])));
+  const float FC14 = vfma(Jzs, c[12], vfma(Jzt, c[13], vfma(Jzw, c[14], c[11])));
+  const float FC21 = vfma(Jsw, c[11], c[4]);
+  const float FC22 = vfma(Jsw, c[12], c[5]);
+  const float FC23 = vfma(Jsw, c[13], c[8]);
+  const float FC24 = vfma(Jsw, c[14], c[12]);
+  // (F C) F^T, lower triangle; rows 3 and 4 of F C equal those of C, so
+  // entries (3,1), (4,0) and (4,1) are FC13, FC04 and FC14
+  const float n30 = vfma(Jys, c[8], vfma(Jyw, c[13], c[6]));
+  const float n32 = vfma(Jsw, c[13], c[8]);
   // compensated C_sw' = C_sw + Jsw C_ww and C_ss' = C_ss + Jsw (2 C_sw + Jsw C_ww)
-  const float dsw = Jsw * (c[14] + T.c14l);
-  const float dss = Jsw * fmaf(2.0f, c[12], dsw);
-  c[0] = fmaf(Jys, FC02, fmaf(Jyw, FC04, FC00));
-  c[1] = fmaf(Jys, FC12, fmaf(Jyw, FC14, FC10));
-  c[2] = fmaf(Jzs, FC12, fmaf(Jzt, FC13, fmaf(Jzw, FC14, FC11)));
-  two_sum(c[3], fmaf(Jys, FC22, fmaf(Jyw, FC24, fmaf(Jsw, c[10], T.c3l))), c[3], T.c3l);
-  c[4] = fmaf(Jzs, FC22, fmaf(Jzt, FC23, fmaf(Jzw, FC24, FC21)));
-  fast_two_sum(c[5], dss + T.c5l, c[5], T.c5l);  // a variance plus a smaller change
+  const float dsw = vmul(Jsw, vadd(c[14], T.c14l));
+  const float dss = vmul(Jsw, vfma(2.0f, c[12], dsw));
+  c[0] = vfma(Jys, FC02, vfma(Jyw, FC04, FC00));
+  c[1] = vfma(Jys, FC12, vfma(Jyw, FC14, FC10));
+  c[2] = vfma(Jzs, FC12, vfma(Jzt, FC13, vfma(Jzw, FC14, FC11)));
+  two_sum(c[3], vfma(Jys, FC22, vfma(Jyw, FC24, vfma(Jsw, c[10], T.c3l))), c[3], T.c3l);
+  c[4] = vfma(Jzs, FC22, vfma(Jzt, FC23, vfma(Jzw, FC24, FC21)));
+  fast_two_sum(c[5], vadd(dss, T.c5l), c[5], T.c5l);  // a variance plus a smaller change
   c[6] = n30;
-  c[7] = n31;
+  c[7] = FC13;
   c[8] = n32;
-  c[10] = n40;
-  c[11] = n41;
-  two_sum(c[12], dsw + T.c12l, c[12], T.c12l);
+  c[10] = FC04;
+  c[11] = FC14;
+  two_sum(c[12], vadd(dsw, T.c12l), c[12], T.c12l);
   // c[9], c[13], c[14] unchanged
   return true;
 }
@@ -217,18 +229,18 @@ __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_m
 // Highland multiple-scattering noise of one pad row.
 __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   const float s = T.snp(), t = T.tl(), w = T.w();
-  const float tt = fmaf(t, t, 1.0f);
-  const float cs2 = fmaf(-s, s, 1.0f);
+  const float tt = vfma(t, t, 1.0f);
+  const float cs2 = vfma(-s, s, 1.0f);
   const float itt = __fdividef(1.0f, tt);
-  const float pinv2 = w * w * itt;                  // 1/p^2
-  const float ib2 = fmaf(mass2, pinv2, 1.0f);       // 1/beta^2
-  const float eps = xx0 * (tt * rsqrtf(tt * cs2));  // xx0 sqrt(tt / cs2)
-  const float lg = fmaf(0.038f, __logf(eps * ib2), 1.0f);
-  const float th2 = (0.0136f * 0.0136f) * pinv2 * ib2 * eps * lg * lg;
-  fast_two_sum(T.c[5], fmaf(th2, cs2 * tt, T.c5l), T.c[5], T.c5l);
-  fast_two_sum(T.c[9], fmaf(th2, tt * tt, T.c9l), T.c[9], T.c9l);
-  fast_two_sum(T.c[14], fmaf(th2, w * w * t * t, T.c14l), T.c[14], T.c14l);
-  T.c[13] = fmaf(th2, tt * w * t, T.c[13]);
+  const float pinv2 = vmul(vmul(w, w), itt);                    // 1/p^2
+  const float ib2 = vfma(mass2, pinv2, 1.0f);                   // 1/beta^2
+  const float eps = vmul(xx0, vmul(tt, rsqrtf(vmul(tt, cs2))));  // xx0 sqrt(tt / cs2)
+  const float lg = vfma(0.038f, __logf(vmul(eps, ib2)), 1.0f);
+  const float th2 = vmul(vmul(vmul(vmul(vmul(0.0136f * 0.0136f, pinv2), ib2), eps), lg), lg);
+  fast_two_sum(T.c[5], vfma(th2, vmul(cs2, tt), T.c5l), T.c[5], T.c5l);
+  fast_two_sum(T.c[9], vfma(th2, vmul(tt, tt), T.c9l), T.c[9], T.c9l);
+  fast_two_sum(T.c[14], vfma(th2, vmul(vmul(vmul(w, w), t), t), T.c14l), T.c[14], T.c14l);
+  T.c[13] = vfma(th2, vmul(vmul(tt, w), t), T.c[13]);
 }
 
 // Mean stopping power (Bethe formula, PDG Review of Particle Physics, passage
@@ -289,12 +301,6 @@ __device__ __forceinline__ bool eloss(Trk &T, float xrho, float kza, float a_coe
   return true;
 }
 
-// Error-free product of two binary32 numbers: a * b = p + e exactly.
-__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-  p = __fmul_rn(a, b);
-  e = fmaf(a, b, -p);
-}
-
 // The quadratic form r^T adj(S) r = S11 r0^2 - 2 S10 r0 r1 + S00 r1^2 as an
 // unevaluated sum qh + ql of two binary32 numbers, from error-free products
 // and sums (the compensated dot product of Ogita, Rump and Oishi, 2005, in
@@ -304,18 +310,18 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
 // 31 binary32 operations cost less than the 5 binary64 ones they replace.
 __device__ __forceinline__ void quad_form2(float S00, float S10, float S11, float r0, float r1, float &qh,
                                            float &ql) {
-  float p1, e1, p2, e2, uh, ul, vh, t, tl, wh;
+  float p1, e1, p2, e2, uh, ul, t, tl;
   two_prod(S11, r0, p1, e1);
-  two_prod(-2.0f * S10, r1, p2, e2);  // -2 S10 exact
+  two_prod(vmul(-2.0f, S10), r1, p2, e2);  // -2 S10 exact
   two_sum(p1, p2, uh, ul);
-  ul += e1 + e2;                       // u = S11 r0 - 2 S10 r1 = uh + ul
-  vh = __fmul_rn(r0, uh);
-  const float vl = fmaf(r0, ul, fmaf(r0, uh, -vh));  // r0 u = vh + vl
+  ul = vadd(ul, vadd(e1, e2));             // u = S11 r0 - 2 S10 r1 = uh + ul
+  const float vh = vmul(r0, uh);
+  const float vl = vfma(r0, ul, vfma(r0, uh, -vh));  // r0 u = vh + vl
   two_prod(r1, r1, t, tl);
-  wh = __fmul_rn(S00, t);
-  const float wl = fmaf(S00, tl, fmaf(S00, t, -wh));  // S00 r1^2 = wh + wl
+  const float wh = vmul(S00, t);
+  const float wl = vfma(S00, tl, vfma(S00, t, -wh));  // S00 r1^2 = wh + wl
   two_sum(vh, wh, qh, ql);
-  ql += vl + wl;
+  ql = vadd(ql, vadd(vl, wl));
 }
 
 // Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: the
@@ -328,62 +334,57 @@ __device__ __forceinline__ void quad_form2(float S00, float S10, float S11, floa
 // determinant (narrowed to binary32 by integer operations), so that the
 // cancellation in det of a strongly correlated S does not reach the gain.
 // Non-finite innovation matrices or residuals give chi2 = NaN and a rejected
-// cluster, as in FP64.  Returns the status (OK / NOT_PD).
+// cluster, as in FP64.  Returns the status (OK, or NOT_PD with T unchanged).
 __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, double gate, uint32_t gate_hi,
                                       uint32_t gate_lo, bool want_chi2, bool &acc, double &chi2) {
   float *c = T.c;
-  const float r0 = (yc - T.ya) - T.dy;
-  const float r1 = (zc - T.za) - T.dz;
-  const float S00 = c[0] + vy, S10 = c[1], S11 = c[2] + vz;
+  const float r0 = vsub(vsub(yc, T.ya), T.dy);
+  const float r1 = vsub(vsub(zc, T.za), T.dz);
+  const float S00 = vadd(c[0], vy), S10 = c[1], S11 = vadd(c[2], vz);
   float qh, ql;
   quad_form2(S00, S10, S11, r0, r1, qh, ql);
-  const bool fin = fabsf((S00 + S11) + (S10 + qh)) < INFINITY;
+  const bool fin = fabsf(vadd(vadd(S00, S11), vadd(S10, qh))) < INFINITY;
   // ---- FP64 island ----
   const double s00 = widen_pos(S00), s11 = widen_pos(S11), s10 = widen(S10);
-  const double det = fma(s00, s11, -(s10 * s10));  // exact products of the binary32 S: rounded once
+  const double det = __fma_rn(s00, s11, -__dmul_rn(s10, s10));  // exact products of the binary32 S: rounded once
   // the gain's 1/det and the FP32 seed of the FP64 reciprocal, from the FP64 determinant
-  const float i32 = __fdividef(1.0f, narrow_pos_or(det, fmaf(S00, S11, -(S10 * S10))));
+  const float i32 = __fdividef(1.0f, narrow_pos_or(det, vfma(S00, S11, -vmul(S10, S10))));
   const double qhd = widen(qh), qld = widen(ql);
+  chi2 = 0.0;
   if (want_chi2) {
     const double y0 = widen_pos(i32);
-    const double ey = fma(-det, y0, 1.0);
-    const double inv = fma(y0, ey, y0);  // 1/det, one Newton step
-    chi2 = fma(qhd, inv, qld * inv);
+    const double ey = __fma_rn(-det, y0, 1.0);
+    const double inv = __fma_rn(y0, ey, y0);  // 1/det, one Newton step
+    chi2 = __fma_rn(qhd, inv, __dmul_rn(qld, inv));
     acc = le_finite64(chi2, gate_hi, gate_lo);
   } else {
-    acc = le0_finite64(fma(-gate, det, qhd) + qld);
+    acc = le0_finite64(__dadd_rn(__fma_rn(-gate, det, qhd), qld));
   }
-  const bool notpd = fin && (le0_finite64(det) || !(S00 > 0.0f) || !(S11 > 0.0f));
   // ---- back to FP32 ----
   if (!fin) {
     acc = false;
     chi2 = __longlong_as_double(0x7ff8000000000000ll);
   }
-  if (notpd) {
+  if (fin && (le0_finite64(det) || !(S00 > 0.0f) || !(S11 > 0.0f))) {
     acc = false;
     return ST_NOT_PD;
   }
-  const float Si00 = S11 * i32, Si10 = -S10 * i32, Si11 = S00 * i32;
   if (acc) {
+    const float Si00 = vmul(S11, i32), Si10 = vmul(-S10, i32), Si11 = vmul(S00, i32);
     float K0[5], K1[5];
     const int col0[5] = {0, 1, 3, 6, 10}, col1[5] = {1, 2, 4, 7, 11};
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       const float ci0 = c[col0[i]], ci1 = c[col1[i]];
-      K0[i] = fmaf(ci0, Si00, ci1 * Si10);
-      K1[i] = fmaf(ci0, Si10, ci1 * Si11);
+      K0[i] = vfma(ci0, Si00, vmul(ci1, Si10));
+      K1[i] = vfma(ci0, Si10, vmul(ci1, Si11));
     }
     // new position offsets relative to this cluster (the new anchor)
-    T.dy = fmaf(K0[0] - 1.0f, r0, K1[0] * r1);
-    T.dz = fmaf(K0[1], r0, (K1[1] - 1.0f) * r1);
-    {
-      float hi, e;
-      two_sum(T.sp, fmaf(K0[2], r0, fmaf(K1[2], r1, T.spl)), hi, e);
-      T.sp = hi;
-      T.spl = e;
-    }
-    T.dtl = fmaf(K0[3], r0, fmaf(K1[3], r1, T.dtl));
-    T.dw = fmaf(K0[4], r0, fmaf(K1[4], r1, T.dw));
+    T.dy = vfma(vsub(K0[0], 1.0f), r0, vmul(K1[0], r1));
+    T.dz = vfma(K0[1], r0, vmul(vsub(K1[1], 1.0f), r1));
+    two_sum(T.sp, vfma(K0[2], r0, vfma(K1[2], r1, T.spl)), T.sp, T.spl);
+    T.dtl = vfma(K0[3], r0, vfma(K1[3], r1, T.dtl));
+    T.dw = vfma(K0[4], r0, vfma(K1[4], r1, T.dw));
     // C -= K (H C).  For the measured columns (j = y, z) this equals K V
     // exactly (C_iH - C_iH S^-1 C_HH = C_iH S^-1 V), computed without
     // cancellation; the angle block uses the subtraction form.
@@ -396,16 +397,16 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
     T.c3l = 0.f;  // C'(2,0) below is a fresh product
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-      c[col0[i]] = K0[i] * vy;  // C'(i,0)
-      if (i >= 1) c[col1[i]] = K1[i] * vz;  // C'(i,1)
+      c[col0[i]] = vmul(K0[i], vy);  // C'(i,0)
+      if (i >= 1) c[col1[i]] = vmul(K1[i], vz);  // C'(i,1)
     }
-    fast_two_sum(c[5], T.c5l - fmaf(K0[2], h0[2], K1[2] * h1[2]), c[5], T.c5l);
-    c[8] = fmaf(-K0[3], h0[2], fmaf(-K1[3], h1[2], c[8]));
-    fast_two_sum(c[9], T.c9l - fmaf(K0[3], h0[3], K1[3] * h1[3]), c[9], T.c9l);
-    two_sum(c[12], T.c12l - fmaf(K0[4], h0[2], K1[4] * h1[2]), c[12], T.c12l);
-    c[13] = fmaf(-K0[4], h0[3], fmaf(-K1[4], h1[3], c[13]));
-    fast_two_sum(c[14], T.c14l - fmaf(K0[4], h0[4], K1[4] * h1[4]), c[14], T.c14l);
-  } else {
+    fast_two_sum(c[5], vsub(T.c5l, vfma(K0[2], h0[2], vmul(K1[2], h1[2]))), c[5], T.c5l);
+    c[8] = vfma(-K0[3], h0[2], vfma(-K1[3], h1[2], c[8]));
+    fast_two_sum(c[9], vsub(T.c9l, vfma(K0[3], h0[3], vmul(K1[3], h1[3]))), c[9], T.c9l);
+    two_sum(c[12], vsub(T.c12l, vfma(K0[4], h0[2], vmul(K1[4], h1[2]))), c[12], T.c12l);
+    c[13] = vfma(-K0[4], h0[3], vfma(-K1[4], h1[3], c[13]));
+    fast_two_sum(c[14], vsub(T.c14l, vfma(K0[4], h0[4], vmul(K1[4], h1[4]))), c[14], T.c14l);
+  } else {  // a rejected cluster still becomes the anchor: offsets to the predicted position
     T.dy = -r0;
     T.dz = -r1;
   }

@@ -51,14 +51,15 @@ constexpr int kStageArrays = 5;           // x, y, z, sy2, sz2
 // A completed fit whose (last) inward pass accepted fewer than this percentage
 // of the track's clusters lost the track for a stretch: status DERAILED.
 constexpr int kDerailPct = 80;
-// dynamic shared memory of k_fit: row table, outward accept bits, staged clusters
+// Dynamic shared memory of k_fit over NCOL track columns (threads x tracks
+// per lane): the row table, the staged chunks ([buf][array][column] 16-byte
+// entries), their row words ([buf][word][column]) and the outward accept bits
+// ([word][column]).
 constexpr size_t kSmemRowx = kMaxRows * sizeof(float);
-template <int BLOCK> __host__ __device__ constexpr size_t smem_bits() { return (size_t)(BLOCK / 32) * kBitWords * 32 * sizeof(uint32_t); }
-// staged floats [buf][array][slot][lane], then staged row words [buf][word][lane]
-constexpr int kStageFloats = kStageBufs * kStageArrays * kChunk;  // per lane
-constexpr int kStageRowWords = kStageBufs * 2;                    // per lane: two aligned words per buffer
-template <int BLOCK> __host__ __device__ constexpr size_t smem_stage() { return (size_t)(kStageFloats + kStageRowWords) * BLOCK * sizeof(float); }
-template <int BLOCK> __host__ __device__ constexpr size_t fit_smem() { return kSmemRowx + smem_bits<BLOCK>() + smem_stage<BLOCK>(); }
+template <int NCOL> __host__ __device__ constexpr size_t smem_f4() { return (size_t)kStageBufs * kStageArrays * NCOL * 16; }
+template <int NCOL> __host__ __device__ constexpr size_t fit_smem() {
+  return kSmemRowx + smem_f4<NCOL>() + (size_t)(kStageBufs * 2 + kBitWords) * NCOL * sizeof(uint32_t);
+}
 
 // 4-byte asynchronous global->shared copy (zero-fill when !valid; the source
 // address is then still a valid element and is not read).
@@ -154,69 +155,89 @@ __global__ void __launch_bounds__(256) k_sort_scatter(FitArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// k_fit: persistent warps over the (sorted) track list.
+// k_fit: persistent warps over the (sorted) track list, one or two tracks
+// per lane.
 // ---------------------------------------------------------------------------
 struct Clu {
   float x, y, z, vy, vz;
   int r;
 };
 
-// Issue the copies of chunk c (clusters a+4c .. a+4c+3, clipped to the track)
-// into buffer `buf` (= c % kStageBufs) of this lane's staging column.  The chunk's four row bytes
-// are copied as the two aligned 32-bit words that hold them (the second only
-// when it holds a byte of the track; an aligned word that holds a byte of an
-// allocation lies inside it, allocations being at least 4-byte granular).
-template <int BLOCK>
-__device__ __forceinline__ void stage_chunk(const FitArgs &A, int64_t a, int64_t e, int c, int buf, float *stg) {
-  const int64_t k0 = a + (int64_t)kChunk * c;
-  float *dst0 = stg + (buf * kStageArrays) * kChunk * BLOCK;
-  if (k0 + kChunk <= e) {  // full chunk: four consecutive clusters of each array
-    const float *src[kStageArrays] = {A.x + k0, A.y + k0, A.z + k0, A.sy2 + k0, A.sz2 + k0};
+// Staging of one track's clusters.  The clusters [a, a+n) are read in chunks
+// of four consecutive cluster indices aligned to the 16-byte boundaries of
+// the cluster arrays: chunk c holds clusters g0+4c .. g0+4c+3 with
+// g0 = a - lead, lead in [0, 3] (slots before a or past the track's end are
+// don't-care).  Shared memory holds, per track column, a ring of kStageBufs
+// chunk buffers: each array's four values of a chunk as one 16-byte entry
+// ([buf][array][column] float4), then the chunk's row bytes as the two
+// aligned 32-bit words that hold them ([buf][word][column]).
+// Clusters in chunk c: slot (k + lead) & 3 of chunk (k + lead) >> 2.
+__device__ __forceinline__ int chunk_lead(const FitArgs &A, int64_t a) {
+  return (int)(((uint64_t)a + (reinterpret_cast<uintptr_t>(A.x) >> 2)) & 3u);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Issue the copies of chunk c of the track [a, e) into buffer `buf` (= c %
+// kStageBufs) of its column; `f4` = the column's float4 entry of buffer 0,
+// array 0 (as floats), `w` = its row word of buffer 0, word 0; NCOL columns.
+// A chunk that lies inside the frame is copied as one 16-byte vector per
+// array when the five arrays share their 16-byte phase (A.stage_vec), else
+// cluster by cluster (only the track's own clusters, zero elsewhere).  A row
+// word is copied only when it holds a byte of the track: an aligned word that
+// holds a byte of an allocation lies inside it, allocations being at least
+// 4-byte granular.
+template <int NCOL>
+__device__ __forceinline__ void stage_chunk(const FitArgs &A, int64_t a, int64_t e, int lead, uint32_t rsh, int c,
+                                            int buf, float *f4, uint32_t *w) {
+  const int64_t k0 = a - lead + 4 * (int64_t)c;
+  float *dst = f4 + buf * (kStageArrays * NCOL * 4);
+  const float *src[kStageArrays] = {A.x, A.y, A.z, A.sy2, A.sz2};
+  if (A.stage_vec && k0 >= 0 && k0 + 4 <= A.n_clusters) {
 #pragma unroll
-    for (int j = 0; j < kStageArrays; ++j)
-#pragma unroll
-      for (int s = 0; s < kChunk; ++s) cp_async4(dst0 + (j * kChunk + s) * BLOCK, src[j] + s, true);
-  } else {  // the track's last chunk: slots past the end are zero-filled from an in-range address
+    for (int j = 0; j < kStageArrays; ++j) cp_async16(dst + j * (NCOL * 4), src[j] + k0);
+  } else {
 #pragma unroll
     for (int s = 0; s < kChunk; ++s) {
       const int64_t k = k0 + s;
-      const bool v = k < e;
-      const int64_t kk = v ? k : e - 1;
-      float *dst = dst0 + s * BLOCK;
-      cp_async4(dst + 0 * kChunk * BLOCK, A.x + kk, v);
-      cp_async4(dst + 1 * kChunk * BLOCK, A.y + kk, v);
-      cp_async4(dst + 2 * kChunk * BLOCK, A.z + kk, v);
-      cp_async4(dst + 3 * kChunk * BLOCK, A.sy2 + kk, v);
-      cp_async4(dst + 4 * kChunk * BLOCK, A.sz2 + kk, v);
+      const bool v = k >= a && k < e;
+      const int64_t kk = v ? k : a;
+#pragma unroll
+      for (int j = 0; j < kStageArrays; ++j) cp_async4(dst + j * (NCOL * 4) + s, src[j] + kk, v);
     }
   }
-  const uint8_t *p0 = A.row + k0;
-  const uint32_t *w0 = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(p0) & ~(uintptr_t)3);
-  const bool v1 = reinterpret_cast<const uint8_t *>(w0 + 1) < A.row + e;
-  float *rdst = stg + (kStageFloats + 2 * buf) * BLOCK;
-  cp_async4(rdst, w0, true);
-  cp_async4(rdst + BLOCK, v1 ? w0 + 1 : w0, v1);
+  const uintptr_t ra = reinterpret_cast<uintptr_t>(A.row) + (uintptr_t)a;   // the track's first row byte
+  const uintptr_t re = reinterpret_cast<uintptr_t>(A.row) + (uintptr_t)e;   // one past its last
+  const uintptr_t w0 = (reinterpret_cast<uintptr_t>(A.row) + (uintptr_t)k0) & ~(uintptr_t)3;
+  const uintptr_t wa = ra & ~(uintptr_t)3;  // a word that holds a byte of the track
+  const bool v0 = w0 + 4 > ra;              // w0 < re: the chunk holds a cluster of the track
+  const bool v1 = rsh != 0u && w0 + 4 < re;
+  uint32_t *wd = w + buf * (2 * NCOL);
+  cp_async4(wd, reinterpret_cast<const void *>(v0 ? w0 : wa), v0);
+  cp_async4(wd + NCOL, reinterpret_cast<const void *>(v1 ? w0 + 4 : wa), v1);
   cp_async_commit();
 }
 
-// Rows of the chunk staged in buffer `buf`, one byte per cluster; `rsh` is the
-// byte offset of the track's first row byte within its aligned word.
-template <int BLOCK>
-__device__ __forceinline__ uint32_t staged_rows(const float *stg, int buf, uint32_t rsh) {
-  const float *src = stg + (kStageFloats + 2 * buf) * BLOCK;
-  return __funnelshift_r(__float_as_uint(src[0]), __float_as_uint(src[BLOCK]), 8u * rsh);
+// Rows of the chunk staged in buffer `buf`, one byte per slot.
+template <int NCOL>
+__device__ __forceinline__ uint32_t staged_rows(const uint32_t *w, int buf, uint32_t rsh) {
+  const uint32_t *src = w + buf * (2 * NCOL);
+  return __funnelshift_r(src[0], src[NCOL], 8u * rsh);
 }
 
 // Cluster in `slot` of the chunk staged in buffer `buf` (whose rows are rows_cur).
-template <int BLOCK>
-__device__ __forceinline__ Clu read_staged(const float *stg, int slot, int buf, uint32_t rows_cur) {
-  const float *src = stg + ((buf * kStageArrays) * kChunk + slot) * BLOCK;
+template <int NCOL>
+__device__ __forceinline__ Clu read_staged(const float *f4, int slot, int buf, uint32_t rows_cur) {
+  const float *src = f4 + buf * (kStageArrays * NCOL * 4) + slot;
   Clu c;
   c.x = src[0];
-  c.y = src[kChunk * BLOCK];
-  c.z = src[2 * kChunk * BLOCK];
-  c.vy = src[3 * kChunk * BLOCK];
-  c.vz = src[4 * kChunk * BLOCK];
+  c.y = src[NCOL * 4];
+  c.z = src[2 * NCOL * 4];
+  c.vy = src[3 * NCOL * 4];
+  c.vz = src[4 * NCOL * 4];
   c.r = (rows_cur >> (8 * slot)) & 0xffu;
   return c;
 }
@@ -229,8 +250,12 @@ __device__ __forceinline__ bool state_finite(const Trk &T) {
   return fin;
 }
 
-template <int BLOCK, bool VAR>
-__device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *stg) {
+// Fit of track t by one lane: outward pass, restart, inward pass (and, in the
+// variant, energy loss and seed iterations).  NCOL = threads of the block: the
+// lane's staging and accept-bit columns are strided by it.
+template <int NCOL, bool VAR>
+__device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *f4,
+                          uint32_t *wrow) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
   const int st0 = A.status[t];
   const float *sd = A.seed + 5 * t;
@@ -266,19 +291,20 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
     }
     float xcur = xref;
 #pragma unroll
-    for (int w = 0; w < kBitWords; ++w) bits[32 * w] = 0u;
+    for (int w = 0; w < kBitWords; ++w) bits[NCOL * w] = 0u;
     uint8_t *const acc_t = A.accept + a;  // this track's accept bytes
     int done = 0;      // clusters (from the outer end) whose accept byte is final
     int out_done = 0;  // clusters the outward pass updated with
     if (st0 == ST_OK) {
       uint32_t gate_hi, gate_lo;
       split64(A.chi2_max_d, gate_hi, gate_lo);
-      const int nch = (n + kChunk - 1) / kChunk;
-      const uint32_t rsh = (uint32_t)(reinterpret_cast<uintptr_t>(A.row + a) & 3u);
+      const int lead = chunk_lead(A, a);
+      const uint32_t rsh = (uint32_t)((reinterpret_cast<uintptr_t>(A.row) + (uintptr_t)(a - lead)) & 3u);
+      const int nch = (lead + n + kChunk - 1) / kChunk;
       // passes: one outward + inward pair, or (the variant) 1 + n_iter of them
       for (int it = 0;; ++it) {
         int nacc_out = 0;
-        // candidate: the next cluster to use, read from the lane's staged chunks.
+        // candidate: the next cluster to use, read from the track's staged chunks.
         // The chunks sit in a ring of kStageBufs buffers; copies are issued and
         // waited for at warp-uniform steps, every kChunk rows of a pass (the
         // same rows for all lanes of a warp, whose tracks cross as many rows),
@@ -289,19 +315,19 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         int kc = 0;
         int staged = nch < kStageBufs ? nch : kStageBufs;  // outward: chunks 0 .. staged-1 issued
         if (it == 0)
-          for (int c = 0; c < staged; ++c) stage_chunk<BLOCK>(A, a, e, c, c, stg);
+          for (int c = 0; c < staged; ++c) stage_chunk<NCOL>(A, a, e, lead, rsh, c, c, f4, wrow);
         cp_async_wait_all();
         int cbuf = 0;  // buffer of the current chunk
-        uint32_t rows_cur = staged_rows<BLOCK>(stg, 0, rsh);
-        Clu cand = read_staged<BLOCK>(stg, 0, 0, rows_cur);
+        uint32_t rows_cur = staged_rows<NCOL>(wrow, 0, rsh);
+        Clu cand = read_staged<NCOL>(f4, lead, 0, rows_cur);
         int rprev = -1;
         st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
         // ---------------- outward pass: rows row[0] .. row[n-1] ----------------
         for (int r = cand.r, step = 0; st == ST_OK; ++r, ++step) {
           if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
             cp_async_wait_all();
-            if (staged < nch && staged <= kc / kChunk + 2) {  // the buffer of chunk staged-3 is consumed
-              stage_chunk<BLOCK>(A, a, e, staged, staged % kStageBufs, stg);
+            if (staged < nch && staged <= ((kc + lead) >> 2) + 2) {  // the buffer of chunk staged-3 is consumed
+              stage_chunk<NCOL>(A, a, e, lead, rsh, staged, staged % kStageBufs, f4, wrow);
               ++staged;
             }
           }
@@ -315,17 +341,18 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo,
                                    A.chi2_out_c != nullptr, acc, chi2);
             if (ust != ST_OK) { st = ust; break; }
-            if (acc) bits[32 * (kc >> 5)] |= 1u << (kc & 31);
+            if (acc) bits[NCOL * (kc >> 5)] |= 1u << (kc & 31);
             if (A.chi2_out_c) A.chi2_out_c[a + kc] = chi2;
             ++out_done;
             nacc_out += acc ? 1 : 0;
             rprev = cand.r;
             if (++kc < n) {
-              if (kc % kChunk == 0) {  // entering chunk kc/4 (arrived)
+              const int p = kc + lead;
+              if ((p & 3) == 0) {  // entering chunk p/4 (arrived)
                 cbuf = cbuf == kStageBufs - 1 ? 0 : cbuf + 1;
-                rows_cur = staged_rows<BLOCK>(stg, cbuf, rsh);
+                rows_cur = staged_rows<NCOL>(wrow, cbuf, rsh);
               }
-              cand = read_staged<BLOCK>(stg, kc % kChunk, cbuf, rows_cur);
+              cand = read_staged<NCOL>(f4, p & 3, cbuf, rows_cur);
               const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
               if (vs != ST_OK) { st = vs; break; }
             }
@@ -396,9 +423,9 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           for (int r = cand.r, step = 0;; --r, ++step) {
             if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
               cp_async_wait_all();
-              if (lowest > 0 && lowest + 1 >= kc / kChunk) {  // the buffer of chunk lowest+2 is consumed
+              if (lowest > 0 && lowest + 1 >= ((kc + lead) >> 2)) {  // the buffer of chunk lowest+2 is consumed
                 --lowest;
-                stage_chunk<BLOCK>(A, a, e, lowest, lowest % kStageBufs, stg);
+                stage_chunk<NCOL>(A, a, e, lead, rsh, lowest, lowest % kStageBufs, f4, wrow);
               }
             }
             const bool has = (cand.r == r);
@@ -419,15 +446,16 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
               if (A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;
               chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
               nacc += acc ? 1 : 0;
-              const uint32_t ob = (bits[32 * (kc >> 5)] >> (kc & 31)) & 1u;
+              const uint32_t ob = (bits[NCOL * (kc >> 5)] >> (kc & 31)) & 1u;
               acc_t[kc] = (uint8_t)(ob | (acc ? 2u : 0u));
               ++done;
               if (--kc >= 0) {
-                if (kc % kChunk == kChunk - 1) {  // entering chunk kc/4 from above (arrived)
+                const int p = kc + lead;
+                if ((p & 3) == 3) {  // entering chunk p/4 from above (arrived)
                   cbuf = cbuf == 0 ? kStageBufs - 1 : cbuf - 1;
-                  rows_cur = staged_rows<BLOCK>(stg, cbuf, rsh);
+                  rows_cur = staged_rows<NCOL>(wrow, cbuf, rsh);
                 }
-                cand = read_staged<BLOCK>(stg, kc % kChunk, cbuf, rows_cur);
+                cand = read_staged<NCOL>(f4, p & 3, cbuf, rows_cur);
               }
             }
             if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
@@ -451,7 +479,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         T.c[14] = A.seed_cov[4];
         T.clear_comp();
 #pragma unroll
-        for (int w = 0; w < kBitWords; ++w) bits[32 * w] = 0u;
+        for (int w = 0; w < kBitWords; ++w) bits[NCOL * w] = 0u;
         done = 0;
         out_done = 0;
         chi2sum = 0.0;
@@ -464,7 +492,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
     // accept bytes not written by the inward pass (failed or unfitted tracks): outward bits only
     for (int64_t k = a; k < e - done; ++k) {
       const int lk = (int)(k - a);
-      A.accept[k] = (lk < kMaxRows) ? (uint8_t)((bits[32 * (lk >> 5)] >> (lk & 31)) & 1u) : (uint8_t)0;
+      A.accept[k] = (lk < kMaxRows) ? (uint8_t)((bits[NCOL * (lk >> 5)] >> (lk & 31)) & 1u) : (uint8_t)0;
     }
     if (A.chi2_in_c)
       for (int64_t k = a; k < e - done; ++k) A.chi2_in_c[k] = __longlong_as_double(0x7ff8000000000000ll);
@@ -494,13 +522,12 @@ template <int BLOCK, int MINB, bool VAR>
 __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   float *s_rowx = reinterpret_cast<float *>(smem);
-  uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + kSmemRowx);
-  float *s_stage = reinterpret_cast<float *>(smem + kSmemRowx + smem_bits<BLOCK>());
+  float *s_f4 = reinterpret_cast<float *>(smem + kSmemRowx);
+  uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + kSmemRowx + smem_f4<BLOCK>());
+  uint32_t *s_bits = s_w + kStageBufs * 2 * BLOCK;
   for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) s_rowx[i] = A.row_x[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint32_t *bits = s_bits + wib * kBitWords * 32 + lane;  // word w of this lane at bits[32*w]
-  float *stg = s_stage + threadIdx.x;                      // this lane's staging column
+  const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(A.work, 32ull);
@@ -509,7 +536,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
     const int64_t i = (int64_t)base + lane;
     if (i < A.n_tracks) {
       const int64_t t = A.perm ? (int64_t)A.perm[i] : i;
-      fit_track<BLOCK, VAR>(A, t, bits, s_rowx, stg);
+      fit_track<BLOCK, VAR>(A, t, s_bits + threadIdx.x, s_rowx, s_f4 + 4 * threadIdx.x, s_w + threadIdx.x);
     }
     __syncwarp();
   }
@@ -557,12 +584,28 @@ template <int BLOCK, int MINB, bool VAR> static cudaError_t launch_fit_as(const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream) {
-  if (a.n_tracks <= 0) return cudaSuccess;
-  const bool el = a.xrho > 0.0f || a.n_iter > 0;  // the variant
-  if (block == 128)
-    return el ? launch_fit_as<128, 4, true>(a, grid, stream) : launch_fit_as<128, 4, false>(a, grid, stream);
-  return el ? launch_fit_as<256, 2, true>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
+// The five cluster arrays share their position within 16-byte lines: whole
+// aligned chunks are then staged as one 16-byte copy per array.
+static bool same_16b_phase(const FitArgs &a) {
+  const uintptr_t p = reinterpret_cast<uintptr_t>(a.x) & 15u;
+  return (reinterpret_cast<uintptr_t>(a.y) & 15u) == p && (reinterpret_cast<uintptr_t>(a.z) & 15u) == p &&
+         (reinterpret_cast<uintptr_t>(a.sy2) & 15u) == p && (reinterpret_cast<uintptr_t>(a.sz2) & 15u) == p;
+}
+
+static bool fit_variant(const FitArgs &a) { return a.xrho > 0.0f || a.n_iter > 0; }
+
+cudaError_t fit_set_attributes(const FitArgs &a, int block) {
+  if (fit_variant(a)) return block == 128 ? set_fit_smem<128, 4, true>() : set_fit_smem<256, 2, true>();
+  return block == 128 ? set_fit_smem<128, 4, false>() : set_fit_smem<256, 2, false>();
+}
+
+cudaError_t launch_fit(const FitArgs &a_in, int grid, int block, cudaStream_t stream) {
+  if (a_in.n_tracks <= 0) return cudaSuccess;
+  FitArgs a = a_in;
+  a.stage_vec = same_16b_phase(a) ? 1 : 0;
+  if (fit_variant(a))
+    return block == 128 ? launch_fit_as<128, 4, true>(a, grid, stream) : launch_fit_as<256, 2, true>(a, grid, stream);
+  return block == 128 ? launch_fit_as<128, 4, false>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
 }
 
 // Occupancy of the fit without energy loss (the variant is compiled under the

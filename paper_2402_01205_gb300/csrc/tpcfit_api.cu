@@ -612,8 +612,8 @@ extern "C" int tpcfit_batch_create(tpcfit_handle *h, const tpcfit_frame *f, tpcf
     return bail(fail(TPCFIT_E_CUDA, "batch stream, event or pinned word"));
   *b->h_err = 0;
   // set the kernel attributes before capture (no such calls inside it)
-  fit_blocks_per_sm(h->fit_block);
   FitArgs a = make_args(h, f, r, b->scratch, 0);
+  if (fit_set_attributes(a, h->fit_block) != cudaSuccess) return bail(fail(TPCFIT_E_CUDA, "fit kernel attributes"));
   const int sgrid = a.sm_state ? smooth_grid() : 0;
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bail(fail(TPCFIT_E_CUDA, "begin capture: %s", cudaGetErrorString(e)));

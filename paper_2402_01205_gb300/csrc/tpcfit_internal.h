@@ -47,6 +47,7 @@ struct FitArgs {
   int32_t reseed_pct;            // inward re-seed below this outward acceptance (percent)
   float seed_cov[5];
   int32_t min_clusters, n_rows;
+  int32_t stage_vec;             // set by launch_fit: cluster arrays share their 16-byte phase
 };
 
 // Host-to-device copies of the clusters [c0, c1) of a host frame into staging
@@ -56,8 +57,13 @@ struct FitArgs {
 // n_clusters): copies off those boundaries run well below the link rate (on
 // GB300: a 4 GB frame in 12 chunks took 20.8 ms unaligned against 19.4 ms
 // aligned; one copy: 19.2 ms).  `view` receives the staging arrays advanced to
-// cluster c0 (n_clusters = c1 - c0).  Returns the first failing CUDA error.
-constexpr int64_t kCopyPad = 256;  // elements: a 256-byte boundary lies within 256 elements of any address
+// cluster c0 (n_clusters = c1 - c0); each 4-byte array's copy lands up to 3
+// elements further into its staging array, so that cluster c0 of every one of
+// them sits at the start of a 16-byte line (the fit then stages whole chunks
+// as 16-byte copies).  Returns the first failing CUDA error.
+// Elements: a 256-byte boundary lies within 256 elements of any address, and
+// 3 more align the 4-byte arrays.
+constexpr int64_t kCopyPad = 260;
 
 struct ClusterArrays {
   float *x, *y, *z, *sy2, *sz2;
@@ -83,34 +89,38 @@ inline cudaError_t copy_clusters_in(const tpcfit_frame &f, int64_t c0, int64_t c
                                     XFill *fill = nullptr) {
   cudaError_t err = cudaSuccess;
   int64_t row_a0 = c0, row_n = 0;
+  // elements to skip at the start of a 4-byte staging array so that cluster c0 lands on a 16-byte line
+  auto shift4 = [&](int64_t first) -> int64_t { return (4 - ((c0 - first) & 3)) & 3; };
   auto one = [&](const void *src, void *dst, size_t elem) -> const void * {
     const uintptr_t base = reinterpret_cast<uintptr_t>(src);
     int64_t a0 = c0 - (int64_t)(((base + (uintptr_t)c0 * elem) & 255u) / elem);
     if (a0 < 0) a0 = 0;
     int64_t a1 = c1 + (int64_t)(((256u - ((base + (uintptr_t)c1 * elem) & 255u)) & 255u) / elem);
     if (a1 > f.n_clusters) a1 = f.n_clusters;
+    char *d = static_cast<char *>(dst) + (elem == 4 ? shift4(a0) * 4 : 0);
     if (c1 > c0 && err == cudaSuccess)
-      err = cudaMemcpyAsync(dst, static_cast<const char *>(src) + a0 * (int64_t)elem, (size_t)(a1 - a0) * elem,
+      err = cudaMemcpyAsync(d, static_cast<const char *>(src) + a0 * (int64_t)elem, (size_t)(a1 - a0) * elem,
                             cudaMemcpyHostToDevice, st);
     if (elem == 1) {
       row_a0 = a0;
       row_n = a1 - a0;
     }
-    return static_cast<const char *>(dst) + (c0 - a0) * (int64_t)elem;
+    return d + (c0 - a0) * (int64_t)elem;
   };
   view.row = static_cast<const uint8_t *>(one(f.row, stage.row, 1));
   if (f.x) {
     view.x = static_cast<const float *>(one(f.x, stage.x, 4));
   } else {
     const int64_t n_fill = c1 > c0 ? row_n : 0;
+    float *xd = stage.x + shift4(row_a0);  // x[k] beside row[k] of the staged rows
     if (fill) {
       fill->row = stage.row;
       fill->n = n_fill;
-      fill->x = stage.x;
+      fill->x = xd;
     } else if (n_fill > 0 && err == cudaSuccess) {
-      err = launch_x_from_rows(stage.row, n_fill, row_x, stage.x, st);
+      err = launch_x_from_rows(stage.row, n_fill, row_x, xd, st);
     }
-    view.x = stage.x + (c0 - row_a0);
+    view.x = xd + (c0 - row_a0);
   }
   view.y = static_cast<const float *>(one(f.y, stage.y, 4));
   view.z = static_cast<const float *>(one(f.z, stage.z, 4));
@@ -200,7 +210,11 @@ int set_error_message(int code, const char *msg);
 // of its launch.
 cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream);
 cudaError_t launch_sort(const FitArgs &a, cudaStream_t stream, int *launches);
+// The fit kernel on `grid` persistent blocks of `block` threads (128 or 256).
 cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t stream);
+// Set the shared-memory attribute of the instantiation launch_fit takes for
+// these arguments (before a stream capture: no such call inside it).
+cudaError_t fit_set_attributes(const FitArgs &a, int block);
 // the two-filter smoother variant in place of the fit (a.sm_state, a.sm_cov set),
 // on a persistent grid of smooth_grid() blocks (0 if the device cannot be queried)
 int smooth_grid();
