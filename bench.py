@@ -620,7 +620,9 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe, leg: bool = False)
                 st, td = fx.wait(tk)
                 assert st == T.DONE, st
                 lat[j], t_done[j] = td - (t0 + arr[j]), td
-        return lat, max(t_done) - (t0 + arr[0])
+            eng = fx.serve_stats()
+        eng["parts_per_launch_mean"] = eng["parts"] / max(eng["launches"], 1)
+        return lat, max(t_done) - (t0 + arr[0]), eng
 
     def sequential(arr):
         lat, t_end = [None] * len(arr), 0.0
@@ -672,7 +674,7 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe, leg: bool = False)
     if leg:
         clocks = ClockSampler(gpu_index(local))
         clocks.start()
-        lat_s, span_s = served(arrivals)
+        lat_s, span_s, eng = served(arrivals)
         clk = clocks.stop()
         lat_q, span_q = sequential(arrivals)
         return {"workload": "serving", "description": WORKLOADS["serving"], "rate_hz": args.serve_rate,
@@ -680,7 +682,7 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe, leg: bool = False)
                 "clusters_per_frame_median": float(np.median(ncl)), "clusters_per_frame_max": float(ncl.max()),
                 "hbm_budget_bytes": budget, "max_slots": 8,
                 "latency": "arrival on the seeded schedule to results in pinned host memory",
-                "served": summary(lat_s, span_s, ncl.sum(), ntr.sum()),
+                "served": dict(summary(lat_s, span_s, ncl.sum(), ntr.sum()), engine=eng),
                 "sequential_plain_fit": summary(lat_q, span_q, ncl.sum(), ntr.sum()), "clocks": clk}
     by_size = sorted(range(len(frames)), key=lambda k: frames[k].n_clusters)
     unloaded_lat = {"largest": unloaded(frames[by_size[-1]]), "median": unloaded(frames[by_size[len(by_size) // 2]])}
@@ -688,13 +690,13 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe, leg: bool = False)
         dist.barrier()
     clocks = ClockSampler(gpu_index(local))
     clocks.start()
-    lat_s, span_s = served(arrivals)
+    lat_s, span_s, eng = served(arrivals)
     clk = clocks.stop()
     lat_q, span_q = sequential(arrivals)
     # capacity: every frame of the schedule due at once
     n_cap = min(n_req, 4 * len(frames))
     zero = np.zeros(n_cap)
-    lat_cs, span_cs = served(zero)
+    lat_cs, span_cs, eng_cap = served(zero)
     lat_cq, span_cq = sequential(zero)
     cap_cl = float(ncl[:n_cap].sum())
     # device-only fit time of each pool frame, resident in HBM
@@ -739,10 +741,10 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe, leg: bool = False)
                        "hbm_budget_bytes": budget, "max_slots": 8, "result_ring": len(ring),
                        "l2": "frames of 1-120 M clusters, copied in per request; no flush",
                        "parallelism": f"replicas x{ws}"},
-            "latency": {"served": summary(lat_s, span_s, ncl.sum(), ntr.sum()),
+            "latency": {"served": dict(summary(lat_s, span_s, ncl.sum(), ntr.sum()), engine=eng),
                         "sequential_plain_fit": summary(lat_q, span_q, ncl.sum(), ntr.sum())},
             "capacity": {"frames": n_cap,
-                         "served": summary(lat_cs, span_cs, cap_cl, float(ntr[:n_cap].sum())),
+                         "served": dict(summary(lat_cs, span_cs, cap_cl, float(ntr[:n_cap].sum())), engine=eng_cap),
                          "sequential_plain_fit": summary(lat_cq, span_cq, cap_cl, float(ntr[:n_cap].sum()))},
             "unloaded_latency": unloaded_lat,
             "device_only_fit_ms": {"p50": percentile(dev_ms, 50), "p99": percentile(dev_ms, 99),

@@ -258,8 +258,9 @@ int tpcfit_batch_destroy(tpcfit_batch *b);
 
 /* Serving (Sec. 4 horizontal parallelism, Sec. 7 rate limiting by frames in
  * flight): copy a host frame into a library-owned resident slot when the HBM
- * budget and a slot allow, fit it overlapped with frames already on the
- * device, and copy the results into *res (host memory).  Returns at once with
+ * budget and a slot allow, fit it together with the frames already on the
+ * device (one engine launch over all of them, see tpcfit_get_serve_stats), and
+ * copy the results into *res (host memory).  Returns at once with
  * a ticket; a frame larger than the whole budget fails with TPCFIT_E_NOMEM.
  * *frame's and *res's buffers must stay valid until the ticket is DONE or
  * FAILED. */
@@ -269,6 +270,20 @@ int tpcfit_submit(tpcfit_handle *h, const tpcfit_frame *frame, tpcfit_result *re
  * done the completion time in seconds on the library's monotonic clock
  * (tpcfit_now).  A finished ticket is forgotten after it is reported. */
 int tpcfit_poll(tpcfit_handle *h, uint64_t ticket, int *state, double *t_done_s);
+
+/* Counters of the serving engine since serving started on the handle (all
+ * zero before the first tpcfit_submit).  The engine fits every part of the
+ * resident frames that is ready (copied in, checked, seeded and sorted) in
+ * one persistent launch, whose warps take (part, 32-track group) descriptors
+ * from a device table; a part's results are copied back as soon as its last
+ * group is fitted.  launches: engine launches; parts: parts they fitted;
+ * max_parts_per_launch: the most parts one launch fitted. */
+typedef struct tpcfit_serve_stats {
+  int64_t launches, parts, max_parts_per_launch;
+} tpcfit_serve_stats;
+
+/* Fill *out (TPCFIT_E_INVAL if h or out is NULL). */
+int tpcfit_get_serve_stats(tpcfit_handle *h, tpcfit_serve_stats *out);
 
 /* Block until a ticket finishes (bounded by timeout_s; < 0 = no bound). */
 int tpcfit_wait(tpcfit_handle *h, uint64_t ticket, double timeout_s, int *state, double *t_done_s);

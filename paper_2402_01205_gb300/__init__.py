@@ -69,6 +69,10 @@ class _Result(ctypes.Structure):
                 ("res_z", ctypes.c_void_p), ("smoothed_state", ctypes.c_void_p), ("smoothed_cov", ctypes.c_void_p)]
 
 
+class _ServeStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("parts", ctypes.c_int64), ("max_parts_per_launch", ctypes.c_int64)]
+
+
 class _Timing(ctypes.Structure):
     _fields_ = [("prepare_ms", ctypes.c_float), ("sort_ms", ctypes.c_float), ("fit_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int32), ("fit_grid", ctypes.c_int32),
@@ -125,6 +129,7 @@ def _load():
     lib.tpcfit_wait.argtypes = [H, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_double)]
     lib.tpcfit_last_timing.argtypes = [H, ctypes.POINTER(_Timing)]
+    lib.tpcfit_get_serve_stats.argtypes = [H, ctypes.POINTER(_ServeStats)]
     lib.tpcfit_reset_timing.argtypes = [H]
     lib.tpcfit_probe_fma_rates.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
@@ -157,7 +162,7 @@ def _load():
     lib.tpcfit_batch_sync.argtypes = [H, ctypes.c_double]
     lib.tpcfit_batch_destroy.argtypes = [H]
     for fn in ("tpcfit_create", "tpcfit_fit", "tpcfit_fit_async", "tpcfit_sync", "tpcfit_submit", "tpcfit_poll",
-               "tpcfit_wait", "tpcfit_last_timing", "tpcfit_reset_timing", "tpcfit_destroy",
+               "tpcfit_wait", "tpcfit_last_timing", "tpcfit_reset_timing", "tpcfit_destroy", "tpcfit_get_serve_stats",
                "tpcfit_probe_fma_rates", "tpcfit_batch_create", "tpcfit_batch_launch", "tpcfit_batch_sync",
                "tpcfit_batch_destroy", "tpcfit_rans_encode", "tpcfit_rans_decode"):
         getattr(lib, fn).restype = ctypes.c_int
@@ -366,6 +371,12 @@ def wait(handle: int, ticket: int, timeout_s: float = -1.0) -> tuple:
     st, td = ctypes.c_int(), ctypes.c_double()
     _check(_load().tpcfit_wait(handle, ticket, timeout_s, ctypes.byref(st), ctypes.byref(td)))
     return st.value, td.value
+
+
+def serve_stats(handle: int) -> dict:
+    s = _ServeStats()
+    _check(_load().tpcfit_get_serve_stats(handle, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in _ServeStats._fields_}
 
 
 def last_timing(handle: int) -> dict:
@@ -655,6 +666,10 @@ class Fitter:
 
     def timing(self) -> dict:
         return last_timing(self.handle)
+
+    def serve_stats(self) -> dict:
+        """Serving engine counters: launches, parts fitted, most parts in one launch."""
+        return serve_stats(self.handle)
 
     def follow(self, hits, seeds: dict, config: Optional[FollowConfig] = None, stream=None) -> dict:
         return follow(self.handle, hits, seeds, config, stream, n_rows=self.config.n_rows)

@@ -543,6 +543,66 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// k_fit_parts: one persistent launch over the resident parts of several time
+// frames (the serving engine).  The track groups of all parts -- 32
+// consecutive tracks of a part's sorted order -- form one range, part p's
+// being [prefix[p], prefix[p+1]); each warp claims the next group with an
+// atomic cursor, fits it with the part's arguments (copied into the warp's
+// shared-memory slot when the part changes), and counts the part's remaining
+// groups down.  The warp that fits a part's last group makes the part's
+// results visible system-wide and sets the part's flag in host-mapped memory,
+// so the host copies that part's results back while the launch still fits
+// the others.
+// ---------------------------------------------------------------------------
+template <int BLOCK, int MINB, bool VAR>
+__global__ void __launch_bounds__(BLOCK, MINB) k_fit_parts(PartsArgs P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *s_rowx = reinterpret_cast<float *>(smem);
+  float *s_f4 = reinterpret_cast<float *>(smem + kSmemRowx);
+  uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + kSmemRowx + smem_f4<BLOCK>());
+  uint32_t *s_bits = s_w + kStageBufs * 2 * BLOCK;
+  FitArgs *s_args = reinterpret_cast<FitArgs *>(smem + fit_smem<BLOCK>());  // one per warp
+  for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) s_rowx[i] = P.parts[0].row_x[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  FitArgs *wa = s_args + (threadIdx.x >> 5);
+  const unsigned long long total = P.prefix[P.n_parts];
+  int cur = -1;  // part whose arguments are in the warp's slot
+  for (;;) {
+    unsigned long long g = 0;
+    if (lane == 0) g = atomicAdd(P.cursor, 1ull);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= total) break;
+    int lo = 0, hi = P.n_parts;  // the part p with prefix[p] <= g < prefix[p+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (P.prefix[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    if (lo != cur) {  // warp-uniform
+      __syncwarp();
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(P.parts + lo);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(wa);
+      for (int k = lane; k < (int)(sizeof(FitArgs) / 4); k += 32) dst[k] = src[k];
+      __syncwarp();
+      cur = lo;
+    }
+    const FitArgs &A = *wa;
+    const int64_t i = (int64_t)(g - P.prefix[lo]) * 32 + lane;
+    if (i < A.n_tracks) {
+      const int64_t t = A.perm ? (int64_t)A.perm[i] : i;
+      fit_track<BLOCK, VAR>(A, t, s_bits + threadIdx.x, s_rowx, s_f4 + 4 * threadIdx.x, s_w + threadIdx.x);
+    }
+    __threadfence();  // this lane's results, before the group counts as fitted
+    __syncwarp();
+    if (lane == 0 && atomicSub(P.remaining + lo, 1u) == 1u) {
+      __threadfence_system();
+      P.done_flag[lo] = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_prepare(const FitArgs &a, cudaStream_t stream) {
@@ -633,6 +693,36 @@ int fit_default_blocks_per_sm(int block) {
   const int occ = fit_blocks_per_sm(block);
   const int want = 512 / (block == 128 ? 128 : 256);
   return occ < want ? occ : want;
+}
+
+template <int BLOCK, int MINB, bool VAR> static cudaError_t launch_parts_as(const PartsArgs &p, int grid,
+                                                                               cudaStream_t stream) {
+  static std::atomic<unsigned long long> done{0};
+  constexpr size_t smem = fit_smem<BLOCK>() + (BLOCK / 32) * sizeof(FitArgs);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(k_fit_parts<BLOCK, MINB, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+  }
+  k_fit_parts<BLOCK, MINB, VAR><<<grid, BLOCK, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit_parts(const PartsArgs &p, bool variant, int grid, int block, cudaStream_t stream) {
+  if (p.n_parts <= 0) return cudaSuccess;
+  if (variant)
+    return block == 128 ? launch_parts_as<128, 4, true>(p, grid, stream) : launch_parts_as<256, 2, true>(p, grid, stream);
+  return block == 128 ? launch_parts_as<128, 4, false>(p, grid, stream) : launch_parts_as<256, 2, false>(p, grid, stream);
+}
+
+FitArgs fit_args_for_launch(const FitArgs &a) {
+  FitArgs b = a;
+  b.stage_vec = same_16b_phase(a) ? 1 : 0;
+  return b;
 }
 
 int fit_regs_per_thread(int block, bool variant) {

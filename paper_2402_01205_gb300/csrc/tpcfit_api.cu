@@ -185,6 +185,7 @@ int serve_start(tpcfit_handle *h);
 void serve_stop(tpcfit_handle *h);
 int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint64_t *ticket);
 int serve_poll(tpcfit_handle *h, uint64_t ticket, int *state, double *t_done, double timeout_s, bool wait);
+int serve_stats(tpcfit_handle *h, tpcfit_serve_stats *out);
 
 struct tpcfit_handle {
   tpcfit_config cfg;
@@ -223,8 +224,8 @@ int run_sequence(tpcfit_handle *h, const FitArgs &a, cudaStream_t st, Scratch &s
 cudaStream_t handle_stream(tpcfit_handle *h) { return h->stream; }
 int64_t handle_chunk_clusters(tpcfit_handle *h) { return h->chunk_clusters; }
 size_t serve_scratch_bytes(int64_t n_tracks) { return Scratch::bytes_for(n_tracks); }
-int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
-                       int64_t off_base, cudaStream_t st, const int32_t **err_dev);
+int serve_prepare_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
+                        int64_t off_base, cudaStream_t st, FitArgs *args, const int32_t **err_dev);
 int handle_device(tpcfit_handle *h) { return h->device; }
 // exposed to the rANS codec (tpcfit_rans.cu)
 int handle_rans_scratch(tpcfit_handle *h, size_t bytes, void **p) {
@@ -246,6 +247,7 @@ const tpcfit_config &handle_config(tpcfit_handle *h) { return h->cfg; }
 ServeState *&handle_serve(tpcfit_handle *h) { return h->serve; }
 std::mutex &handle_mutex(tpcfit_handle *h) { return h->mu; }
 int handle_fit_grid(tpcfit_handle *h) { return h->fit_grid; }
+int handle_fit_block(tpcfit_handle *h) { return h->fit_block; }
 const float *handle_rowx(tpcfit_handle *h) { return h->d_rowx; }
 
 // ----------------------------------------------------------------------------
@@ -487,14 +489,17 @@ int run_sequence(tpcfit_handle *h, const FitArgs &a, cudaStream_t st, Scratch &s
 
 // Fit of one resident serving frame (or part of a frame, whose offsets start
 // at off_base) on a slot stream; scratch lives in the slot's allocation.
-int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
-                       int64_t off_base, cudaStream_t st, const int32_t **err_dev) {
+// Serving: the checks, seeds and sort of one resident part on `st`; *args
+// receives the part's fit arguments for the serving engine's launch.
+int serve_prepare_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
+                        int64_t off_base, cudaStream_t st, FitArgs *args, const int32_t **err_dev) {
   Scratch s;
   s.layout((char *)scratch_base, f->n_tracks);
   CU(cudaMemsetAsync(s.hist, 0, s.small_bytes, st));
   FitArgs a = make_args(h, f, r, s, off_base);
-  int rc = run_sequence(h, a, st, s, false, nullptr);
-  if (rc) return rc;
+  CU(launch_prepare(a, st));
+  CU(launch_sort(a, st, nullptr));
+  *args = fit_args_for_launch(a);
   *err_dev = s.err;
   return TPCFIT_OK;
 }
@@ -928,4 +933,9 @@ extern "C" int tpcfit_wait(tpcfit_handle *h, uint64_t ticket, double timeout_s, 
   if (!h || !state) return fail(TPCFIT_E_INVAL, "NULL argument");
   if (!h->serve) return fail(TPCFIT_E_NOTFOUND, "no ticket was issued");
   return serve_poll(h, ticket, state, t_done_s, timeout_s, true);
+}
+
+extern "C" int tpcfit_get_serve_stats(tpcfit_handle *h, tpcfit_serve_stats *out) {
+  if (!h || !out) return fail(TPCFIT_E_INVAL, "NULL argument");
+  return serve_stats(h, out);
 }

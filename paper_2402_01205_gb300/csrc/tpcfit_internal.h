@@ -215,6 +215,26 @@ cudaError_t launch_fit(const FitArgs &a, int grid, int block, cudaStream_t strea
 // Set the shared-memory attribute of the instantiation launch_fit takes for
 // these arguments (before a stream capture: no such call inside it).
 cudaError_t fit_set_attributes(const FitArgs &a, int block);
+
+// One fit launch over the prepared parts of several resident frames (the
+// serving engine, tpcfit_serve.cu): `parts` is a device table of their
+// arguments (as from fit_args_for_launch, after k_prepare and the sort ran for
+// each), `prefix` their track-group offsets (32 tracks per group; part p owns
+// groups [prefix[p], prefix[p+1])), `cursor` a zeroed group counter,
+// `remaining` each part's group count, and `done_flag` one host-mapped word
+// per part that the launch sets to 1 once that part's results are complete and
+// visible to the host and to copies.
+struct PartsArgs {
+  const FitArgs *parts;
+  const unsigned long long *prefix;
+  unsigned long long *cursor;
+  unsigned *remaining;
+  volatile int32_t *done_flag;
+  int n_parts;
+};
+cudaError_t launch_fit_parts(const PartsArgs &p, bool variant, int grid, int block, cudaStream_t stream);
+// the arguments with the launch-time fields (cluster staging mode) filled in
+FitArgs fit_args_for_launch(const FitArgs &a);
 // the two-filter smoother variant in place of the fit (a.sm_state, a.sm_cov set),
 // on a persistent grid of smooth_grid() blocks (0 if the device cannot be queried)
 int smooth_grid();

@@ -1,16 +1,26 @@
 // Serving runtime: time frames submitted from the host are admitted into
-// resident device slots as slots and HBM budget free up, fitted on one stream
-// per slot (so the copies and kernels of different frames overlap on the
-// device), and their results copied back into the caller's buffers.  A frame
-// is split into parts of about host_chunk_clusters clusters (tracks are
-// independent), each admitted to a slot of its own, so that the copies of one
-// part overlap the fit of the previous part of the same frame; a ticket is
-// done when all its parts are.
+// resident device slots as slots and HBM budget free up, and their results
+// copied back into the caller's buffers.  A frame is split into parts of
+// about host_chunk_clusters clusters (tracks are independent), each admitted
+// to a slot of its own; a ticket is done when all its parts are.
+//
+// A part moves through four phases.  Admission copies its clusters in on the
+// slot's stream (one part's copies after the other's: the link is shared) and
+// runs the checks, seeds and sort there.  The serving engine then fits every
+// part prepared at that moment in ONE persistent launch on the engine stream:
+// warps claim (part, 32-track group) descriptors from a device table with an
+// atomic cursor, so the parts of different frames share the GPU instead of
+// queueing as separate kernels; each part's completion counter reaches zero
+// when its last group is fitted, and the warp that fitted it sets the part's
+// flag in host-mapped memory.  The worker sees the flag and copies that part's
+// results back (after its residual codes, if requested) on the slot's stream
+// while the launch still fits the other parts.
 //
 // The paper's asynchronous reconstruction limits the number of time frames in
 // flight and throttles their injection (Sec. 7) and processes several time
 // frames at once ("horizontal" parallelism, Sec. 4); here that becomes
-// admission by slot count and device-memory budget.
+// admission by slot count and device-memory budget, and fitting the resident
+// frames together.
 //
 // Admission is FIFO with bounded backfill: a later, smaller frame may overtake
 // the head of the queue while the head does not fit, but only for
@@ -43,10 +53,12 @@ cudaStream_t handle_stream(tpcfit_handle *h);
 int handle_device(tpcfit_handle *h);
 const tpcfit_config &handle_config(tpcfit_handle *h);
 ServeState *&handle_serve(tpcfit_handle *h);
-int serve_launch_frame(tpcfit_handle *h, const tpcfit_frame *dev_frame, tpcfit_result *dev_res, void *scratch_base,
-                       int64_t off_base, cudaStream_t st, const int32_t **err_dev);
+int serve_prepare_frame(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, void *scratch_base,
+                        int64_t off_base, cudaStream_t st, FitArgs *args, const int32_t **err_dev);
 int64_t handle_chunk_clusters(tpcfit_handle *h);
 const float *handle_rowx(tpcfit_handle *h);
+int handle_fit_grid(tpcfit_handle *h);
+int handle_fit_block(tpcfit_handle *h);
 size_t serve_scratch_bytes(int64_t n_tracks);
 void serve_stop(tpcfit_handle *h);
 
@@ -58,6 +70,11 @@ bool debug_on() {
 }
 
 constexpr double kBackfillWindow = 0.050;  // seconds a blocked queue head may be overtaken
+// The engine launch fills every SM, so parts admitted meanwhile are checked,
+// seeded and sorted right after it ends, all at once.  An idle engine waits for
+// the parts still being prepared, at most this long after the first part is
+// ready, so that one launch takes them all.
+constexpr double kGatherWindow = 0.0002;
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -86,15 +103,23 @@ struct Part {
   size_t bytes = 0;
 };
 
+enum Phase { kFree, kPreparing, kReady, kFitting, kFinishing };
+
 struct Slot {
-  bool busy = false;
+  Phase phase = kFree;
   Part part;
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
-  cudaEvent_t in_done = nullptr;  // recorded after this slot's input copies
+  cudaEvent_t prepared = nullptr;  // recorded after the part's checks, seeds and sort
+  cudaEvent_t done = nullptr;      // recorded after the part's result copies
+  cudaEvent_t in_done = nullptr;   // recorded after this slot's input copies
   void *mem = nullptr;
   size_t bytes = 0;
-  int32_t *h_err = nullptr;  // pinned
+  tpcfit_frame df;                 // the resident part (device arrays in mem)
+  tpcfit_result dr;
+  FitArgs args;                    // its fit arguments (valid from kReady)
+  const int32_t *err_dev = nullptr;
+  int pos = -1;                    // its index in the engine launch (kFitting)
+  int32_t *h_err = nullptr;        // pinned
   bool failed = false;
 };
 
@@ -113,7 +138,20 @@ struct ServeState {
   uint64_t next_ticket = 1;
   double head_blocked_since = -1.0;
   cudaMemPool_t pool = nullptr;
-  cudaEvent_t last_in = nullptr;  // input copies of the latest launched part (the next part's copies wait for it)
+  cudaEvent_t last_in = nullptr;  // input copies of the latest admitted part (the next part's copies wait for it)
+  // the engine: one launch at a time over the prepared parts
+  cudaStream_t engine = nullptr;
+  cudaEvent_t engine_done = nullptr;
+  bool engine_busy = false;
+  double ready_since = -1.0;  // when the oldest part waiting for the idle engine became ready
+  // its part table, built in pinned memory and copied to the device per launch:
+  // FitArgs[n], then prefix u64[n+1], then remaining u32[n]
+  size_t table_bytes = 0;
+  char *h_table = nullptr, *d_table = nullptr;
+  unsigned long long *d_cursor = nullptr;
+  int32_t *h_flags = nullptr;  // host-mapped, one per part of a launch
+  int32_t *d_flags = nullptr;
+  tpcfit_serve_stats stats{};
 };
 
 // Carve one allocation into the frame and result arrays of a resident frame.
@@ -152,8 +190,9 @@ static void carve(void *mem, int64_t nt, int64_t nc, bool want_ry, bool want_rz,
   *scratch = p;
 }
 
-// Enqueue copy-in, fit and copy-out of part P on slot `si` (lock held).
-static bool launch(ServeState *S, const Part &P, int si) {
+// Admit part P to slot `si` (lock held): allocation, input copies, then the
+// part's checks, seeds and sort, all on the slot's stream.
+static bool admit(ServeState *S, const Part &P, int si) {
   Request &R = S->reqs[P.ticket];
   Slot &L = S->slots[si];
   const tpcfit_frame &F = R.frame;
@@ -166,58 +205,77 @@ static bool launch(ServeState *S, const Part &P, int si) {
     return false;
   }
   L.bytes = P.bytes;
-  L.busy = true;
   L.part = P;
   L.failed = false;
+  L.pos = -1;
+  L.err_dev = nullptr;
   S->used += P.bytes;
-  tpcfit_frame df;
-  tpcfit_result dr;
   void *scratch = nullptr;
-  carve(L.mem, nt, nc + 2 * kCopyPad, R.res.res_y != nullptr, R.res.res_z != nullptr, &df, &dr, &scratch);
+  carve(L.mem, nt, nc + 2 * kCopyPad, R.res.res_y != nullptr, R.res.res_z != nullptr, &L.df, &L.dr, &scratch);
   bool ok = true;
-  auto cp = [&](const void *dst, const void *src, size_t b, cudaMemcpyKind k) {
-    if (!b || !ok) return;
-    if (cudaError_t e = cudaMemcpyAsync((void *)dst, src, b, k, L.stream); e != cudaSuccess) {
-      ok = false;
-      if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: copy of %zu bytes failed: %s\n",
-                                   (unsigned long long)P.ticket, b, cudaGetErrorString(e));
-    }
-  };
-  // input copies in launch order, one part at a time: the link is shared, and a
+  // input copies in admission order, one part at a time: the link is shared, and a
   // part whose bytes arrive first can be fitted while the next one is copied
   if (S->last_in && cudaStreamWaitEvent(L.stream, S->last_in, 0) != cudaSuccess) ok = false;
-  cp(df.track_offsets, F.track_offsets + P.t0, (size_t)(nt + 1) * 8, cudaMemcpyHostToDevice);
+  if (ok && cudaMemcpyAsync((void *)L.df.track_offsets, F.track_offsets + P.t0, (size_t)(nt + 1) * 8,
+                            cudaMemcpyHostToDevice, L.stream) != cudaSuccess)
+    ok = false;
   if (ok) {
-    const ClusterArrays stage{const_cast<float *>(df.x), const_cast<float *>(df.y), const_cast<float *>(df.z),
-                              const_cast<float *>(df.sy2), const_cast<float *>(df.sz2), const_cast<uint8_t *>(df.row)};
-    if (cudaError_t e = copy_clusters_in(F, c0, c1, stage, handle_rowx(S->h), df, L.stream); e != cudaSuccess) {
+    const ClusterArrays stage{const_cast<float *>(L.df.x), const_cast<float *>(L.df.y), const_cast<float *>(L.df.z),
+                              const_cast<float *>(L.df.sy2), const_cast<float *>(L.df.sz2),
+                              const_cast<uint8_t *>(L.df.row)};
+    if (cudaError_t e = copy_clusters_in(F, c0, c1, stage, handle_rowx(S->h), L.df, L.stream); e != cudaSuccess) {
       ok = false;
       if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: input copy failed: %s\n",
                                    (unsigned long long)P.ticket, cudaGetErrorString(e));
     }
   }
   if (ok) {
-    if (cudaError_t e = cudaEventRecord(L.in_done, L.stream); e != cudaSuccess) ok = false;
+    if (cudaEventRecord(L.in_done, L.stream) != cudaSuccess) ok = false;
     else S->last_in = L.in_done;
   }
-  const int32_t *err_dev = nullptr;
-  if (ok && serve_launch_frame(S->h, &df, &dr, scratch, c0, L.stream, &err_dev) != TPCFIT_OK) ok = false;
-  if (ok) cp(L.h_err, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (ok && serve_prepare_frame(S->h, &L.df, &L.dr, scratch, c0, L.stream, &L.args, &L.err_dev) != TPCFIT_OK)
+    ok = false;
+  if (ok && cudaEventRecord(L.prepared, L.stream) != cudaSuccess) ok = false;
+  if (!ok) cudaGetLastError();
+  L.failed = !ok;
+  L.phase = kPreparing;
+  return true;
+}
+
+// Copy part results back and release the slot's memory, on the slot's stream
+// (lock held); the part must be fitted (or failed: nothing is copied).
+static void finish(ServeState *S, int si) {
+  Slot &L = S->slots[si];
+  Request &R = S->reqs[L.part.ticket];
+  const Part &P = L.part;
+  const int64_t c0 = R.frame.track_offsets[P.t0];
+  const int64_t nt = P.t1 - P.t0, nc = R.frame.track_offsets[P.t1] - c0;
+  bool ok = !L.failed;
+  auto cp = [&](void *dst, const void *src, size_t b) {
+    if (!b || !ok) return;
+    if (cudaError_t e = cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, L.stream); e != cudaSuccess) {
+      ok = false;
+      if (debug_on()) std::fprintf(stderr, "tpcfit serve: ticket %llu: copy of %zu bytes failed: %s\n",
+                                   (unsigned long long)P.ticket, b, cudaGetErrorString(e));
+    }
+  };
+  if (ok && nt > 0 && launch_residuals(L.args, L.stream) != cudaSuccess) ok = false;
+  if (L.err_dev) cp(L.h_err, L.err_dev, sizeof(int32_t));
   const tpcfit_result &O = R.res;
-  cp(O.state + 5 * P.t0, dr.state, (size_t)nt * 20, cudaMemcpyDeviceToHost);
-  cp(O.cov + 15 * P.t0, dr.cov, (size_t)nt * 60, cudaMemcpyDeviceToHost);
-  cp(O.x_ref + P.t0, dr.x_ref, (size_t)nt * 4, cudaMemcpyDeviceToHost);
-  cp(O.chi2 + P.t0, dr.chi2, (size_t)nt * 8, cudaMemcpyDeviceToHost);
-  cp(O.ndf + P.t0, dr.ndf, (size_t)nt * 4, cudaMemcpyDeviceToHost);
-  cp(O.status + P.t0, dr.status, (size_t)nt * 4, cudaMemcpyDeviceToHost);
-  cp(O.accept + c0, dr.accept, (size_t)nc, cudaMemcpyDeviceToHost);
-  if (dr.res_y) cp(O.res_y + c0, dr.res_y, (size_t)nc * 2, cudaMemcpyDeviceToHost);
-  if (dr.res_z) cp(O.res_z + c0, dr.res_z, (size_t)nc * 2, cudaMemcpyDeviceToHost);
+  cp(O.state + 5 * P.t0, L.dr.state, (size_t)nt * 20);
+  cp(O.cov + 15 * P.t0, L.dr.cov, (size_t)nt * 60);
+  cp(O.x_ref + P.t0, L.dr.x_ref, (size_t)nt * 4);
+  cp(O.chi2 + P.t0, L.dr.chi2, (size_t)nt * 8);
+  cp(O.ndf + P.t0, L.dr.ndf, (size_t)nt * 4);
+  cp(O.status + P.t0, L.dr.status, (size_t)nt * 4);
+  cp(O.accept + c0, L.dr.accept, (size_t)nc);
+  if (L.dr.res_y) cp(O.res_y + c0, L.dr.res_y, (size_t)nc * 2);
+  if (L.dr.res_z) cp(O.res_z + c0, L.dr.res_z, (size_t)nc * 2);
   if (!ok) cudaGetLastError();
   L.failed = !ok;
   cudaFreeAsync(L.mem, L.stream);  // released in stream order after the copies
   cudaEventRecord(L.done, L.stream);
-  return true;
+  L.phase = kFinishing;
 }
 
 // One part of a request has finished (lock held).
@@ -230,35 +288,136 @@ static void part_done(ServeState *S, uint64_t tk, bool failed) {
   }
 }
 
+// One engine launch over every prepared part (lock held, engine idle).
+static void launch_engine(ServeState *S) {
+  const int ns = (int)S->slots.size();
+  FitArgs *parts = reinterpret_cast<FitArgs *>(S->h_table);
+  unsigned long long *prefix = reinterpret_cast<unsigned long long *>(S->h_table + ns * sizeof(FitArgs));
+  unsigned *remaining = reinterpret_cast<unsigned *>(S->h_table + ns * sizeof(FitArgs) + (ns + 1) * 8);
+  int n = 0;
+  unsigned long long groups = 0;
+  for (int i = 0; i < ns; ++i) {
+    Slot &L = S->slots[i];
+    if (L.phase != kReady) continue;
+    parts[n] = L.args;
+    prefix[n] = groups;
+    const unsigned g = (unsigned)((L.args.n_tracks + 31) / 32);
+    remaining[n] = g;
+    groups += g;
+    S->h_flags[n] = 0;
+    L.pos = n;
+    L.phase = kFitting;
+    ++n;
+  }
+  prefix[n] = groups;
+  if (n == 0) return;
+  const tpcfit_config &c = handle_config(S->h);
+  PartsArgs pa;
+  pa.parts = reinterpret_cast<const FitArgs *>(S->d_table);
+  pa.prefix = reinterpret_cast<const unsigned long long *>(S->d_table + ns * sizeof(FitArgs));
+  pa.remaining = reinterpret_cast<unsigned *>(S->d_table + ns * sizeof(FitArgs) + (ns + 1) * 8);
+  pa.cursor = S->d_cursor;
+  pa.done_flag = S->d_flags;
+  pa.n_parts = n;
+  bool ok = cudaMemcpyAsync(S->d_table, S->h_table, S->table_bytes, cudaMemcpyHostToDevice, S->engine) == cudaSuccess &&
+            cudaMemsetAsync(S->d_cursor, 0, sizeof(unsigned long long), S->engine) == cudaSuccess &&
+            launch_fit_parts(pa, c.xrho_per_row > 0.0f || c.fit_iterations > 0, handle_fit_grid(S->h),
+                             handle_fit_block(S->h), S->engine) == cudaSuccess &&
+            cudaEventRecord(S->engine_done, S->engine) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (debug_on()) std::fprintf(stderr, "tpcfit serve: engine launch over %d parts failed\n", n);
+    for (int i = 0; i < ns; ++i)
+      if (S->slots[i].phase == kFitting) {
+        S->slots[i].failed = true;
+        finish(S, i);
+      }
+    return;
+  }
+  S->engine_busy = true;
+  S->stats.launches += 1;
+  S->stats.parts += n;
+  S->stats.max_parts_per_launch = std::max<int64_t>(S->stats.max_parts_per_launch, n);
+}
+
 static void worker_loop(ServeState *S) {
   cudaSetDevice(handle_device(S->h));
   std::unique_lock<std::mutex> lk(S->mu);
   while (!S->stop) {
     bool progress = false;
-    // completions
     for (size_t i = 0; i < S->slots.size(); ++i) {
       Slot &L = S->slots[i];
-      if (!L.busy) continue;
-      cudaError_t q = cudaEventQuery(L.done);
-      if (q == cudaErrorNotReady) continue;
-      const bool failed = !(q == cudaSuccess && !L.failed && *L.h_err == 0);
-      if (failed && debug_on())
-        std::fprintf(stderr, "tpcfit serve: ticket %llu failed: event %s, enqueue %s, frame error word %d\n",
-                     (unsigned long long)L.part.ticket, cudaGetErrorString(q), L.failed ? "failed" : "ok", *L.h_err);
-      part_done(S, L.part.ticket, failed);
-      if (q != cudaSuccess) cudaGetLastError();
-      S->used -= L.bytes;
-      L.busy = false;
-      L.mem = nullptr;
-      progress = true;
+      if (L.phase == kFinishing) {  // results copied back
+        cudaError_t q = cudaEventQuery(L.done);
+        if (q == cudaErrorNotReady) continue;
+        const bool failed = !(q == cudaSuccess && !L.failed && *L.h_err == 0);
+        if (failed && debug_on())
+          std::fprintf(stderr, "tpcfit serve: ticket %llu failed: event %s, enqueue %s, frame error word %d\n",
+                       (unsigned long long)L.part.ticket, cudaGetErrorString(q), L.failed ? "failed" : "ok", *L.h_err);
+        part_done(S, L.part.ticket, failed);
+        if (q != cudaSuccess) cudaGetLastError();
+        S->used -= L.bytes;
+        L.phase = kFree;
+        L.mem = nullptr;
+        progress = true;
+      } else if (L.phase == kPreparing) {  // checks, seeds and sort done?
+        cudaError_t q = cudaEventQuery(L.prepared);
+        if (L.failed) q = cudaErrorUnknown;
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess || L.args.n_tracks == 0) {  // nothing for the engine
+          if (q != cudaSuccess) {
+            cudaGetLastError();
+            L.failed = true;
+          }
+          finish(S, (int)i);
+        } else {
+          L.phase = kReady;
+        }
+        progress = true;
+      } else if (L.phase == kFitting && *(volatile int32_t *)(S->h_flags + L.pos) == 1) {  // fitted
+        finish(S, (int)i);
+        progress = true;
+      }
     }
     if (progress) S->cv_done.notify_all();
+    // the engine launch finished: every part it fitted has raised its flag,
+    // unless the launch failed
+    if (S->engine_busy && cudaEventQuery(S->engine_done) != cudaErrorNotReady) {
+      const bool launch_ok = cudaEventQuery(S->engine_done) == cudaSuccess;
+      if (!launch_ok) cudaGetLastError();
+      for (size_t i = 0; i < S->slots.size(); ++i) {
+        Slot &L = S->slots[i];
+        if (L.phase != kFitting) continue;
+        if (!(launch_ok && *(volatile int32_t *)(S->h_flags + L.pos) == 1)) L.failed = true;
+        finish(S, (int)i);
+      }
+      S->engine_busy = false;
+      progress = true;
+    }
+    if (!S->engine_busy) {
+      bool ready = false, preparing = false;
+      for (auto &L : S->slots) {
+        ready |= L.phase == kReady;
+        preparing |= L.phase == kPreparing;
+      }
+      if (!ready) {
+        S->ready_since = -1.0;
+      } else {
+        const double t = tpcfit_now();
+        if (S->ready_since < 0) S->ready_since = t;
+        if (!preparing || t - S->ready_since > kGatherWindow) {
+          launch_engine(S);
+          S->ready_since = -1.0;
+          progress = true;
+        }
+      }
+    }
     // admissions
     const double now = tpcfit_now();
     for (auto it = S->queue.begin(); it != S->queue.end();) {
       int free_slot = -1;
       for (size_t i = 0; i < S->slots.size(); ++i)
-        if (!S->slots[i].busy) {
+        if (S->slots[i].phase == kFree) {
           free_slot = (int)i;
           break;
         }
@@ -266,7 +425,7 @@ static void worker_loop(ServeState *S) {
       const Part P = *it;
       const bool is_head = (it == S->queue.begin());
       if (S->used + P.bytes <= S->budget) {
-        if (!launch(S, P, free_slot)) {
+        if (!admit(S, P, free_slot)) {
           part_done(S, P.ticket, true);
           S->cv_done.notify_all();
         }
@@ -281,8 +440,8 @@ static void worker_loop(ServeState *S) {
       }
       ++it;
     }
-    bool busy = false;
-    for (auto &L : S->slots) busy |= L.busy;
+    bool busy = S->engine_busy;
+    for (auto &L : S->slots) busy |= L.phase != kFree;
     if (!progress) {
       if (busy) {
         lk.unlock();
@@ -313,20 +472,32 @@ int serve_start(tpcfit_handle *h) {
   }
   uint64_t keep = (uint64_t)S->budget;
   cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  S->slots.resize((size_t)c.max_slots);
+  const int ns = c.max_slots;
+  S->slots.resize((size_t)ns);
+  S->table_bytes = (size_t)ns * sizeof(FitArgs) + (size_t)(ns + 1) * 8 + (size_t)ns * 4;
+  bool ok = cudaStreamCreateWithFlags(&S->engine, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&S->engine_done, cudaEventDisableTiming) == cudaSuccess &&
+            cudaMallocHost(&S->h_table, S->table_bytes) == cudaSuccess &&
+            cudaMalloc(&S->d_table, S->table_bytes) == cudaSuccess &&
+            cudaMalloc(&S->d_cursor, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaHostAlloc(&S->h_flags, (size_t)ns * sizeof(int32_t), cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer(&S->d_flags, S->h_flags, 0) == cudaSuccess;
   for (auto &L : S->slots) {
-    if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&L.in_done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&L.h_err, sizeof(int32_t)) != cudaSuccess) {
-      cudaGetLastError();
-      handle_serve(h) = S;
-      serve_stop(h);
-      return TPCFIT_E_CUDA;
-    }
-    *L.h_err = 0;
+    if (!ok) break;
+    ok = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&L.prepared, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&L.in_done, cudaEventDisableTiming) == cudaSuccess &&
+         cudaMallocHost(&L.h_err, sizeof(int32_t)) == cudaSuccess;
+    if (ok) *L.h_err = 0;
   }
   handle_serve(h) = S;
+  if (!ok) {
+    cudaGetLastError();
+    serve_stop(h);
+    return TPCFIT_E_CUDA;
+  }
+  for (int i = 0; i < ns; ++i) S->h_flags[i] = 0;
   S->worker = std::thread(worker_loop, S);
   return TPCFIT_OK;
 }
@@ -340,16 +511,33 @@ void serve_stop(tpcfit_handle *h) {
   }
   S->cv_work.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  if (S->engine) cudaStreamSynchronize(S->engine);
   for (auto &L : S->slots) {
     if (L.stream) cudaStreamSynchronize(L.stream);
+    if (L.prepared) cudaEventDestroy(L.prepared);
     if (L.done) cudaEventDestroy(L.done);
     if (L.in_done) cudaEventDestroy(L.in_done);
     if (L.stream) cudaStreamDestroy(L.stream);
     if (L.h_err) cudaFreeHost(L.h_err);
   }
+  if (S->engine_done) cudaEventDestroy(S->engine_done);
+  if (S->engine) cudaStreamDestroy(S->engine);
+  if (S->h_table) cudaFreeHost(S->h_table);
+  if (S->d_table) cudaFree(S->d_table);
+  if (S->d_cursor) cudaFree(S->d_cursor);
+  if (S->h_flags) cudaFreeHost(S->h_flags);
   if (S->pool) cudaMemPoolDestroy(S->pool);
   handle_serve(h) = nullptr;
   delete S;
+}
+
+int serve_stats(tpcfit_handle *h, tpcfit_serve_stats *out) {
+  ServeState *S = handle_serve(h);
+  std::memset(out, 0, sizeof(*out));
+  if (!S) return TPCFIT_OK;
+  std::lock_guard<std::mutex> lk(S->mu);
+  *out = S->stats;
+  return TPCFIT_OK;
 }
 
 int serve_submit(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, uint64_t *ticket) {

@@ -142,3 +142,31 @@ def test_served_fit_variant_equals_its_plain_fit(T):
         assert fx.wait(fx.submit(pinned_frame(f), r), 60)[0] == T.DONE
     for k in ref:
         assert np.array_equal(ref[k], r[k].numpy(), equal_nan=k in ("state", "cov")), k
+
+
+def test_engine_fits_the_parts_of_several_frames_in_one_launch(T):
+    """The serving engine fits every part that is ready in one persistent
+    launch (warps take (part, group) descriptors from a device table): with
+    many small frames submitted at once, launches fit several parts each, and
+    every frame's results equal its plain fit, including residual codes."""
+    pool = tpcgen.generate("detector50k", n_tracks=24_000, seed=11)
+    frames = [pool.subset(i * 1_000, (i + 1) * 1_000 - 7 * i) for i in range(24)]
+    ref = []
+    with T.Fitter() as fx:
+        for f in frames:
+            r = T.alloc_result(f.n_tracks, f.n_clusters, residuals=True)
+            fx.fit(f, r)
+            ref.append(r)
+    pinned = [pinned_frame(f) for f in frames]  # pinned first: the submissions follow one another at once
+    with T.Fitter(max_slots=16) as fx:
+        assert fx.serve_stats() == {"launches": 0, "parts": 0, "max_parts_per_launch": 0}
+        res = [T.alloc_result(f.n_tracks, f.n_clusters, pinned=True, residuals=True) for f in frames]
+        tickets = [fx.submit(p, r) for p, r in zip(pinned, res)]
+        for tk in tickets:
+            assert fx.wait(tk, timeout_s=60)[0] == T.DONE
+        st = fx.serve_stats()
+    assert st["parts"] == len(frames)
+    assert st["launches"] < len(frames) and st["max_parts_per_launch"] >= 2, st
+    for r, rf in zip(res, ref):
+        for k in rf:
+            assert np.array_equal(r[k].numpy(), rf[k], equal_nan=k in ("state", "cov")), k
