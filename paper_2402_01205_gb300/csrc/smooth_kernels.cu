@@ -10,7 +10,7 @@
 //
 //  1. forward filter = the fit's outward pass.  Before its update at cluster
 //     k the predicted state (p-, C-) (clusters 0..k-1 and the seed prior) is
-//     written into the caller's smoothed-output slots of cluster k;
+//     stored in the prediction scratch;
 //  2. backward filter = the inward pass, started as the fit starts it (the
 //     outward state with the inflated diagonal restart covariance, or the
 //     reversed three-point seed), except that at each crossed row it adds the
@@ -19,7 +19,7 @@
 //  3. after its update at cluster k it holds (p+, C+) from clusters k..n-1
 //     and combines them with the stored prediction of the same state:
 //       S = C- + C+,  K = C- S^-1,  p = p- + K (p+ - p-),  C = K C+,
-//     and overwrites the slots of cluster k with the smoothed state.  When
+//     and writes the smoothed state into the caller's slots of cluster k.  When
 //     the forward filter lost the track (it accepted fewer than reseed_pct %
 //     of the clusters, so that the backward filter re-seeds) its predictions
 //     carry no valid information: the smoothed state is the backward
@@ -37,7 +37,15 @@
 //
 // One thread per track on the persistent grid of the fit (same sort, same
 // work counter); clusters are read directly from global memory (no staging
-// ring: a variant, not the benchmark path).
+// ring: a variant, not the benchmark path).  The 20 floats of a prediction
+// are kept in scratch owned by the warp, [cluster of the track][lane] slots of
+// 96 bytes (three whole 32-byte sectors, so that no sector is shared between
+// lanes whose tracks reach that cluster at different times) written and read
+// as five 16-byte vectors, where scalar accesses to the caller's per-cluster
+// slots took 20 requests per lane.  The backward filter loads a cluster's
+// prediction before it propagates to that cluster, so the load overlaps the
+// step's arithmetic; the smoothed outputs are written with the widest vector
+// stores their alignment allows.
 
 #include <cuda_runtime.h>
 
@@ -185,7 +193,63 @@ __device__ void seed_cov_of(const FitArgs &A, Trk &T) {
   T.clear_comp();
 }
 
-__device__ void smooth_track(const FitArgs &A, int64_t t) {
+constexpr int kPredSlot = 24;  // floats per prediction slot (20 used): 96 bytes
+
+// The prediction slot of cluster j of the lane's track in the warp's scratch
+// (`pred` = the warp's base + the lane's slot).
+__device__ __forceinline__ float4 *pred_slot(float *pred, int j) {
+  return reinterpret_cast<float4 *>(pred + j * (32 * kPredSlot));
+}
+
+// N floats to a 4-byte aligned address whose first H floats lie before a
+// 16-byte boundary: scalar / 8-byte head, 16-byte body, 8-byte / scalar tail.
+template <int N, int H> __device__ __forceinline__ void store_from(float *dst, const float *v) {
+  int i = 0;
+  if (H & 1) {
+    dst[0] = v[0];
+    i = 1;
+  }
+  if (H & 2) {
+    *reinterpret_cast<float2 *>(dst + i) = make_float2(v[i], v[i + 1]);
+    i += 2;
+  }
+#pragma unroll
+  for (int q = 0; q < (N - H) / 4; ++q, i += 4)
+    *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  if ((N - H) & 2) {
+    *reinterpret_cast<float2 *>(dst + i) = make_float2(v[i], v[i + 1]);
+    i += 2;
+  }
+  if ((N - H) & 1) dst[i] = v[i];
+}
+// N floats with the widest aligned vector stores (fewer store instructions and
+// memory requests per lane than N scalar stores).
+template <int N> __device__ __forceinline__ void store_vec(float *dst, const float (&v)[N]) {
+  switch ((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u) {  // floats past a 16-byte boundary
+    case 0: store_from<N, 0>(dst, v); break;
+    case 1: store_from<N, 3>(dst, v); break;
+    case 2: store_from<N, 2>(dst, v); break;
+    default: store_from<N, 1>(dst, v); break;
+  }
+}
+
+// One cluster as the filters read it.  Each pass keeps the current cluster and
+// the loads of the next one in the pass direction, issued when the current one
+// became current, so that their latency overlaps a whole step.
+struct Cl {
+  float x, y, z, vy, vz;
+  int r;
+};
+__device__ __forceinline__ void load_cl(const FitArgs &A, int64_t k, Cl &c) {
+  c.x = A.x[k];
+  c.y = A.y[k];
+  c.z = A.z[k];
+  c.vy = A.sy2[k];
+  c.vz = A.sz2[k];
+  c.r = A.row[k];
+}
+
+__device__ void smooth_track(const FitArgs &A, int64_t t, float *pred) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
   const int st0 = A.status[t];
   const float *sd = A.seed + 5 * t;
@@ -225,30 +289,39 @@ __device__ void smooth_track(const FitArgs &A, int64_t t) {
       // ---------------- forward filter (outward pass) ----------------
       int nacc_out = 0, rprev = -1;
       int64_t k = a;
-      int rk = A.row[k];
-      st = check_cluster(rk, rprev, A.n_rows, A.x[k], A.y[k], A.z[k], A.sy2[k], A.sz2[k]);
+      Cl cur, nxt;
+      load_cl(A, k, cur);
+      if (k + 1 < e) load_cl(A, k + 1, nxt);
+      int rk = cur.r;
+      st = check_cluster(rk, rprev, A.n_rows, cur.x, cur.y, cur.z, cur.vy, cur.vz);
       for (int r = rk; st == ST_OK; ++r) {
         const bool has = (rk == r);
-        const float xt = has ? A.x[k] : A.row_x[r];
+        const float xt = has ? cur.x : A.row_x[r];
         if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
         xcur = xt;
         if (has) {
           float pm[5], cm[15];
           state_of(T, pm);
           cov_of(T, cm);
-          store5(A.sm_state + 5 * k, pm);
-          store15(A.sm_cov + 15 * k, cm);
+          float4 *slot = pred_slot(pred, (int)(k - a));
+          slot[0] = make_float4(pm[0], pm[1], pm[2], pm[3]);
+          slot[1] = make_float4(pm[4], cm[0], cm[1], cm[2]);
+          slot[2] = make_float4(cm[3], cm[4], cm[5], cm[6]);
+          slot[3] = make_float4(cm[7], cm[8], cm[9], cm[10]);
+          slot[4] = make_float4(cm[11], cm[12], cm[13], cm[14]);
           bool acc;
           double chi2;
-          const int ust = update(T, A.y[k], A.z[k], A.sy2[k], A.sz2[k], A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
+          const int ust = update(T, cur.y, cur.z, cur.vy, cur.vz, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
           if (ust != ST_OK) { st = ust; break; }
           A.accept[k] = acc ? 1u : 0u;
           nacc_out += acc ? 1 : 0;
           ++fw_done;
           rprev = rk;
           if (++k < e) {
-            rk = A.row[k];
-            const int vs = check_cluster(rk, rprev, A.n_rows, A.x[k], A.y[k], A.z[k], A.sy2[k], A.sz2[k]);
+            cur = nxt;
+            if (k + 1 < e) load_cl(A, k + 1, nxt);
+            rk = cur.r;
+            const int vs = check_cluster(rk, rprev, A.n_rows, cur.x, cur.y, cur.z, cur.vy, cur.vz);
             if (vs != ST_OK) { st = vs; break; }
           }
         }
@@ -290,18 +363,29 @@ __device__ void smooth_track(const FitArgs &A, int64_t t) {
         }
         // ---------------- backward filter and combination ----------------
         k = e - 1;
-        rk = A.row[k];
+        load_cl(A, k, cur);
+        if (k - 1 >= a) load_cl(A, k - 1, nxt);
+        rk = cur.r;
         for (int r = rk, step = 0;; --r, ++step) {
           const bool has = (rk == r);
-          const float xt = has ? A.x[k] : A.row_x[r];
+          const float xt = has ? cur.x : A.row_x[r];
+          float pm[5], cm[15];  // the forward prediction at this cluster, loaded ahead of its use
+          if (has && fw_valid) {
+            const float4 *slot = pred_slot(pred, (int)(k - a));
+            const float4 s0 = slot[0], s1 = slot[1], s2 = slot[2], s3 = slot[3], s4 = slot[4];
+            pm[0] = s0.x; pm[1] = s0.y; pm[2] = s0.z; pm[3] = s0.w; pm[4] = s1.x;
+            cm[0] = s1.y; cm[1] = s1.z; cm[2] = s1.w;
+            cm[3] = s2.x; cm[4] = s2.y; cm[5] = s2.z; cm[6] = s2.w;
+            cm[7] = s3.x; cm[8] = s3.y; cm[9] = s3.z; cm[10] = s3.w;
+            cm[11] = s4.x; cm[12] = s4.y; cm[13] = s4.z; cm[14] = s4.w;
+          }
           if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
           xcur = xt;
           if (step > 0 && A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);  // the row's kink lies beyond its measurement
           if (has) {
             bool acc;
             double chi2;
-            const int ust = update(T, A.y[k], A.z[k], A.sy2[k], A.sz2[k], A.chi2_max_d, gate_hi, gate_lo, true, acc,
-                                   chi2);
+            const int ust = update(T, cur.y, cur.z, cur.vy, cur.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc, chi2);
             if (ust != ST_OK) { st = ust; break; }
             chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
             nacc += acc ? 1 : 0;
@@ -310,25 +394,22 @@ __device__ void smooth_track(const FitArgs &A, int64_t t) {
             state_of(T, pp);
             cov_of(T, cp);
             if (fw_valid) {
-              float pm[5], cm[15];
-#pragma unroll
-              for (int i = 0; i < 5; ++i) pm[i] = A.sm_state[5 * k + i];
-#pragma unroll
-              for (int i = 0; i < 15; ++i) cm[i] = A.sm_cov[15 * k + i];
               if (!combine(pm, cm, pp, cp, ps, cs)) { st = ST_NOT_PD; break; }
             } else {
               store5(ps, pp);
               store15(cs, cp);
             }
-            store5(A.sm_state + 5 * k, ps);
-            store15(A.sm_cov + 15 * k, cs);
+            store_vec<5>(A.sm_state + 5 * k, ps);
+            store_vec<15>(A.sm_cov + 15 * k, cs);
             smoothed_from = k;
             if (k == a) {
               store5(out_p, ps);
               store15(out_c, cs);
             }
             if (--k < a) break;
-            rk = A.row[k];
+            cur = nxt;
+            if (k - 1 >= a) load_cl(A, k - 1, nxt);
+            rk = cur.r;
           }
         }
         if (st == ST_OK) {
@@ -371,13 +452,15 @@ __device__ void smooth_track(const FitArgs &A, int64_t t) {
 
 __global__ void __launch_bounds__(kSmoothBlock) k_smooth(FitArgs A) {
   const int lane = threadIdx.x & 31;
+  const size_t warp = ((size_t)blockIdx.x * kSmoothBlock + threadIdx.x) >> 5;
+  float *pred = A.sm_pred + (warp * (size_t)A.n_rows * 32 + lane) * kPredSlot;  // this warp's scratch, this lane's slots
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(A.work, 32ull);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)A.n_tracks) break;
     const int64_t i = (int64_t)base + lane;
-    if (i < A.n_tracks) smooth_track(A, A.perm ? (int64_t)A.perm[i] : i);
+    if (i < A.n_tracks) smooth_track(A, A.perm ? (int64_t)A.perm[i] : i, pred);
     __syncwarp();
   }
 }
@@ -395,9 +478,16 @@ int smooth_grid() {
   return sms * per_sm;
 }
 
+// Scratch of the forward predictions: per warp of the grid, a 96-byte slot
+// for each of up to n_rows clusters of each of its 32 lanes' tracks (a track
+// has at most one cluster per pad row).
+size_t smooth_pred_bytes(int grid, int n_rows) {
+  return (size_t)grid * (kSmoothBlock / 32) * (size_t)n_rows * 32 * kPredSlot * sizeof(float);
+}
+
 cudaError_t launch_smooth(const FitArgs &a, int grid, cudaStream_t stream) {
   if (a.n_tracks <= 0) return cudaSuccess;
-  if (!a.sm_state || !a.sm_cov || grid <= 0) return cudaErrorInvalidValue;
+  if (!a.sm_state || !a.sm_cov || !a.sm_pred || grid <= 0) return cudaErrorInvalidValue;
   k_smooth<<<grid, kSmoothBlock, 0, stream>>>(a);
   return cudaGetLastError();
 }

@@ -106,6 +106,7 @@ static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // counter and frame-error word, carved from one allocation.
 struct Scratch {
   DevBuf buf;
+  DevBuf pred;  // the smoother's forward predictions (allocated on its first use)
   float *seed = nullptr;
   int32_t *perm = nullptr;
   uint32_t *hist = nullptr;  // 2*kKeyBins
@@ -368,6 +369,7 @@ extern "C" int tpcfit_destroy(tpcfit_handle *h) {
   if (h->h2d) cudaStreamSynchronize(h->h2d);
   if (h->d2h) cudaStreamSynchronize(h->d2h);
   h->scratch.buf.release();
+  h->scratch.pred.release();
   h->rans_buf.release();
   h->follow_buf.release();
   for (auto &s : h->stage) {
@@ -547,12 +549,24 @@ static int wait_stream(cudaStream_t s, double timeout_s) {
   }
 }
 
+// The smoother's prediction scratch of `s` (sized by the smoother's grid and
+// the handle's pad rows, fixed per handle: allocated once) into a.sm_pred.
+static int smoother_scratch(tpcfit_handle *h, Scratch &s, FitArgs &a) {
+  const int grid = smooth_grid();
+  if (grid <= 0) return fail(TPCFIT_E_CUDA, "smoother grid");
+  int rc = s.pred.ensure(smooth_pred_bytes(grid, h->cfg.n_rows));
+  if (rc) return rc;
+  a.sm_pred = s.pred.as<float>();
+  return TPCFIT_OK;
+}
+
 // device frame -> device results on stream st
 static int fit_device(tpcfit_handle *h, const tpcfit_frame *f, tpcfit_result *r, cudaStream_t st) {
   int rc = h->scratch.ensure(f->n_tracks);
   if (rc) return rc;
   CU(cudaMemsetAsync(h->scratch.hist, 0, h->scratch.small_bytes, st));
   FitArgs a = make_args(h, f, r, h->scratch, 0);
+  if (a.sm_state && (rc = smoother_scratch(h, h->scratch, a))) return rc;
   int launches = 0;
   rc = run_sequence(h, a, st, h->scratch, true, &launches);
   if (rc) return rc;
@@ -583,6 +597,7 @@ static void batch_free(tpcfit_batch *b) {
   if (b->stream) cudaStreamDestroy(b->stream);
   if (b->h_err) cudaFreeHost(b->h_err);
   b->scratch.buf.release();
+  b->scratch.pred.release();
   delete b;
 }
 
@@ -618,6 +633,7 @@ extern "C" int tpcfit_batch_create(tpcfit_handle *h, const tpcfit_frame *f, tpcf
   *b->h_err = 0;
   // set the kernel attributes before capture (no such calls inside it)
   FitArgs a = make_args(h, f, r, b->scratch, 0);
+  if (a.sm_state && (rc = smoother_scratch(h, b->scratch, a))) return bail(rc);
   if (fit_set_attributes(a, h->fit_block) != cudaSuccess) return bail(fail(TPCFIT_E_CUDA, "fit kernel attributes"));
   const int sgrid = a.sm_state ? smooth_grid() : 0;
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);

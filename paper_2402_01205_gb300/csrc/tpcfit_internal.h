@@ -27,6 +27,7 @@ struct FitArgs {
   double *chi2_out_c, *chi2_in_c;  // optional per-cluster chi2 (nullptr: not written)
   float *restart_state;            // optional inward restart state (nullptr: not written)
   float *sm_state, *sm_cov;        // smoother variant: per-cluster smoothed state / packed covariance (nullptr: fit)
+  float *sm_pred;                  // smoother variant: the forward predictions, smooth_pred_bytes() of scratch
   int16_t *res_y, *res_z;          // optional residual codes (nullptr: not written)
   float res_inv_step_y, res_inv_step_z;
   // scratch (device)
@@ -238,6 +239,8 @@ FitArgs fit_args_for_launch(const FitArgs &a);
 // the two-filter smoother variant in place of the fit (a.sm_state, a.sm_cov set),
 // on a persistent grid of smooth_grid() blocks (0 if the device cannot be queried)
 int smooth_grid();
+// device scratch the smoother needs on that grid for frames of n_rows pad rows
+size_t smooth_pred_bytes(int grid, int n_rows);
 cudaError_t launch_smooth(const FitArgs &a, int grid, cudaStream_t stream);
 // track-model compression residual codes (nothing when a.res_y and a.res_z are null)
 cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream);
