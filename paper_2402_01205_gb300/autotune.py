@@ -4,8 +4,12 @@ The persistent fit kernel has three launch choices that change its speed but
 not its results (every choice is bit-identical; the GPU tests check it):
 
 * ``block_threads``  threads per block, 128 or 256 (tracks per warp are fixed
-  at 32, one track per lane, so that each warp-wide FP64 instruction of the
-  innovation inverse and chi2 serves 32 tracks);
+  at 32, one track per lane: each warp-wide FP64 instruction of the
+  innovation inverse and chi2 costs the FP64 pipe the same with 1 or 32
+  lanes active, so k lanes per track would multiply its time per cluster by
+  k; two tracks per lane, advanced with paired FP32 instructions, was built
+  and measured 1.8 times slower on the Pb-Pb frame: half the resident warps,
+  and packing the pairs cost more issue slots than the pairing saved);
 * ``blocks_per_sm``  resident blocks per SM (grid = SMs x blocks_per_sm);
 * ``sort_tracks``    longest-first order of tracks, or frame order.
 
