@@ -15,6 +15,9 @@
 //               sorted order, one thread per track, and steps pad row by pad
 //               row through the outward and the inward pass (every lane
 //               propagates each step; lanes with a cluster on the row update).
+// Serving fits the prepared parts of several frames with k_fit_parts instead:
+// the same fit of each track, the warps claiming (part, 32-track group)
+// descriptors from a device table.
 //
 // Precision: propagation, covariance transport and the gain/update are FP32.
 // The innovation-matrix determinant and reciprocal, the quadratic form
@@ -562,6 +565,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_fit_parts(PartsArgs P) {
   uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + kSmemRowx + smem_f4<BLOCK>());
   uint32_t *s_bits = s_w + kStageBufs * 2 * BLOCK;
   FitArgs *s_args = reinterpret_cast<FitArgs *>(smem + fit_smem<BLOCK>());  // one per warp
+  // the parts come from one handle and share its pad-row table
   for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) s_rowx[i] = P.parts[0].row_x[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
