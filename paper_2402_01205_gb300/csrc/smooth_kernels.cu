@@ -61,6 +61,7 @@ namespace {
 
 constexpr int kSmoothBlock = 128;
 constexpr int kSmoothDerailPct = 80;  // as the fit: DERAILED below 80 % inward acceptance
+constexpr int kSmoothBitWords = kMaxRows / 32;  // forward accept bits of one track (<= 256 clusters)
 
 // absolute state of a track
 __device__ __forceinline__ void state_of(const Trk &T, float p[5]) {
@@ -249,7 +250,10 @@ __device__ __forceinline__ void load_cl(const FitArgs &A, int64_t k, Cl &c) {
   c.r = A.row[k];
 }
 
-__device__ void smooth_track(const FitArgs &A, int64_t t, float *pred) {
+// `bits`: the lane's column of forward accept bits in shared memory (word w at
+// bits[w * kSmoothBlock]), so that the backward filter writes each accept
+// byte once instead of reading back the forward filter's.
+__device__ void smooth_track(const FitArgs &A, int64_t t, float *pred, uint32_t *bits) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
   const int st0 = A.status[t];
   const float *sd = A.seed + 5 * t;
@@ -283,6 +287,8 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred) {
     cov_of(T, out_c);
     float xcur = xref;
     int64_t fw_done = a;  // clusters the forward filter updated with
+#pragma unroll
+    for (int w = 0; w < kSmoothBitWords; ++w) bits[w * kSmoothBlock] = 0u;
     if (st0 == ST_OK) {
       uint32_t gate_hi, gate_lo;
       split64(A.chi2_max_d, gate_hi, gate_lo);
@@ -313,7 +319,10 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred) {
           double chi2;
           const int ust = update(T, cur.y, cur.z, cur.vy, cur.vz, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
           if (ust != ST_OK) { st = ust; break; }
-          A.accept[k] = acc ? 1u : 0u;
+          if (acc) {
+            const int j = (int)(k - a);
+            bits[(j >> 5) * kSmoothBlock] |= 1u << (j & 31);
+          }
           nacc_out += acc ? 1 : 0;
           ++fw_done;
           rprev = rk;
@@ -389,7 +398,10 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred) {
             if (ust != ST_OK) { st = ust; break; }
             chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
             nacc += acc ? 1 : 0;
-            A.accept[k] = (uint8_t)(A.accept[k] | (acc ? 2u : 0u));
+            {
+              const int j = (int)(k - a);
+              A.accept[k] = (uint8_t)(((bits[(j >> 5) * kSmoothBlock] >> (j & 31)) & 1u) | (acc ? 2u : 0u));
+            }
             float pp[5], cp[15], ps[5], cs[15];
             state_of(T, pp);
             cov_of(T, cp);
@@ -427,15 +439,17 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred) {
         cov_of(T, out_c);
       }
     }
-    // accept bytes the forward filter did not reach; clusters without a smoothed state
-    for (int64_t q = fw_done; q < e; ++q) A.accept[q] = 0u;
+    // clusters without a smoothed state (the backward filter wrote the accept
+    // bytes of the others): their forward bit, 0 where the forward filter did
+    // not reach (the backward filter runs only after a complete forward pass,
+    // so fw_done <= smoothed_from whenever fw_done < e)
     for (int64_t q = a; q < smoothed_from; ++q) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) A.sm_state[5 * q + i] = qnan;
 #pragma unroll
       for (int i = 0; i < 15; ++i) A.sm_cov[15 * q + i] = qnan;
-      if (q >= fw_done) continue;
-      A.accept[q] = (uint8_t)(A.accept[q] & 1u);  // forward bit only
+      const int j = (int)(q - a);
+      A.accept[q] = q < fw_done ? (uint8_t)((bits[(j >> 5) * kSmoothBlock] >> (j & 31)) & 1u) : (uint8_t)0u;
     }
   }
   if (st0 == ST_BAD_INPUT) {
@@ -451,6 +465,7 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred) {
 }
 
 __global__ void __launch_bounds__(kSmoothBlock) k_smooth(FitArgs A) {
+  __shared__ uint32_t s_bits[kSmoothBitWords * kSmoothBlock];
   const int lane = threadIdx.x & 31;
   const size_t warp = ((size_t)blockIdx.x * kSmoothBlock + threadIdx.x) >> 5;
   float *pred = A.sm_pred + (warp * (size_t)A.n_rows * 32 + lane) * kPredSlot;  // this warp's scratch, this lane's slots
@@ -460,7 +475,7 @@ __global__ void __launch_bounds__(kSmoothBlock) k_smooth(FitArgs A) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)A.n_tracks) break;
     const int64_t i = (int64_t)base + lane;
-    if (i < A.n_tracks) smooth_track(A, A.perm ? (int64_t)A.perm[i] : i, pred);
+    if (i < A.n_tracks) smooth_track(A, A.perm ? (int64_t)A.perm[i] : i, pred, s_bits + threadIdx.x);
     __syncwarp();
   }
 }
