@@ -170,3 +170,30 @@ def test_engine_fits_the_parts_of_several_frames_in_one_launch(T):
     for r, rf in zip(res, ref):
         for k in rf:
             assert np.array_equal(r[k].numpy(), rf[k], equal_nan=k in ("state", "cov")), k
+
+
+def test_engine_under_budget_pressure_with_few_slots_and_small_parts(T):
+    """Frames of random sizes (1 to 4,000 tracks) through 3 slots, parts of
+    about 150,000 clusters and a budget of about two of the largest frames:
+    admission waits for memory and slots, engine launches take whatever parts
+    are ready, and every ticket finishes with the results of its plain fit."""
+    pool = tpcgen.generate("detector50k", n_tracks=60_000, seed=21)
+    sizes = np.random.default_rng(5).integers(1, 4_000, size=30)
+    frames, t0 = [], 0
+    for s in sizes:
+        frames.append(pool.subset(t0, t0 + int(s)))
+        t0 += int(s)
+    ref = [alone(T, f) for f in frames]
+    big = max(frames, key=lambda f: f.n_clusters)
+    budget = int(2 * (big.n_clusters * 24 + big.n_tracks * 140) + (8 << 20))
+    pinned = [pinned_frame(f) for f in frames]
+    with T.Fitter(hbm_budget_bytes=budget, max_slots=3, host_chunk_clusters=150_000) as fx:
+        res = [T.alloc_result(f.n_tracks, f.n_clusters, pinned=True) for f in frames]
+        tickets = [fx.submit(p, r) for p, r in zip(pinned, res)]
+        for tk in tickets:
+            assert fx.wait(tk, timeout_s=120)[0] == T.DONE
+        st = fx.serve_stats()
+    assert st["parts"] >= len(frames) and st["launches"] <= st["parts"]
+    for r, rf in zip(res, ref):
+        for k in rf:
+            assert np.array_equal(r[k].numpy(), rf[k], equal_nan=k in ("state", "cov")), k
