@@ -122,6 +122,20 @@ def test_parity_sees_swapped_variances(T):
     check(f, fit_gpu(T, f), orc)  # and the unswapped frame passes
 
 
+def test_parity_256_pad_rows(T):
+    """The largest geometry the library takes: 256 pad rows (0.625 cm apart,
+    exact in binary32, so the library's and the oracle's row tables agree),
+    tracks of up to 255 clusters that fill the 256 outward accept bits and run
+    the staging ring over 64 chunks; sorted and frame order."""
+    f = tpcgen.generate("detector50k", n_tracks=20_011, seed=13, n_rows=256, row_pitch=0.625)
+    n = np.diff(f.offsets)
+    assert n.max() >= 250 and (n > 230).sum() > 10_000
+    orc = oracle.fit(f, oracle.FitConfig(xx0=5e-4, n_rows=256, row_pitch=0.625), diagnostics=True)
+    for srt in (1, 0):
+        gpu = fit_gpu(T, f, n_rows=256, row_pitch_cm=0.625, sort_tracks=srt)
+        check(f, gpu, orc)
+
+
 def test_parity_full_size_pbpb_frame_sampled(T):
     """2,000,000 tracks fitted whole (benchmark launch); oracle on 8 blocks of 2,500 tracks."""
     f = tpcgen.generate("pbpb2m")

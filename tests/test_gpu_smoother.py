@@ -79,6 +79,15 @@ def test_smoother_matches_oracle(T, preset, kw):
     check(f, gpu, orc)
 
 
+def test_smoother_with_256_pad_rows(T):
+    """Tracks of up to 255 clusters: the forward predictions fill every slot of
+    the prediction scratch, which is sized by the handle's pad rows."""
+    f = tpcgen.generate("detector50k", n_tracks=10_007, seed=14, n_rows=256, row_pitch=0.625)
+    assert np.diff(f.offsets).max() >= 250
+    gpu = smooth_gpu(T, f, n_rows=256, row_pitch_cm=0.625)
+    check(f, gpu, oracle.smooth(f, oracle.FitConfig(n_rows=256, row_pitch=0.625)))
+
+
 def test_smoother_with_unequal_variances_and_edge_cases(T):
     f = tpcgen.generate("detector50k", n_tracks=20_011, seed=12, var_mode=1)
     gpu = smooth_gpu(T, f)
