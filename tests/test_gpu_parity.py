@@ -135,6 +135,17 @@ def test_parity_reversed_and_strong_field(T, bz):
     check(f, gpu, orc)
 
 
+def test_parity_high_momentum_tracks(T):
+    """pT of 20-1000 GeV/c: q/pT between 1e-3 and 5e-2, tracks almost
+    straight over the 162 cm of pad rows, where q/pT and its variance are
+    carried as small numbers (anchor + offset, compensated variance)."""
+    f = tpcgen.generate("detector50k", n_tracks=20_011, seed=23, pt_min=20.0, pt_max=1000.0)
+    gpu = fit_gpu(T, f)
+    orc = oracle.fit(f, orc_cfg(5e-4), diagnostics=True)
+    assert np.all(orc["status"] == 0)
+    check(f, gpu, orc)
+
+
 def test_parity_256_pad_rows(T):
     """The largest geometry the library takes: 256 pad rows (0.625 cm apart,
     exact in binary32, so the library's and the oracle's row tables agree),
