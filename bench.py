@@ -126,9 +126,9 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the sources the fit kernel is compiled from (its file and the shared device code)."""
+    """Hash of the sources the fit kernel is compiled from (its file, the shared device code and the staging)."""
     h = hashlib.sha256()
-    for name in ("fit_kernels.cu", "fit_device.cuh"):
+    for name in ("fit_kernels.cu", "fit_device.cuh", "stage_device.cuh"):
         with open(os.path.join(ROOT, "paper_2402_01205_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -36,16 +36,16 @@
 // knows far more than the other (near the ends of the track).
 //
 // One thread per track on the persistent grid of the fit (same sort, same
-// work counter); clusters are read directly from global memory (no staging
-// ring: a variant, not the benchmark path).  The 20 floats of a prediction
-// are kept in scratch owned by the warp, [cluster of the track][lane] slots of
-// 96 bytes (three whole 32-byte sectors, so that no sector is shared between
-// lanes whose tracks reach that cluster at different times) written and read
-// as five 16-byte vectors, where scalar accesses to the caller's per-cluster
-// slots took 20 requests per lane.  The backward filter loads a cluster's
-// prediction before it propagates to that cluster, so the load overlaps the
-// step's arithmetic; the smoothed outputs are written with the widest vector
-// stores their alignment allows.
+// work counter); both filters read the clusters through the fit's staging
+// ring (stage_device.cuh).  The 20 floats of a prediction are kept in scratch
+// owned by the warp as five 16-byte vectors laid out [row step of the
+// track][vector][lane]: the tracks of a warp cross as many rows and step
+// through them together, so a warp-wide vector access is one contiguous
+// 512-byte run (scalar accesses to the caller's per-cluster slots took 20
+// requests per lane).  The backward filter loads the next cluster's
+// prediction right after the combination at the current one, so the load
+// overlaps a whole step; the smoothed outputs are written with the widest
+// vector stores their alignment allows.
 
 #include <cuda_runtime.h>
 
@@ -53,6 +53,7 @@
 #include <stdint.h>
 
 #include "fit_device.cuh"
+#include "stage_device.cuh"
 #include "tpcfit_internal.h"
 
 namespace tpcfit {
@@ -99,8 +100,9 @@ __device__ __forceinline__ bool combine(const float pm[5], const float cm[15], c
     if (!(v > 0.0f)) return false;
     d[i] = rsqrtf(v);
   }
-  // L L^T = D S D (unit diagonal), lower triangle packed in place
-  float L[15];
+  // L L^T = D S D (unit diagonal), lower triangle packed in place; rl[j] =
+  // 1 / L_jj (the substitutions multiply by it instead of dividing)
+  float L[15], rl[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
@@ -113,6 +115,7 @@ __device__ __forceinline__ bool combine(const float pm[5], const float cm[15], c
     if (!(s > 0.0f)) return false;
     const float r = rsqrtf(s);
     L[pk(j, j)] = s * r;  // sqrt(s)
+    rl[j] = r;
 #pragma unroll
     for (int i = j + 1; i < 5; ++i) {
       float t = L[pk(i, j)];
@@ -133,14 +136,14 @@ __device__ __forceinline__ bool combine(const float pm[5], const float cm[15], c
       float t = v[i];
 #pragma unroll
       for (int m = 0; m < i; ++m) t = fmaf(-L[pk(i, m)], v[m], t);
-      v[i] = t / L[pk(i, i)];
+      v[i] = t * rl[i];
     }
 #pragma unroll
     for (int i = 4; i >= 0; --i) {  // L^T x = y
       float t = v[i];
 #pragma unroll
       for (int m = i + 1; m < 5; ++m) t = fmaf(-L[pk(m, i)], v[m], t);
-      v[i] = t / L[pk(i, i)];
+      v[i] = t * rl[i];
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) X[i][c] = d[i] * v[i];
@@ -194,12 +197,18 @@ __device__ void seed_cov_of(const FitArgs &A, Trk &T) {
   T.clear_comp();
 }
 
-constexpr int kPredSlot = 24;  // floats per prediction slot (20 used): 96 bytes
+constexpr int kPredVec = 5;  // 16-byte vectors of one prediction (20 floats)
 
-// The prediction slot of cluster j of the lane's track in the warp's scratch
-// (`pred` = the warp's base + the lane's slot).
-__device__ __forceinline__ float4 *pred_slot(float *pred, int j) {
-  return reinterpret_cast<float4 *>(pred + j * (32 * kPredSlot));
+// Vector q of the prediction at row step j (row of the track's first
+// cluster + j) of the lane's track in the warp's scratch, laid out [row step
+// j][vector q][lane] (`pred` = the warp's base + the lane's 16-byte column):
+// the lanes' q-th vectors of one row step are one contiguous 512-byte run.
+// The tracks of a warp cross as many rows and step through them together, so
+// the lanes that have a cluster on the step's row write that run at once and
+// read it back at once (rows without a cluster leave their lane's entries
+// unused).
+__device__ __forceinline__ float4 *pred_vec(float *pred, int j, int q) {
+  return reinterpret_cast<float4 *>(pred + (j * kPredVec + q) * (32 * 4));
 }
 
 // N floats to a 4-byte aligned address whose first H floats lie before a
@@ -234,26 +243,37 @@ template <int N> __device__ __forceinline__ void store_vec(float *dst, const flo
   }
 }
 
-// One cluster as the filters read it.  Each pass keeps the current cluster and
-// the loads of the next one in the pass direction, issued when the current one
-// became current, so that their latency overlaps a whole step.
-struct Cl {
-  float x, y, z, vy, vz;
-  int r;
-};
-__device__ __forceinline__ void load_cl(const FitArgs &A, int64_t k, Cl &c) {
-  c.x = A.x[k];
-  c.y = A.y[k];
-  c.z = A.z[k];
-  c.vy = A.sy2[k];
-  c.vz = A.sz2[k];
-  c.r = A.row[k];
+// The forward prediction (state and packed covariance) at row step j of the
+// lane's track.
+__device__ __forceinline__ void store_pred(float *pred, int j, const float pm[5], const float cm[15]) {
+  *pred_vec(pred, j, 0) = make_float4(pm[0], pm[1], pm[2], pm[3]);
+  *pred_vec(pred, j, 1) = make_float4(pm[4], cm[0], cm[1], cm[2]);
+  *pred_vec(pred, j, 2) = make_float4(cm[3], cm[4], cm[5], cm[6]);
+  *pred_vec(pred, j, 3) = make_float4(cm[7], cm[8], cm[9], cm[10]);
+  *pred_vec(pred, j, 4) = make_float4(cm[11], cm[12], cm[13], cm[14]);
+}
+__device__ __forceinline__ void load_pred(const float *pred, int j, float pm[5], float cm[15]) {
+  float *pw = const_cast<float *>(pred);
+  const float4 s0 = *pred_vec(pw, j, 0), s1 = *pred_vec(pw, j, 1), s2 = *pred_vec(pw, j, 2), s3 = *pred_vec(pw, j, 3),
+               s4 = *pred_vec(pw, j, 4);
+  pm[0] = s0.x; pm[1] = s0.y; pm[2] = s0.z; pm[3] = s0.w; pm[4] = s1.x;
+  cm[0] = s1.y; cm[1] = s1.z; cm[2] = s1.w;
+  cm[3] = s2.x; cm[4] = s2.y; cm[5] = s2.z; cm[6] = s2.w;
+  cm[7] = s3.x; cm[8] = s3.y; cm[9] = s3.z; cm[10] = s3.w;
+  cm[11] = s4.x; cm[12] = s4.y; cm[13] = s4.z; cm[14] = s4.w;
 }
 
-// `bits`: the lane's column of forward accept bits in shared memory (word w at
-// bits[w * kSmoothBlock]), so that the backward filter writes each accept
-// byte once instead of reading back the forward filter's.
-__device__ void smooth_track(const FitArgs &A, int64_t t, float *pred, uint32_t *bits) {
+// Smoothing of track t by one lane.  Clusters are staged as in the fit (the
+// lane's column of the block's staging ring: `f4`, `wrow`; copies issued and
+// waited for at warp-uniform steps every kChunk rows of a pass), the pad-row
+// table is `s_rowx`, `bits` the lane's column of forward accept bits (word w
+// at bits[w * kSmoothBlock]), so that the backward filter writes each accept
+// byte once instead of reading back the forward filter's, and `pred` the
+// lane's column of the warp's prediction scratch.  The backward filter loads the next cluster's
+// prediction as soon as the combination of the current one has used its
+// registers, a whole step ahead of its use.
+__device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, float *f4, uint32_t *wrow,
+                             uint32_t *bits, float *pred) {
   const int64_t a = A.off[t] - A.off_base, e = A.off[t + 1] - A.off_base;
   const int st0 = A.status[t];
   const float *sd = A.seed + 5 * t;
@@ -286,72 +306,83 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred, uint32_t 
     state_of(T, out_p);  // the outputs of a track that is not fitted
     cov_of(T, out_c);
     float xcur = xref;
-    int64_t fw_done = a;  // clusters the forward filter updated with
+    int fw_done = 0;  // clusters the forward filter updated with
 #pragma unroll
     for (int w = 0; w < kSmoothBitWords; ++w) bits[w * kSmoothBlock] = 0u;
     if (st0 == ST_OK) {
       uint32_t gate_hi, gate_lo;
       split64(A.chi2_max_d, gate_hi, gate_lo);
+      const int lead = chunk_lead(A, a);
+      const uint32_t rsh = (uint32_t)((reinterpret_cast<uintptr_t>(A.row) + (uintptr_t)(a - lead)) & 3u);
+      const int nch = (lead + n + kChunk - 1) / kChunk;
       // ---------------- forward filter (outward pass) ----------------
+      int kc = 0;
+      int staged = nch < kStageBufs ? nch : kStageBufs;  // chunks 0 .. staged-1 issued
+      for (int c = 0; c < staged; ++c) stage_chunk<kSmoothBlock>(A, a, e, lead, rsh, c, c, f4, wrow);
+      cp_async_wait_all();
+      int cbuf = 0;  // buffer of the current chunk
+      uint32_t rows_cur = staged_rows<kSmoothBlock>(wrow, 0, rsh);
+      Clu cand = read_staged<kSmoothBlock>(f4, lead, 0, rows_cur);
       int nacc_out = 0, rprev = -1;
-      int64_t k = a;
-      Cl cur, nxt;
-      load_cl(A, k, cur);
-      if (k + 1 < e) load_cl(A, k + 1, nxt);
-      int rk = cur.r;
-      st = check_cluster(rk, rprev, A.n_rows, cur.x, cur.y, cur.z, cur.vy, cur.vz);
-      for (int r = rk; st == ST_OK; ++r) {
-        const bool has = (rk == r);
-        const float xt = has ? cur.x : A.row_x[r];
+      const int r0 = cand.r;  // predictions are kept by row step r - r0
+      st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
+      for (int r = cand.r, step = 0; st == ST_OK; ++r, ++step) {
+        if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
+          cp_async_wait_all();
+          if (staged < nch && staged <= ((kc + lead) >> 2) + 2) {  // the buffer of chunk staged-3 is consumed
+            stage_chunk<kSmoothBlock>(A, a, e, lead, rsh, staged, staged % kStageBufs, f4, wrow);
+            ++staged;
+          }
+        }
+        const bool has = (cand.r == r);
+        const float xt = has ? cand.x : s_rowx[r];
         if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
         xcur = xt;
         if (has) {
-          float pm[5], cm[15];
-          state_of(T, pm);
-          cov_of(T, cm);
-          float4 *slot = pred_slot(pred, (int)(k - a));
-          slot[0] = make_float4(pm[0], pm[1], pm[2], pm[3]);
-          slot[1] = make_float4(pm[4], cm[0], cm[1], cm[2]);
-          slot[2] = make_float4(cm[3], cm[4], cm[5], cm[6]);
-          slot[3] = make_float4(cm[7], cm[8], cm[9], cm[10]);
-          slot[4] = make_float4(cm[11], cm[12], cm[13], cm[14]);
+          {
+            float pm[5], cm[15];
+            state_of(T, pm);
+            cov_of(T, cm);
+            store_pred(pred, r - r0, pm, cm);
+          }
           bool acc;
           double chi2;
-          const int ust = update(T, cur.y, cur.z, cur.vy, cur.vz, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
+          const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
           if (ust != ST_OK) { st = ust; break; }
-          if (acc) {
-            const int j = (int)(k - a);
-            bits[(j >> 5) * kSmoothBlock] |= 1u << (j & 31);
-          }
+          if (acc) bits[(kc >> 5) * kSmoothBlock] |= 1u << (kc & 31);
           nacc_out += acc ? 1 : 0;
           ++fw_done;
-          rprev = rk;
-          if (++k < e) {
-            cur = nxt;
-            if (k + 1 < e) load_cl(A, k + 1, nxt);
-            rk = cur.r;
-            const int vs = check_cluster(rk, rprev, A.n_rows, cur.x, cur.y, cur.z, cur.vy, cur.vz);
+          rprev = cand.r;
+          if (++kc < n) {
+            const int p = kc + lead;
+            if ((p & 3) == 0) {  // entering chunk p/4 (arrived)
+              cbuf = cbuf == kStageBufs - 1 ? 0 : cbuf + 1;
+              rows_cur = staged_rows<kSmoothBlock>(wrow, cbuf, rsh);
+            }
+            cand = read_staged<kSmoothBlock>(f4, p & 3, cbuf, rows_cur);
+            const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
             if (vs != ST_OK) { st = vs; break; }
           }
         }
         if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
-        if (k == e) break;
+        if (kc == n) break;
       }
       if (st == ST_OK) {
         // ---------------- restart, as the fit's inward pass ----------------
+        // cand holds the outermost cluster n-1
         const bool fw_valid = 100 * nacc_out >= A.reseed_pct * n;
         if (!fw_valid) {
           float p[5];
           const int64_t m = a + n / 2;
-          seed3(A.x[e - 1], A.y[e - 1], A.z[e - 1], A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
+          seed3(cand.x, cand.y, cand.z, A.x[m], A.y[m], A.x[a], A.y[a], A.z[a], A.b, p);
           T.sp = -p[2];
           T.spl = 0.f;
           T.tl0 = -p[3];
           T.dtl = 0.f;
           T.w0 = -p[4];
           T.dw = 0.f;
-          T.ya = A.y[e - 1];
-          T.za = A.z[e - 1];
+          T.ya = cand.y;
+          T.za = cand.z;
           T.dy = 0.f;
           T.dz = 0.f;
           seed_cov_of(A, T);
@@ -371,57 +402,62 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred, uint32_t 
           T.clear_comp();
         }
         // ---------------- backward filter and combination ----------------
-        k = e - 1;
-        load_cl(A, k, cur);
-        if (k - 1 >= a) load_cl(A, k - 1, nxt);
-        rk = cur.r;
-        for (int r = rk, step = 0;; --r, ++step) {
-          const bool has = (rk == r);
-          const float xt = has ? cur.x : A.row_x[r];
-          float pm[5], cm[15];  // the forward prediction at this cluster, loaded ahead of its use
-          if (has && fw_valid) {
-            const float4 *slot = pred_slot(pred, (int)(k - a));
-            const float4 s0 = slot[0], s1 = slot[1], s2 = slot[2], s3 = slot[3], s4 = slot[4];
-            pm[0] = s0.x; pm[1] = s0.y; pm[2] = s0.z; pm[3] = s0.w; pm[4] = s1.x;
-            cm[0] = s1.y; cm[1] = s1.z; cm[2] = s1.w;
-            cm[3] = s2.x; cm[4] = s2.y; cm[5] = s2.z; cm[6] = s2.w;
-            cm[7] = s3.x; cm[8] = s3.y; cm[9] = s3.z; cm[10] = s3.w;
-            cm[11] = s4.x; cm[12] = s4.y; cm[13] = s4.z; cm[14] = s4.w;
+        // the ring holds the last kStageBufs chunks, arrived; the last is current
+        kc = n - 1;
+        int lowest = nch > kStageBufs ? nch - kStageBufs : 0;  // the lowest chunk issued
+        float pm[5], cm[15];  // the forward prediction at the current cluster, loaded a step ahead of its use
+        if (fw_valid) load_pred(pred, cand.r - r0, pm, cm);
+        for (int r = cand.r, step = 0;; --r, ++step) {
+          if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
+            cp_async_wait_all();
+            if (lowest > 0 && lowest + 1 >= ((kc + lead) >> 2)) {  // the buffer of chunk lowest+2 is consumed
+              --lowest;
+              stage_chunk<kSmoothBlock>(A, a, e, lead, rsh, lowest, lowest % kStageBufs, f4, wrow);
+            }
           }
+          const bool has = (cand.r == r);
+          const float xt = has ? cand.x : s_rowx[r];
           if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
           xcur = xt;
           if (step > 0 && A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);  // the row's kink lies beyond its measurement
           if (has) {
             bool acc;
             double chi2;
-            const int ust = update(T, cur.y, cur.z, cur.vy, cur.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc, chi2);
+            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc, chi2);
             if (ust != ST_OK) { st = ust; break; }
             chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
             nacc += acc ? 1 : 0;
+            const int64_t k = a + kc;
+            A.accept[k] = (uint8_t)(((bits[(kc >> 5) * kSmoothBlock] >> (kc & 31)) & 1u) | (acc ? 2u : 0u));
+            float ps[5], cs[15];
             {
-              const int j = (int)(k - a);
-              A.accept[k] = (uint8_t)(((bits[(j >> 5) * kSmoothBlock] >> (j & 31)) & 1u) | (acc ? 2u : 0u));
+              float pp[5], cp[15];
+              state_of(T, pp);
+              cov_of(T, cp);
+              if (fw_valid) {
+                if (!combine(pm, cm, pp, cp, ps, cs)) { st = ST_NOT_PD; break; }
+              } else {
+                store5(ps, pp);
+                store15(cs, cp);
+              }
             }
-            float pp[5], cp[15], ps[5], cs[15];
-            state_of(T, pp);
-            cov_of(T, cp);
-            if (fw_valid) {
-              if (!combine(pm, cm, pp, cp, ps, cs)) { st = ST_NOT_PD; break; }
-            } else {
-              store5(ps, pp);
-              store15(cs, cp);
+            if (--kc >= 0) {
+              const int p = kc + lead;
+              if ((p & 3) == 3) {  // entering chunk p/4 from above (arrived)
+                cbuf = cbuf == 0 ? kStageBufs - 1 : cbuf - 1;
+                rows_cur = staged_rows<kSmoothBlock>(wrow, cbuf, rsh);
+              }
+              cand = read_staged<kSmoothBlock>(f4, p & 3, cbuf, rows_cur);
+              if (fw_valid) load_pred(pred, cand.r - r0, pm, cm);  // the next cluster's, a step ahead
             }
             store_vec<5>(A.sm_state + 5 * k, ps);
             store_vec<15>(A.sm_cov + 15 * k, cs);
             smoothed_from = k;
-            if (k == a) {
+            if (kc < 0) {
               store5(out_p, ps);
               store15(out_c, cs);
+              break;
             }
-            if (--k < a) break;
-            cur = nxt;
-            if (k - 1 >= a) load_cl(A, k - 1, nxt);
-            rk = cur.r;
           }
         }
         if (st == ST_OK) {
@@ -434,6 +470,7 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred, uint32_t 
         }
         if (st == ST_OK && 100 * nacc < kSmoothDerailPct * n) st = ST_DERAILED;
       }
+      cp_async_wait_all();  // no copy may land in the column after this track
       if (st != ST_OK && st != ST_DERAILED) {  // a failed fit: the state where it stopped
         state_of(T, out_p);
         cov_of(T, out_c);
@@ -442,14 +479,14 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred, uint32_t 
     // clusters without a smoothed state (the backward filter wrote the accept
     // bytes of the others): their forward bit, 0 where the forward filter did
     // not reach (the backward filter runs only after a complete forward pass,
-    // so fw_done <= smoothed_from whenever fw_done < e)
+    // so a + fw_done <= smoothed_from whenever fw_done < n)
     for (int64_t q = a; q < smoothed_from; ++q) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) A.sm_state[5 * q + i] = qnan;
 #pragma unroll
       for (int i = 0; i < 15; ++i) A.sm_cov[15 * q + i] = qnan;
       const int j = (int)(q - a);
-      A.accept[q] = q < fw_done ? (uint8_t)((bits[(j >> 5) * kSmoothBlock] >> (j & 31)) & 1u) : (uint8_t)0u;
+      A.accept[q] = j < fw_done ? (uint8_t)((bits[(j >> 5) * kSmoothBlock] >> (j & 31)) & 1u) : (uint8_t)0u;
     }
   }
   if (st0 == ST_BAD_INPUT) {
@@ -464,18 +501,30 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, float *pred, uint32_t 
   A.status[t] = st;
 }
 
+// Shared memory of k_smooth: the fit's staging (pad-row table, chunk ring,
+// row words) and the forward accept bits, over kSmoothBlock track columns.
+constexpr size_t kSmoothSmem = stage_smem<kSmoothBlock>() + (size_t)kSmoothBitWords * kSmoothBlock * sizeof(uint32_t);
+
 __global__ void __launch_bounds__(kSmoothBlock) k_smooth(FitArgs A) {
-  __shared__ uint32_t s_bits[kSmoothBitWords * kSmoothBlock];
+  __shared__ __align__(16) unsigned char smem[kSmoothSmem];
+  float *s_rowx = reinterpret_cast<float *>(smem);
+  float *s_f4 = reinterpret_cast<float *>(smem + kSmemRowx);
+  uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + kSmemRowx + smem_f4<kSmoothBlock>());
+  uint32_t *s_bits = s_w + kStageBufs * 2 * kSmoothBlock;
+  for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) s_rowx[i] = A.row_x[i];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const size_t warp = ((size_t)blockIdx.x * kSmoothBlock + threadIdx.x) >> 5;
-  float *pred = A.sm_pred + (warp * (size_t)A.n_rows * 32 + lane) * kPredSlot;  // this warp's scratch, this lane's slots
+  float *pred = A.sm_pred + warp * (size_t)A.n_rows * (32 * 4 * kPredVec) + 4 * lane;  // this warp's scratch, this lane's column
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(A.work, 32ull);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)A.n_tracks) break;
     const int64_t i = (int64_t)base + lane;
-    if (i < A.n_tracks) smooth_track(A, A.perm ? (int64_t)A.perm[i] : i, pred, s_bits + threadIdx.x);
+    if (i < A.n_tracks)
+      smooth_track(A, A.perm ? (int64_t)A.perm[i] : i, s_rowx, s_f4 + 4 * threadIdx.x, s_w + threadIdx.x,
+                   s_bits + threadIdx.x, pred);
     __syncwarp();
   }
 }
@@ -493,17 +542,17 @@ int smooth_grid() {
   return sms * per_sm;
 }
 
-// Scratch of the forward predictions: per warp of the grid, a 96-byte slot
-// for each of up to n_rows clusters of each of its 32 lanes' tracks (a track
-// has at most one cluster per pad row).
+// Scratch of the forward predictions: per warp of the grid, 80 bytes for
+// each of up to n_rows clusters of each of its 32 lanes' tracks (a track has
+// at most one cluster per pad row).
 size_t smooth_pred_bytes(int grid, int n_rows) {
-  return (size_t)grid * (kSmoothBlock / 32) * (size_t)n_rows * 32 * kPredSlot * sizeof(float);
+  return (size_t)grid * (kSmoothBlock / 32) * (size_t)n_rows * 32 * 4 * kPredVec * sizeof(float);
 }
 
 cudaError_t launch_smooth(const FitArgs &a, int grid, cudaStream_t stream) {
   if (a.n_tracks <= 0) return cudaSuccess;
   if (!a.sm_state || !a.sm_cov || !a.sm_pred || grid <= 0) return cudaErrorInvalidValue;
-  k_smooth<<<grid, kSmoothBlock, 0, stream>>>(a);
+  k_smooth<<<grid, kSmoothBlock, 0, stream>>>(fit_args_for_launch(a));  // with stage_vec set
   return cudaGetLastError();
 }
 
