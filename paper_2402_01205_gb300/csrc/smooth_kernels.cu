@@ -338,13 +338,14 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, f
         const float xt = has ? cand.x : s_rowx[r];
         if (!propagate(T, xt - xcur, A.b, A.snp_max)) { st = ST_SNP_LIMIT; break; }
         xcur = xt;
+        {  // the prediction at every row step, also on rows without a cluster (never read back there):
+           // the warp's stores then cover whole sectors, which L2 takes without reading them from DRAM
+          float pm[5], cm[15];
+          state_of(T, pm);
+          cov_of(T, cm);
+          store_pred(pred, r - r0, pm, cm);
+        }
         if (has) {
-          {
-            float pm[5], cm[15];
-            state_of(T, pm);
-            cov_of(T, cm);
-            store_pred(pred, r - r0, pm, cm);
-          }
           bool acc;
           double chi2;
           const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
