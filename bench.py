@@ -56,7 +56,8 @@ WORKLOADS = {"pbpb2m": "Pb-Pb-scale time frame: 2,000,000 tracks, exponential pT
 FIT_PARAMS = {"pbpb2m_eloss": ({"xrho_per_row": 0.0145}, {"xrho": 0.0145})}
 # the metric of the benchmark, the same string in both arms
 METRIC = "clusters/s and tracks/s fitted on 1 GB300 at stated FP64-oracle error; p50/p99 frame latency"
-FP64_PER_CLUSTER = 11         # FP64 lane-instructions per cluster: 4 (outward update) + 7 (inward update + sum)
+FP64_PER_CLUSTER = 11         # the FP64 island as the method states it, per cluster: 4 (outward det, gate) + 7 (inward det, reciprocal, chi2, sum)
+FP64_EXECUTED_PER_CLUSTER = 8 # FP64 lane-instructions the kernel executes per cluster (ncu): 2 (outward det) + 6 (inward)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
 
@@ -173,20 +174,25 @@ def fit_roofline(nc, nt, nc_fit, fit_s, launch, probe, sms, sm_mhz, variant: str
     """Roofline of the fit kernel against its binding algorithmic roof.
 
     The fit's algorithmic work per cluster is 11 FP64 lane-operations (the
-    innovation-matrix determinant, the outward gate, the inward reciprocal,
-    chi2 and its sum; a lane-operation = one lane of one FP64 instruction,
-    an FMA counting once), about 725 FP32 flops, and 22 bytes of HBM
-    traffic (+108 per track).  On GB300 the FP64 roof binds: the kernel
-    cannot beat 11 lane-ops per cluster at the FP64 pipe's rate.  So
-    ``achieved`` = FP64 lane-ops per launch / mean launch time, ``peak`` =
-    the FP64 FMA rate measured live in the same run (one lane-op per FMA),
-    and beside it the FP32 and HBM fractions and the instruction-issue
+    FP64 island as the method states it: in the outward update the
+    innovation-matrix determinant and the gate, in the inward update the
+    determinant, the reciprocal, chi2 and its sum; a lane-operation = one
+    lane of one FP64 instruction, an FMA counting once), about 800 FP32
+    flops, and 22 bytes of HBM traffic (+108 per track).  On GB300 the FP64
+    roof binds.  So ``achieved`` = FP64 lane-ops per launch / mean launch
+    time, ``peak`` = the FP64 FMA rate measured live in the same run (one
+    lane-op per FMA), and beside it the FP64 pipe's own share (the kernel
+    executes 8 of the 11 on the FP64 pipe: the outward gate is decided in
+    binary32 with the FP64 outcome, and the inward reciprocal and chi2 take
+    3 instead of 4), the FP32 and HBM fractions and the instruction-issue
     roof (from the ncu counters committed for this kernel and launch)."""
     peaks, peak_src = measured_peaks()
     c, note = profiled_counters(nc, launch, variant)
     fp64 = FP64_PER_CLUSTER * passes * nc_fit / fit_s  # each seed iteration repeats both passes
     hbm = (BYTES_PER_CLUSTER * nc + BYTES_PER_TRACK * nt) / fit_s / 1e9
     beside = {
+        "fp64_pipe": {"executed_lane_ops_per_cluster": FP64_EXECUTED_PER_CLUSTER,
+                      "frac": FP64_EXECUTED_PER_CLUSTER * passes * nc_fit / fit_s / probe["fp64_fma_per_s"]},
         "hbm": {"achieved_gbs": hbm, "peak_gbs": peaks["hbm_gbs"], "frac": hbm / peaks["hbm_gbs"],
                 "peak_source": peak_src, "bytes_per_cluster": BYTES_PER_CLUSTER, "bytes_per_track": BYTES_PER_TRACK},
     }

@@ -55,17 +55,6 @@ __device__ __forceinline__ bool le0_finite64(double x) {
   split64(x, hi, lo);
   return (int32_t)hi < 0 || (hi | lo) == 0u;
 }
-// binary64 -> binary32 narrowing with integer operations, rounding toward
-// zero (relative error below 2^-23), for a positive x whose magnitude lies in
-// the normal binary32 range; `other` for any x outside it (zero, negative,
-// subnormal or too large as a binary32, non-finite).
-__device__ __forceinline__ float narrow_pos_or(double x, float other) {
-  uint32_t hi, lo;
-  split64(x, hi, lo);
-  // biased binary64 exponent in [897, 1150] <=> binary32 exponent in [1, 254]; sign bit clear
-  const bool in_range = hi - (897u << 20) < (254u << 20);
-  return in_range ? __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29)) : other;
-}
 // x <= g for a finite x and a positive finite g given as (ghi, glo).
 __device__ __forceinline__ bool le_finite64(double x, uint32_t ghi, uint32_t glo) {
   uint32_t hi, lo;
@@ -324,19 +313,41 @@ __device__ __forceinline__ void quad_form2(float S00, float S10, float S11, floa
   ql = vadd(ql, vadd(vl, wl));
 }
 
+// The chi2 gate of the Kalman update: chi2_max (configured in binary32) as
+// binary64, its two 32-bit halves (integer comparisons of FP64 values) and
+// as binary32.
+struct Gate {
+  double d;
+  uint32_t hi, lo;
+  float f;
+};
+__device__ __forceinline__ Gate make_gate(float chi2_max, double chi2_max_d) {
+  Gate g;
+  g.d = chi2_max_d;
+  split64(chi2_max_d, g.hi, g.lo);
+  g.f = chi2_max;
+  return g;
+}
+
 // Gated Kalman update with the cluster (yc, zc, vy, vz).  FP64 island: the
-// inversion of S -- its determinant, and where the chi2 value is needed
-// (inward pass, diagnostics) the reciprocal of det (Newton step from an FP32
-// seed), chi2 = q / det and (by the caller) the chi2 sum; otherwise the gate
-// is decided in FP64 as q - chi2_max det <= 0.  The quadratic form
-// q = r^T adj(S) r enters as the exact binary64 sum of its two binary32
-// parts.  The gain's S^-1 = adj(S) / det takes its 1/det from the FP64
+// inversion of S -- its determinant det = S00 S11 - S10^2 (the products of
+// the binary32 entries are exact in binary64, rounded once) and, where the
+// chi2 value is needed (inward pass, diagnostics), chi2 = q / det with one
+// FP64 Newton correction of the binary32 reciprocal, and (by the caller) the
+// chi2 sum.  The quadratic form q = r^T adj(S) r is an unevaluated sum of two
+// binary32 numbers (quad_form2).  Without the chi2 value the gate
+// q - chi2_max det <= 0 is decided in binary32 from det narrowed toward zero
+// when its margin exceeds 2^-19 of the magnitudes of its terms (every rounding
+// of that evaluation stays below 2^-21 of them, so its sign is that of the
+// exact value, which the FP64 evaluation also gives), else in FP64: the same
+// decision as the FP64 evaluation, at 2 FP64 operations per outward update
+// instead of 4.  The gain's S^-1 = adj(S) / det takes its 1/det from the FP64
 // determinant (narrowed to binary32 by integer operations), so that the
 // cancellation in det of a strongly correlated S does not reach the gain.
 // Non-finite innovation matrices or residuals give chi2 = NaN and a rejected
 // cluster, as in FP64.  Returns the status (OK, or NOT_PD with T unchanged).
-__device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, double gate, uint32_t gate_hi,
-                                      uint32_t gate_lo, bool want_chi2, bool &acc, double &chi2) {
+__device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, const Gate &G, bool want_chi2,
+                                      bool &acc, double &chi2) {
   float *c = T.c;
   const float r0 = vsub(vsub(yc, T.ya), T.dy);
   const float r1 = vsub(vsub(zc, T.za), T.dz);
@@ -347,18 +358,35 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
   // ---- FP64 island ----
   const double s00 = widen_pos(S00), s11 = widen_pos(S11), s10 = widen(S10);
   const double det = __fma_rn(s00, s11, -__dmul_rn(s10, s10));  // exact products of the binary32 S: rounded once
-  // the gain's 1/det and the FP32 seed of the FP64 reciprocal, from the FP64 determinant
-  const float i32 = __fdividef(1.0f, narrow_pos_or(det, vfma(S00, S11, -vmul(S10, S10))));
-  const double qhd = widen(qh), qld = widen(ql);
+  // det narrowed to binary32 toward zero (relative error below 2^-23) where it
+  // lies in the normal binary32 range (d_in); the gain's 1/det and the seed of
+  // the FP64 reciprocal come from it
+  uint32_t dhi, dlo;
+  split64(det, dhi, dlo);
+  const bool d_in = dhi - (897u << 20) < (254u << 20);
+  const float d32 = __uint_as_float(((dhi - (896u << 20)) << 3) | (dlo >> 29));
+  const float i32 = __fdividef(1.0f, d_in ? d32 : vfma(S00, S11, -vmul(S10, S10)));
   chi2 = 0.0;
   if (want_chi2) {
-    const double y0 = widen_pos(i32);
-    const double ey = __fma_rn(-det, y0, 1.0);
-    const double inv = __fma_rn(y0, ey, y0);  // 1/det, one Newton step
-    chi2 = __fma_rn(qhd, inv, __dmul_rn(qld, inv));
-    acc = le_finite64(chi2, gate_hi, gate_lo);
+    // q / det = q y0 / (1 - e) with y0 = i32 and e = 1 - det y0 (|e| < 2^-21):
+    // q y0 = p + pl to twice the binary32 precision (q renormalised so that
+    // its low part is below half an ulp of its high part, the error-free
+    // product of the high part and y0, plus the low part times y0), times
+    // (1 + e) in FP64: relative error O(e^2), about 2^-42
+    float qn, qnl, p, pe;
+    fast_two_sum(qh, ql, qn, qnl);
+    two_prod(qn, i32, p, pe);
+    const float pl = vfma(qnl, i32, pe);
+    const double e = __fma_rn(-det, widen_pos(i32), 1.0);
+    const double P = widen(p);
+    chi2 = __dadd_rn(P, __fma_rn(P, e, widen(pl)));
+    acc = le_finite64(chi2, G.hi, G.lo);
   } else {
-    acc = le0_finite64(__dadd_rn(__fma_rn(-gate, det, qhd), qld));
+    const float m = vadd(vfma(-G.f, d32, qh), ql);
+    const float mag = vadd(vfma(G.f, d32, fabsf(qh)), fabsf(ql));
+    acc = m < 0.0f;
+    if (!(d_in && fabsf(m) > vmul(0x1p-19f, mag)))  // near the boundary, or det outside binary32
+      acc = le0_finite64(__dadd_rn(__fma_rn(-G.d, det, widen(qh)), widen(ql)));
   }
   // ---- back to FP32 ----
   if (!fin) {

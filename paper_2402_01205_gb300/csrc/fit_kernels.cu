@@ -20,15 +20,17 @@
 // descriptors from a device table.
 //
 // Precision: propagation, covariance transport and the gain/update are FP32.
-// The innovation-matrix determinant and reciprocal, the quadratic form
-// chi2 = r^T S^-1 r, the gate decision and the chi2 sum are FP64.  GB300
-// executes FP64 at ~1/64 of the FP32 rate and a warp-wide FP64 instruction
-// costs the same with one active lane as with 32, so the FP64 island is kept
-// to 4 instructions per outward update (det, gate) and 7 per inward update
-// (det, reciprocal, chi2, sum); the quadratic form of the residual is formed
-// in twice the binary32 precision on the FP32 pipe, every FP32->FP64 widening
-// is done with integer operations, and warps are filled with tracks of equal
-// length so that the FP64 instructions of a step serve (almost) every lane.
+// The innovation-matrix determinant, the reciprocal correction of chi2 =
+// r^T S^-1 r and the chi2 sum are FP64.  GB300 executes FP64 at ~1/64 of the
+// FP32 rate and a warp-wide FP64 instruction costs the same with one active
+// lane as with 32, so the FP64 island is kept to 2 instructions per outward
+// update (det; the gate is decided in FP64 only within 2^-19 of its boundary,
+// else in binary32 with the same outcome) and 6 per inward update (det,
+// reciprocal correction and chi2, sum); the quadratic form of the residual is
+// formed in twice the binary32 precision on the FP32 pipe, every FP32->FP64
+// widening is done with integer operations, and warps are filled with tracks
+// of equal length so that the FP64 instructions of a step serve (almost)
+// every lane.
 //
 // Track positions are carried as FP32 offsets (dy, dz) from the last
 // cluster's coordinates: residuals are then formed from small numbers and the
@@ -202,8 +204,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
     int done = 0;      // clusters (from the outer end) whose accept byte is final
     int out_done = 0;  // clusters the outward pass updated with
     if (st0 == ST_OK) {
-      uint32_t gate_hi, gate_lo;
-      split64(A.chi2_max_d, gate_hi, gate_lo);
+      const Gate gate = make_gate(A.chi2_max, A.chi2_max_d);
       const int lead = chunk_lead(A, a);
       const uint32_t rsh = (uint32_t)((reinterpret_cast<uintptr_t>(A.row) + (uintptr_t)(a - lead)) & 3u);
       const int nch = (lead + n + kChunk - 1) / kChunk;
@@ -244,7 +245,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           if (has) {
             bool acc;
             double chi2;
-            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo,
+            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate,
                                    A.chi2_out_c != nullptr, acc, chi2);
             if (ust != ST_OK) { st = ust; break; }
             if (acc) bits[NCOL * (kc >> 5)] |= 1u << (kc & 31);
@@ -346,7 +347,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             if (has) {
               bool acc;
               double chi2;
-              const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc,
+              const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate, true, acc,
                                      chi2);
               if (ust != ST_OK) { st = ust; break; }
               if (A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;

@@ -310,8 +310,7 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, f
 #pragma unroll
     for (int w = 0; w < kSmoothBitWords; ++w) bits[w * kSmoothBlock] = 0u;
     if (st0 == ST_OK) {
-      uint32_t gate_hi, gate_lo;
-      split64(A.chi2_max_d, gate_hi, gate_lo);
+      const Gate gate = make_gate(A.chi2_max, A.chi2_max_d);
       const int lead = chunk_lead(A, a);
       const uint32_t rsh = (uint32_t)((reinterpret_cast<uintptr_t>(A.row) + (uintptr_t)(a - lead)) & 3u);
       const int nch = (lead + n + kChunk - 1) / kChunk;
@@ -348,7 +347,7 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, f
         if (has) {
           bool acc;
           double chi2;
-          const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
+          const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate, false, acc, chi2);
           if (ust != ST_OK) { st = ust; break; }
           if (acc) bits[(kc >> 5) * kSmoothBlock] |= 1u << (kc & 31);
           nacc_out += acc ? 1 : 0;
@@ -424,7 +423,7 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, f
           if (has) {
             bool acc;
             double chi2;
-            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, A.chi2_max_d, gate_hi, gate_lo, true, acc, chi2);
+            const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate, true, acc, chi2);
             if (ust != ST_OK) { st = ust; break; }
             chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
             nacc += acc ? 1 : 0;

@@ -97,8 +97,7 @@ __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
   T.c[9] = A.seed_cov[3];
   T.c[14] = A.seed_cov[4];
   T.clear_comp();
-  uint32_t gate_hi, gate_lo;
-  split64(A.chi2_max_d, gate_hi, gate_lo);
+  const Gate gate = make_gate(A.chi2_max, A.chi2_max_d);
   const int r0 = A.seed_row[s], sec = A.seed_sector[s];
   int status = FL_END, misses = 0, n = 0;
   int32_t *att = A.att + s * A.n_rows;
@@ -168,7 +167,7 @@ __global__ void __launch_bounds__(256) k_follow(FollowArgs A) {
     bool acc = false;
     if (best >= 0) {
       double chi2;
-      const int ust = update(T, bc.x, bc.y, bc.z, bc.w, A.chi2_max_d, gate_hi, gate_lo, false, acc, chi2);
+      const int ust = update(T, bc.x, bc.y, bc.z, bc.w, gate, false, acc, chi2);
       if (ust != ST_OK) { status = ust; break; }
     }
     if (acc) {
