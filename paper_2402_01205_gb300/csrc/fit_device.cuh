@@ -85,6 +85,21 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
   s = vadd(a, b);
   e = vsub(b, vsub(s, a));
 }
+// Two Fast2Sums at once, (a0 + b0, a1 + b1) = (s0 + e0, s1 + e1), with the
+// paired binary32 instructions of sm_100 and later (each half rounds as the
+// scalar instruction does; s - a and b - z as fused multiply-adds by -1,
+// which round the difference once).
+__device__ __forceinline__ void fast_two_sum_x2(float a0, float a1, float b0, float b1, float &s0, float &s1,
+                                                float &e0, float &e1) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 a = make_float2(a0, a1), b = make_float2(b0, b1);
+  const float2 s = __fadd2_rn(a, b);
+  const float2 e = __ffma2_rn(__ffma2_rn(a, m1, s), m1, b);  // b - (s - a)
+  s0 = s.x;
+  s1 = s.y;
+  e0 = e.x;
+  e1 = e.y;
+}
 // Error-free product of two binary32 numbers: a * b = p + e exactly.
 __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
   p = vmul(a, b);
@@ -97,7 +112,7 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
 // Track state in FP32 with extended precision where the Kalman recursion
 // accumulates many small increments onto a large value:
 //  - y, z:       offsets (dy, dz) from the last cluster's coordinates (ya, za)
-//  - sinphi:     compensated sum sp + spl (TwoSum on every increment)
+//  - sinphi:     compensated sum sp + spl
 //  - tanlambda:  anchor tl0 + offset dtl;  q/pT: anchor w0 + offset dw
 //  - variances of tanlambda and q/pT: compensated sums c[9] + c9l, c[14] + c14l
 //    (transport leaves them unchanged; after a restart they shrink by orders of
@@ -108,6 +123,12 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
 //    alone (every other step in FP64) moves the fitted covariance of a track
 //    that was lost and found again in the outward pass by up to 1.2e-4 of
 //    its diagonal; with them compensated, by less than 2e-5.
+// Each compensated sum adds (increment + low part) to the high part with
+// Fast2Sum, which is exact when the high part is the larger; where an
+// increment exceeds it (a covariance or sinphi passing through zero) that
+// step's error is at most half a binary32 ulp of the increment, i.e. the
+// step is as accurate as an uncompensated binary32 sum of small values.
+// The sums are done in pairs with the paired binary32 instructions.
 struct Trk {
   float dy, dz, sp, spl, tl0, dtl, w0, dw;
   float ya, za;
@@ -158,12 +179,6 @@ __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_m
   const float sT = vmul(L, g);                         // signed transverse arc length
   T.dy = vfma(dx, Tn, T.dy);
   T.dz = vfma(tl, sT, T.dz);
-  {  // sinphi += C dx, compensated
-    float hi, e;
-    two_sum(T.sp, vmul(C, dx), hi, e);
-    T.sp = hi;
-    T.spl = vadd(T.spl, e);
-  }
   // Jacobian
   const float Q = vmul(vmul(vfma(c1, c2, vfma(s1, s2, 1.0f)), iB), iB);
   const float dTds = vmul(Q, vadd(ic1, ic2));
@@ -202,15 +217,16 @@ __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_m
   c[0] = vfma(Jys, FC02, vfma(Jyw, FC04, FC00));
   c[1] = vfma(Jys, FC12, vfma(Jyw, FC14, FC10));
   c[2] = vfma(Jzs, FC12, vfma(Jzt, FC13, vfma(Jzw, FC14, FC11)));
-  two_sum(c[3], vfma(Jys, FC22, vfma(Jyw, FC24, vfma(Jsw, c[10], T.c3l))), c[3], T.c3l);
   c[4] = vfma(Jzs, FC22, vfma(Jzt, FC23, vfma(Jzw, FC24, FC21)));
-  fast_two_sum(c[5], vadd(dss, T.c5l), c[5], T.c5l);  // a variance plus a smaller change
+  // compensated sums, two at a time: (C_ys, C_ss) and (sinphi, C_sw)
+  fast_two_sum_x2(c[3], c[5], vfma(Jys, FC22, vfma(Jyw, FC24, vfma(Jsw, c[10], T.c3l))), vadd(dss, T.c5l), c[3],
+                  c[5], T.c3l, T.c5l);
+  fast_two_sum_x2(T.sp, c[12], vfma(C, dx, T.spl), vadd(dsw, T.c12l), T.sp, c[12], T.spl, T.c12l);
   c[6] = n30;
   c[7] = FC13;
   c[8] = n32;
   c[10] = FC04;
   c[11] = FC14;
-  two_sum(c[12], vadd(dsw, T.c12l), c[12], T.c12l);
   // c[9], c[13], c[14] unchanged
   return true;
 }
@@ -227,8 +243,8 @@ __device__ __forceinline__ void ms_noise(Trk &T, float xx0, float mass2) {
   const float lg = vfma(0.038f, __logf(vmul(eps, ib2)), 1.0f);
   const float th2 = vmul(vmul(vmul(vmul(vmul(0.0136f * 0.0136f, pinv2), ib2), eps), lg), lg);
   fast_two_sum(T.c[5], vfma(th2, vmul(cs2, tt), T.c5l), T.c[5], T.c5l);
-  fast_two_sum(T.c[9], vfma(th2, vmul(tt, tt), T.c9l), T.c[9], T.c9l);
-  fast_two_sum(T.c[14], vfma(th2, vmul(vmul(vmul(w, w), t), t), T.c14l), T.c[14], T.c14l);
+  fast_two_sum_x2(T.c[9], T.c[14], vfma(th2, vmul(tt, tt), T.c9l), vfma(th2, vmul(vmul(vmul(w, w), t), t), T.c14l),
+                  T.c[9], T.c[14], T.c9l, T.c14l);
   T.c[13] = vfma(th2, vmul(vmul(tt, w), t), T.c[13]);
 }
 
@@ -410,7 +426,6 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
     // new position offsets relative to this cluster (the new anchor)
     T.dy = vfma(vsub(K0[0], 1.0f), r0, vmul(K1[0], r1));
     T.dz = vfma(K0[1], r0, vmul(vsub(K1[1], 1.0f), r1));
-    two_sum(T.sp, vfma(K0[2], r0, vfma(K1[2], r1, T.spl)), T.sp, T.spl);
     T.dtl = vfma(K0[3], r0, vfma(K1[3], r1, T.dtl));
     T.dw = vfma(K0[4], r0, vfma(K1[4], r1, T.dw));
     // C -= K (H C).  For the measured columns (j = y, z) this equals K V
@@ -430,10 +445,11 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
     }
     fast_two_sum(c[5], vsub(T.c5l, vfma(K0[2], h0[2], vmul(K1[2], h1[2]))), c[5], T.c5l);
     c[8] = vfma(-K0[3], h0[2], vfma(-K1[3], h1[2], c[8]));
-    fast_two_sum(c[9], vsub(T.c9l, vfma(K0[3], h0[3], vmul(K1[3], h1[3]))), c[9], T.c9l);
-    two_sum(c[12], vsub(T.c12l, vfma(K0[4], h0[2], vmul(K1[4], h1[2]))), c[12], T.c12l);
+    fast_two_sum_x2(T.sp, c[12], vfma(K0[2], r0, vfma(K1[2], r1, T.spl)),
+                    vsub(T.c12l, vfma(K0[4], h0[2], vmul(K1[4], h1[2]))), T.sp, c[12], T.spl, T.c12l);
     c[13] = vfma(-K0[4], h0[3], vfma(-K1[4], h1[3], c[13]));
-    fast_two_sum(c[14], vsub(T.c14l, vfma(K0[4], h0[4], vmul(K1[4], h1[4]))), c[14], T.c14l);
+    fast_two_sum_x2(c[9], c[14], vsub(T.c9l, vfma(K0[3], h0[3], vmul(K1[3], h1[3]))),
+                    vsub(T.c14l, vfma(K0[4], h0[4], vmul(K1[4], h1[4]))), c[9], c[14], T.c9l, T.c14l);
   } else {  // a rejected cluster still becomes the anchor: offsets to the predicted position
     T.dy = -r0;
     T.dz = -r1;
