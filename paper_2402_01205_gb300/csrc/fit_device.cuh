@@ -158,7 +158,8 @@ __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_m
   if (fabsf(s1) >= snp_max || fabsf(s2) >= snp_max) return false;
   const float q1 = vfma(-s1, s1, 1.0f), q2 = vfma(-s2, s2, 1.0f);
   const float ic1 = rsqrtf(q1), ic2 = rsqrtf(q2);
-  const float c1 = vmul(q1, ic1), c2 = vmul(q2, ic2);  // cos phi at both planes
+  const float2 cc = __fmul2_rn(make_float2(q1, q2), make_float2(ic1, ic2));
+  const float c1 = cc.x, c2 = cc.y;  // cos phi at both planes
   const float iB = __fdividef(1.0f, vadd(c1, c2));
   const float Tn = vmul(vadd(s1, s2), iB);             // tangent of the chord direction
   const float kk2 = vfma(Tn, Tn, 1.0f);
@@ -177,8 +178,11 @@ __device__ __forceinline__ bool propagate(Trk &T, float dx, float b, float snp_m
     h = (rsqrtf(1.0f - u2) - g) / (2.0f * u2);
   }
   const float sT = vmul(L, g);                         // signed transverse arc length
-  T.dy = vfma(dx, Tn, T.dy);
-  T.dz = vfma(tl, sT, T.dz);
+  {
+    const float2 d = __ffma2_rn(make_float2(dx, tl), make_float2(Tn, sT), make_float2(T.dy, T.dz));
+    T.dy = d.x;
+    T.dz = d.y;
+  }
   // Jacobian
   const float Q = vmul(vmul(vfma(c1, c2, vfma(s1, s2, 1.0f)), iB), iB);
   const float dTds = vmul(Q, vadd(ic1, ic2));
@@ -365,8 +369,11 @@ __device__ __forceinline__ Gate make_gate(float chi2_max, double chi2_max_d) {
 __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, float vz, const Gate &G, bool want_chi2,
                                       bool &acc, double &chi2) {
   float *c = T.c;
-  const float r0 = vsub(vsub(yc, T.ya), T.dy);
-  const float r1 = vsub(vsub(zc, T.za), T.dz);
+  // residual (yc - ya) - dy, (zc - za) - dz as a pair (a fused multiply-add by -1 rounds a difference once)
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 rr =
+      __ffma2_rn(make_float2(T.dy, T.dz), m1, __ffma2_rn(make_float2(T.ya, T.za), m1, make_float2(yc, zc)));
+  const float r0 = rr.x, r1 = rr.y;
   const float S00 = vadd(c[0], vy), S10 = c[1], S11 = vadd(c[2], vz);
   float qh, ql;
   quad_form2(S00, S10, S11, r0, r1, qh, ql);
@@ -440,8 +447,14 @@ __device__ __forceinline__ int update(Trk &T, float yc, float zc, float vy, floa
     T.c3l = 0.f;  // C'(2,0) below is a fresh product
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-      c[col0[i]] = vmul(K0[i], vy);  // C'(i,0)
-      if (i >= 1) c[col1[i]] = vmul(K1[i], vz);  // C'(i,1)
+      if (i == 1 || i >= 3) {  // C'(i,0), C'(i,1) as a pair
+        const float2 v = __fmul2_rn(make_float2(K0[i], K1[i]), make_float2(vy, vz));
+        c[col0[i]] = v.x;
+        c[col1[i]] = v.y;
+      } else {
+        c[col0[i]] = vmul(K0[i], vy);              // C'(i,0)
+        if (i >= 1) c[col1[i]] = vmul(K1[i], vz);  // C'(i,1)
+      }
     }
     fast_two_sum(c[5], vsub(T.c5l, vfma(K0[2], h0[2], vmul(K1[2], h1[2]))), c[5], T.c5l);
     c[8] = vfma(-K0[3], h0[2], vfma(-K1[3], h1[2], c[8]));
