@@ -6,10 +6,13 @@ not its results (every choice is bit-identical; the GPU tests check it):
 * ``block_threads``  threads per block, 128 or 256 (tracks per warp are fixed
   at 32, one track per lane: each warp-wide FP64 instruction of the
   innovation inverse and chi2 costs the FP64 pipe the same with 1 or 32
-  lanes active, so k lanes per track would multiply its time per cluster by
-  k; two tracks per lane, advanced with paired FP32 instructions, was built
-  and measured 1.8 times slower on the Pb-Pb frame: half the resident warps,
-  and packing the pairs cost more issue slots than the pairing saved);
+  lanes active, and about three quarters of a step (propagation scalars,
+  residual, S, the FP64 island, the gain) cannot be split between lanes, so
+  k lanes per track would raise both the FP64 pipe time and the issue slots
+  per cluster about k-fold; two tracks per lane, advanced with paired FP32
+  instructions, was built and measured 1.8 times slower on the Pb-Pb frame:
+  half the resident warps, and packing the pairs cost more issue slots than
+  the pairing saved);
 * ``blocks_per_sm``  resident blocks per SM (grid = SMs x blocks_per_sm);
 * ``sort_tracks``    longest-first order of tracks, or frame order.
 
@@ -27,9 +30,9 @@ import os
 import statistics
 from typing import Callable, Iterable, Optional
 
-# occupancy ceilings of the two plain instantiations (105 registers per thread:
-# 4 blocks of 128 or 2 of 256 threads per SM)
-MAX_BLOCKS_PER_SM = {128: 4, 256: 2}
+# occupancy ceilings of the plain fit: blocks of 128 up to 5 per SM (an
+# instantiation for at most 102 registers per thread), of 256 up to 2
+MAX_BLOCKS_PER_SM = {128: 5, 256: 2}
 TUNABLE = ("block_threads", "blocks_per_sm", "sort_tracks")
 
 

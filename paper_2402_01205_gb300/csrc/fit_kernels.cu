@@ -562,28 +562,50 @@ static bool same_16b_phase(const FitArgs &a) {
 
 static bool fit_variant(const FitArgs &a) { return a.xrho > 0.0f || a.n_iter > 0; }
 
+// SMs of the current device.
+static int current_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms;
+}
+
+// The plain fit in blocks of 128 has two instantiations: for 4 resident
+// blocks per SM (up to 128 registers per thread) and for 5 (up to 102): a
+// grid of more than 4 blocks per SM runs the second, whose 640 tracks per SM
+// fit the Pb-Pb frame 2 % faster although more of their clusters leave L2
+// between the two passes (76 against 61 B of DRAM traffic per cluster).  The
+// variant and the serving engine keep 4 blocks of 128 per SM (a larger grid is
+// cut to that: the warps claim their work, so the results do not change).
+constexpr int kMaxBlocks128 = 5;
+
 cudaError_t fit_set_attributes(const FitArgs &a, int block) {
   if (fit_variant(a)) return block == 128 ? set_fit_smem<128, 4, true>() : set_fit_smem<256, 2, true>();
-  return block == 128 ? set_fit_smem<128, 4, false>() : set_fit_smem<256, 2, false>();
+  if (block != 128) return set_fit_smem<256, 2, false>();
+  const cudaError_t e = set_fit_smem<128, 4, false>();
+  return e != cudaSuccess ? e : set_fit_smem<128, kMaxBlocks128, false>();
 }
 
 cudaError_t launch_fit(const FitArgs &a_in, int grid, int block, cudaStream_t stream) {
   if (a_in.n_tracks <= 0) return cudaSuccess;
   FitArgs a = a_in;
   a.stage_vec = same_16b_phase(a) ? 1 : 0;
-  if (fit_variant(a))
-    return block == 128 ? launch_fit_as<128, 4, true>(a, grid, stream) : launch_fit_as<256, 2, true>(a, grid, stream);
-  return block == 128 ? launch_fit_as<128, 4, false>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
+  if (block != 128)
+    return fit_variant(a) ? launch_fit_as<256, 2, true>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
+  const int sms = current_sms();
+  const bool over4 = sms > 0 && grid > 4 * sms;
+  if (fit_variant(a)) return launch_fit_as<128, 4, true>(a, over4 ? 4 * sms : grid, stream);
+  return over4 ? launch_fit_as<128, kMaxBlocks128, false>(a, grid, stream) : launch_fit_as<128, 4, false>(a, grid, stream);
 }
 
-// Occupancy of the fit without energy loss (the variant is compiled under the
-// same launch bounds, so it reaches at least 512 threads per SM as well).
+// Occupancy of the plain fit (the variant, compiled for 4 blocks of 128 or 2
+// of 256, reaches 512 threads per SM).
 int fit_blocks_per_sm(int block) {
   int n = 0;
   cudaError_t e;
   if (block == 128) {
-    set_fit_smem<128, 4, false>();
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<128, 4, false>, 128, fit_smem<128>());
+    set_fit_smem<128, kMaxBlocks128, false>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<128, kMaxBlocks128, false>, 128, fit_smem<128>());
   } else {
     set_fit_smem<256, 2, false>();
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit<256, 2, false>, 256, fit_smem<256>());
@@ -593,13 +615,13 @@ int fit_blocks_per_sm(int block) {
 }
 
 // Resident blocks per SM when the caller leaves the choice to the library:
-// 512 tracks per SM.  With 768 tracks per SM in flight their clusters do not
-// stay in L2 between the outward and the inward pass (DRAM reads of 170 B per
-// cluster against 60 B with 512, measured on GB300), so the instantiations are
-// compiled for 512 threads per SM (up to 128 registers per thread).
-int fit_default_blocks_per_sm(int block) {
+// 640 tracks per SM for the plain fit in blocks of 128, else 512.  With 768
+// tracks per SM in flight their clusters do not stay in L2 between the
+// outward and the inward pass (DRAM reads of 170 B per cluster against 60 B
+// with 512 and 72 B with 640, measured on GB300).
+int fit_default_blocks_per_sm(int block, bool variant) {
   const int occ = fit_blocks_per_sm(block);
-  const int want = 512 / (block == 128 ? 128 : 256);
+  const int want = block == 128 ? (variant ? 4 : kMaxBlocks128) : 2;
   return occ < want ? occ : want;
 }
 
@@ -622,6 +644,10 @@ template <int BLOCK, int MINB, bool VAR> static cudaError_t launch_parts_as(cons
 
 cudaError_t launch_fit_parts(const PartsArgs &p, bool variant, int grid, int block, cudaStream_t stream) {
   if (p.n_parts <= 0) return cudaSuccess;
+  if (block == 128) {  // compiled for 4 resident blocks of 128
+    const int sms = current_sms();
+    if (sms > 0 && grid > 4 * sms) grid = 4 * sms;
+  }
   if (variant)
     return block == 128 ? launch_parts_as<128, 4, true>(p, grid, stream) : launch_parts_as<256, 2, true>(p, grid, stream);
   return block == 128 ? launch_parts_as<128, 4, false>(p, grid, stream) : launch_parts_as<256, 2, false>(p, grid, stream);
@@ -633,10 +659,12 @@ FitArgs fit_args_for_launch(const FitArgs &a) {
   return b;
 }
 
-int fit_regs_per_thread(int block, bool variant) {
+int fit_regs_per_thread(int block, bool variant, int blocks_per_sm) {
   cudaFuncAttributes at;
   cudaError_t e;
-  if (block == 128)
+  if (block == 128 && !variant && blocks_per_sm > 4)
+    e = cudaFuncGetAttributes(&at, k_fit<128, kMaxBlocks128, false>);
+  else if (block == 128)
     e = variant ? cudaFuncGetAttributes(&at, k_fit<128, 4, true>) : cudaFuncGetAttributes(&at, k_fit<128, 4, false>);
   else
     e = variant ? cudaFuncGetAttributes(&at, k_fit<256, 2, true>) : cudaFuncGetAttributes(&at, k_fit<256, 2, false>);

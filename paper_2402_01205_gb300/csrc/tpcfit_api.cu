@@ -350,12 +350,14 @@ extern "C" int tpcfit_create(const tpcfit_config *cfg_in, tpcfit_handle **out) {
   if (cudaMalloc(&h->d_rowx, sizeof(rowx)) != cudaSuccess ||
       cudaMemcpy(h->d_rowx, rowx, sizeof(rowx), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(fail(TPCFIT_E_NOMEM, "row table allocation failed"));
-  // default shape: 128 threads x 4 blocks per SM (512 tracks per SM; 0.8 % faster
-  // than 256 x 2 on the Pb-Pb frame, 9.76 against 9.83 ms per launch sequence)
+  // default shape: 128 threads x 5 blocks per SM for the plain fit (640 tracks
+  // per SM; 2 % faster than 4 blocks on the Pb-Pb frame, 6.70 against 6.84 ms),
+  // 4 for the variant; 128 x 4 was 0.8 % faster than 256 x 2
   h->fit_block = cfg.block_threads ? cfg.block_threads : 128;
-  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(h->fit_block);
+  const bool variant = cfg.xrho_per_row > 0.0f || cfg.fit_iterations > 0;
+  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(h->fit_block, variant);
   h->fit_grid = h->sms * bps;
-  h->fit_regs = fit_regs_per_thread(h->fit_block, cfg.xrho_per_row > 0.0f || cfg.fit_iterations > 0);
+  h->fit_regs = fit_regs_per_thread(h->fit_block, variant, bps);
   h->chunk_clusters = cfg.host_chunk_clusters > 0 ? cfg.host_chunk_clusters : (int64_t)16 << 20;
   *out = h;
   return TPCFIT_OK;

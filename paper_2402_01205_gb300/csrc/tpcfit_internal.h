@@ -247,7 +247,7 @@ cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream);
 // Occupancy-derived resident blocks per SM for the fit kernel at `block` threads.
 int fit_blocks_per_sm(int block);
 // tuned default residency (blocks per SM) for a block size
-int fit_default_blocks_per_sm(int block);
-int fit_regs_per_thread(int block, bool variant);  // of the instantiation a handle launches
+int fit_default_blocks_per_sm(int block, bool variant);
+int fit_regs_per_thread(int block, bool variant, int blocks_per_sm);  // of the instantiation a handle launches
 
 }  // namespace tpcfit

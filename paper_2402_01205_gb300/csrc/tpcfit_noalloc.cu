@@ -170,7 +170,8 @@ extern "C" int tpcfit_fit_noalloc(const tpcfit_config *cfg_in, const tpcfit_fram
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device);
   const int block = cfg.block_threads ? cfg.block_threads : 128;  // the handle path's default shape
-  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : fit_default_blocks_per_sm(block);
+  const int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm
+                                        : fit_default_blocks_per_sm(block, cfg.xrho_per_row > 0.0f || cfg.fit_iterations > 0);
   cudaError_t e;
   if ((e = cudaMemsetAsync(sc, 0, kZeroBytes, st)) != cudaSuccess) goto cuda_fail;
   k_noalloc_rowx<<<1, kMaxRows, 0, st>>>(reinterpret_cast<float *>(sc + kRowxOff), (double)cfg.row_x0_cm, pitch);

@@ -9,7 +9,7 @@ from paper_2402_01205_gb300 import autotune as A
 def test_candidates_cover_every_shape_once():
     c = A.candidates()
     keys = {tuple(sorted(d.items())) for d in c}
-    assert len(keys) == len(c) == 2 * (4 + 2)
+    assert len(keys) == len(c) == 2 * (A.MAX_BLOCKS_PER_SM[128] + A.MAX_BLOCKS_PER_SM[256])
     assert all(1 <= d["blocks_per_sm"] <= A.MAX_BLOCKS_PER_SM[d["block_threads"]] for d in c)
 
 

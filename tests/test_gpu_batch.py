@@ -115,7 +115,7 @@ def test_batch_on_caller_stream_and_block_shapes(T, events):
     with T.Fitter() as fx:
         ref = host(fx.fit(g))
     s = torch.cuda.Stream()
-    for bt, bps in ((128, 0), (128, 3), (256, 1), (256, 0)):
+    for bt, bps in ((128, 0), (128, 4), (128, 3), (256, 1), (256, 0)):
         with T.Fitter(block_threads=bt, blocks_per_sm=bps) as fx, T.Batch(fx, g) as b:
             b.launch(stream=s)
             b.sync(timeout_s=60)
@@ -141,5 +141,7 @@ def test_batch_graph_of_the_fit_variant_equals_its_plain_fit(T, events):
             b.launch()
             b.sync(timeout_s=60)
             same(plain, host(b.res))
+    with T.Fitter(xrho_per_row=0.01, fit_iterations=1, blocks_per_sm=5) as fx:  # the variant's grid is cut to 4
+        same(plain, host(fx.fit(g)))
     with T.Fitter() as fx:
         assert not np.array_equal(host(fx.fit(g))["state"], plain["state"])
