@@ -159,7 +159,8 @@ __device__ __forceinline__ bool state_finite(const Trk &T) {
 }
 
 // Fit of track t by one lane: outward pass, restart, inward pass (and, in the
-// variant, energy loss and seed iterations).  NCOL = threads of the block: the
+// variant, energy loss, seed iterations and the per-cluster diagnostics:
+// chi2 of every update and the inward restart state).  NCOL = threads of the block: the
 // lane's staging and accept-bit columns are strided by it.
 template <int NCOL, bool VAR>
 __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const float *s_rowx, float *f4,
@@ -211,6 +212,9 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       // passes: one outward + inward pair, or (the variant) 1 + n_iter of them
       for (int it = 0;; ++it) {
         int nacc_out = 0;
+        // outward accept bits of the current 32-cluster word, written to the
+        // track's shared-memory words when complete and after the pass
+        uint32_t ow = 0u, obit = 1u;
         // candidate: the next cluster to use, read from the track's staged chunks.
         // The chunks sit in a ring of kStageBufs buffers; copies are issued and
         // waited for at warp-uniform steps, every kChunk rows of a pass (the
@@ -246,13 +250,18 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             bool acc;
             double chi2;
             const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate,
-                                   A.chi2_out_c != nullptr, acc, chi2);
+                                   VAR && A.chi2_out_c != nullptr, acc, chi2);
             if (ust != ST_OK) { st = ust; break; }
-            if (acc) bits[NCOL * (kc >> 5)] |= 1u << (kc & 31);
-            if (A.chi2_out_c) A.chi2_out_c[a + kc] = chi2;
+            if (acc) ow |= obit;
+            if (VAR && A.chi2_out_c) A.chi2_out_c[a + kc] = chi2;
             ++out_done;
             nacc_out += acc ? 1 : 0;
             rprev = cand.r;
+            obit = __funnelshift_l(obit, obit, 1);  // rotate: the bit of cluster kc + 1 in its word
+            if (obit == 1u) {                      // clusters kc - 31 .. kc complete a word
+              bits[NCOL * (kc >> 5)] = ow;
+              ow = 0u;
+            }
             if (++kc < n) {
               const int p = kc + lead;
               if ((p & 3) == 0) {  // entering chunk p/4 (arrived)
@@ -271,6 +280,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           }
           if (kc == n) break;
         }
+        if (kc & 31) bits[NCOL * (kc >> 5)] = ow;  // the last, partial word
         // ---------------- restart ----------------
         if (st == ST_OK) {
           // cand holds the outermost cluster n-1
@@ -314,7 +324,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
             T.c[14] = d4;
           }
           T.clear_comp();
-          if (A.restart_state) {
+          if (VAR && A.restart_state) {
             float *rs = A.restart_state + 5 * t;
             rs[0] = T.ya + T.dy;
             rs[1] = T.za + T.dz;
@@ -324,6 +334,7 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
           }
           // ---------------- inward pass: rows row[n-1] .. row[0] ----------------
           kc = n - 1;
+          uint32_t iw = bits[NCOL * (kc >> 5)] << (31 - (kc & 31));  // the outward bit of cluster kc in bit 31
           // the ring holds the last kStageBufs chunks (the outward pass reached
           // the last one, so all of them have arrived); the last is current
           int lowest = nch > kStageBufs ? nch - kStageBufs : 0;  // inward: the lowest chunk issued
@@ -350,13 +361,16 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
               const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate, true, acc,
                                      chi2);
               if (ust != ST_OK) { st = ust; break; }
-              if (A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;
+              if (VAR && A.chi2_in_c) A.chi2_in_c[a + kc] = chi2;
               chi2sum += __longlong_as_double(acc ? __double_as_longlong(chi2) : 0ll);
               nacc += acc ? 1 : 0;
-              const uint32_t ob = (bits[NCOL * (kc >> 5)] >> (kc & 31)) & 1u;
-              acc_t[kc] = (uint8_t)(ob | (acc ? 2u : 0u));
+              acc_t[kc] = (uint8_t)((iw >> 31) | (acc ? 2u : 0u));
               ++done;
               if (--kc >= 0) {
+                if ((kc & 31) == 31)
+                  iw = bits[NCOL * (kc >> 5)];
+                else
+                  iw <<= 1;
                 const int p = kc + lead;
                 if ((p & 3) == 3) {  // entering chunk p/4 from above (arrived)
                   cbuf = cbuf == 0 ? kStageBufs - 1 : cbuf - 1;
@@ -401,9 +415,9 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
       const int lk = (int)(k - a);
       A.accept[k] = (lk < kMaxRows) ? (uint8_t)((bits[NCOL * (lk >> 5)] >> (lk & 31)) & 1u) : (uint8_t)0;
     }
-    if (A.chi2_in_c)
+    if (VAR && A.chi2_in_c)
       for (int64_t k = a; k < e - done; ++k) A.chi2_in_c[k] = __longlong_as_double(0x7ff8000000000000ll);
-    if (A.chi2_out_c)
+    if (VAR && A.chi2_out_c)
       for (int64_t k = a + out_done; k < e; ++k) A.chi2_out_c[k] = __longlong_as_double(0x7ff8000000000000ll);
   }
   A.x_ref[t] = xref;
@@ -422,9 +436,9 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
   A.status[t] = st;
 }
 
-// VAR: the variant -- energy loss and seed iteration, each checked at run
-// time (a separate instantiation, so that the plain fit keeps its own
-// register allocation and schedule).
+// VAR: the variant -- energy loss, seed iteration and the diagnostic
+// outputs, each checked at run time (a separate instantiation, so that the
+// plain fit keeps its own register allocation and schedule).
 template <int BLOCK, int MINB, bool VAR>
 __global__ void __launch_bounds__(BLOCK, MINB) k_fit(FitArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -560,7 +574,10 @@ static bool same_16b_phase(const FitArgs &a) {
          (reinterpret_cast<uintptr_t>(a.sy2) & 15u) == p && (reinterpret_cast<uintptr_t>(a.sz2) & 15u) == p;
 }
 
-static bool fit_variant(const FitArgs &a) { return a.xrho > 0.0f || a.n_iter > 0; }
+// The variant instantiation: energy loss, seed iteration or diagnostic outputs.
+static bool fit_variant(const FitArgs &a) {
+  return a.xrho > 0.0f || a.n_iter > 0 || a.chi2_out_c || a.chi2_in_c || a.restart_state;
+}
 
 // SMs of the current device.
 static int current_sms() {
