@@ -232,15 +232,21 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
         uint32_t rows_cur = staged_rows<NCOL>(wrow, 0, rsh);
         Clu cand = read_staged<NCOL>(f4, lead, 0, rows_cur);
         int rprev = -1;
-        st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
         // ---------------- outward pass: rows row[0] .. row[n-1] ----------------
-        for (int r = cand.r, step = 0; st == ST_OK; ++r, ++step) {
+        for (int r = cand.r, step = 0;; ++r, ++step) {
           if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
             cp_async_wait_all();
             if (staged < nch && staged <= ((kc + lead) >> 2) + 2) {  // the buffer of chunk staged-3 is consumed
               stage_chunk<NCOL>(A, a, e, lead, rsh, staged, staged % kStageBufs, f4, wrow);
               ++staged;
             }
+          }
+          {  // the next cluster is validated when the pass reaches it, before any
+             // propagation towards it (checked at every row until it is used: the
+             // values were read at the end of the previous step, so the test does
+             // not wait for them)
+            const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
+            if (vs != ST_OK) { st = vs; break; }
           }
           const bool has = (cand.r == r);
           const float xt = has ? cand.x : s_rowx[r];
@@ -269,8 +275,6 @@ __device__ void fit_track(const FitArgs &A, int64_t t, uint32_t *bits, const flo
                 rows_cur = staged_rows<NCOL>(wrow, cbuf, rsh);
               }
               cand = read_staged<NCOL>(f4, p & 3, cbuf, rows_cur);
-              const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
-              if (vs != ST_OK) { st = vs; break; }
             }
           }
           if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);

@@ -324,14 +324,18 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, f
       Clu cand = read_staged<kSmoothBlock>(f4, lead, 0, rows_cur);
       int nacc_out = 0, rprev = -1;
       const int r0 = cand.r;  // predictions are kept by row step r - r0
-      st = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
-      for (int r = cand.r, step = 0; st == ST_OK; ++r, ++step) {
+      uint32_t ow = 0u, obit = 1u;  // forward accept bits of the current 32-cluster word
+      for (int r = cand.r, step = 0;; ++r, ++step) {
         if (step > 0 && (step & (kChunk - 1)) == 0) {  // staging step (warp-uniform)
           cp_async_wait_all();
           if (staged < nch && staged <= ((kc + lead) >> 2) + 2) {  // the buffer of chunk staged-3 is consumed
             stage_chunk<kSmoothBlock>(A, a, e, lead, rsh, staged, staged % kStageBufs, f4, wrow);
             ++staged;
           }
+        }
+        {  // the next cluster, validated as in the fit before any propagation towards it
+          const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
+          if (vs != ST_OK) { st = vs; break; }
         }
         const bool has = (cand.r == r);
         const float xt = has ? cand.x : s_rowx[r];
@@ -349,10 +353,15 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, f
           double chi2;
           const int ust = update(T, cand.y, cand.z, cand.vy, cand.vz, gate, false, acc, chi2);
           if (ust != ST_OK) { st = ust; break; }
-          if (acc) bits[(kc >> 5) * kSmoothBlock] |= 1u << (kc & 31);
+          if (acc) ow |= obit;
           nacc_out += acc ? 1 : 0;
           ++fw_done;
           rprev = cand.r;
+          obit = __funnelshift_l(obit, obit, 1);  // rotate: the bit of cluster kc + 1 in its word
+          if (obit == 1u) {                      // clusters kc - 31 .. kc complete a word
+            bits[(kc >> 5) * kSmoothBlock] = ow;
+            ow = 0u;
+          }
           if (++kc < n) {
             const int p = kc + lead;
             if ((p & 3) == 0) {  // entering chunk p/4 (arrived)
@@ -360,13 +369,12 @@ __device__ void smooth_track(const FitArgs &A, int64_t t, const float *s_rowx, f
               rows_cur = staged_rows<kSmoothBlock>(wrow, cbuf, rsh);
             }
             cand = read_staged<kSmoothBlock>(f4, p & 3, cbuf, rows_cur);
-            const int vs = check_cluster(cand.r, rprev, A.n_rows, cand.x, cand.y, cand.z, cand.vy, cand.vz);
-            if (vs != ST_OK) { st = vs; break; }
           }
         }
         if (A.xx0 > 0.f) ms_noise(T, A.xx0, A.mass2);
         if (kc == n) break;
       }
+      if (kc & 31) bits[(kc >> 5) * kSmoothBlock] = ow;  // the last, partial word
       if (st == ST_OK) {
         // ---------------- restart, as the fit's inward pass ----------------
         // cand holds the outermost cluster n-1
