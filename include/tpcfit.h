@@ -90,7 +90,9 @@ typedef struct tpcfit_config {
   int32_t max_slots;      /* serving: frames resident at once (8) */
   int32_t device;         /* CUDA device ordinal (0) */
   int32_t block_threads;  /* fit kernel block size: 128 or 256 (0 = 128) */
-  int32_t blocks_per_sm;  /* fit kernel resident blocks per SM; 0 = tuned default (512 threads per SM) */
+  int32_t blocks_per_sm;  /* fit kernel resident blocks per SM; 0 = tuned default (640 threads per SM for the
+                             plain fit in blocks of 128, else 512; the variant and the serving engine run
+                             at most 4 blocks of 128 per SM) */
   int32_t sort_tracks;    /* 1: fit tracks longest-first (default); 0: in frame order */
   float res_step_y_cm;    /* residual code step in y (0.01 cm), see tpcfit_result.res_y */
   float res_step_z_cm;    /* residual code step in z (0.01 cm) */

@@ -546,7 +546,7 @@ int smooth_grid() {
     cudaGetLastError();
     return 0;
   }
-  const int per_sm = occ < 4 ? (occ > 0 ? occ : 1) : 4;  // up to 512 tracks per SM, as the fit
+  const int per_sm = occ < 4 ? (occ > 0 ? occ : 1) : 4;  // up to 512 tracks per SM (its prediction scratch grows with the grid)
   return sms * per_sm;
 }
 
