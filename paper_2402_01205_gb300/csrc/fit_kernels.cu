@@ -595,7 +595,9 @@ static int current_sms() {
 // blocks per SM (up to 128 registers per thread) and for 5 (up to 102): a
 // grid of more than 4 blocks per SM runs the second, whose 640 tracks per SM
 // fit the Pb-Pb frame 2 % faster although more of their clusters leave L2
-// between the two passes (76 against 61 B of DRAM traffic per cluster).  The
+// between the two passes (76 against 61 B of DRAM traffic per cluster).  A
+// frame with no more tracks than 4 blocks per SM hold gains nothing from the
+// fifth block and runs the first (its tracks' steps are shorter).  The
 // variant and the serving engine keep 4 blocks of 128 per SM (a larger grid is
 // cut to that: the warps claim their work, so the results do not change).
 constexpr int kMaxBlocks128 = 5;
@@ -615,7 +617,9 @@ cudaError_t launch_fit(const FitArgs &a_in, int grid, int block, cudaStream_t st
     return fit_variant(a) ? launch_fit_as<256, 2, true>(a, grid, stream) : launch_fit_as<256, 2, false>(a, grid, stream);
   const int sms = current_sms();
   const bool over4 = sms > 0 && grid > 4 * sms;
-  if (fit_variant(a)) return launch_fit_as<128, 4, true>(a, over4 ? 4 * sms : grid, stream);
+  if (fit_variant(a) || (over4 && a.n_tracks <= (int64_t)4 * sms * 128))
+    return fit_variant(a) ? launch_fit_as<128, 4, true>(a, over4 ? 4 * sms : grid, stream)
+                          : launch_fit_as<128, 4, false>(a, 4 * sms, stream);
   return over4 ? launch_fit_as<128, kMaxBlocks128, false>(a, grid, stream) : launch_fit_as<128, 4, false>(a, grid, stream);
 }
 
