@@ -21,6 +21,7 @@ no data exchange), max time over ranks, weak scaling.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -29,6 +30,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from contextlib import contextmanager
 
 import numpy as np
 
@@ -60,6 +62,20 @@ FP64_PER_CLUSTER = 11         # the FP64 island as the method states it, per clu
 FP64_EXECUTED_PER_CLUSTER = 8 # FP64 lane-instructions the kernel executes per cluster (ncu): 2 (outward det) + 6 (inward)
 BYTES_PER_CLUSTER = 22        # 21 B read (x, y, z, sy2, sz2 f32 + row u8) + 1 B accept written
 BYTES_PER_TRACK = 108         # 8 B offset + 100 B results
+
+
+@contextmanager
+def host_timed():
+    """A host-timed region: Python's garbage collector off, as timeit does, so
+    that a collection of the interpreter's objects does not land inside a
+    timed step (the library's own work is unaffected)."""
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
 
 
 def dist_env():
@@ -489,11 +505,13 @@ def run_events(args, ws, rank, local, T, torch, dist, probe, leg: bool = False):
             fx.fit(host, hres)
         if dist:
             dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            fx.fit(host, hres)
-            _ = float(hres["chi2"][0])
-        dt = reduce_max(dist, torch, time.perf_counter() - t0)
+        with host_timed():
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                fx.fit(host, hres)
+                _ = float(hres["chi2"][0])
+            dt = time.perf_counter() - t0
+        dt = reduce_max(dist, torch, dt)
         e2e = {"value": nc_all * args.e2e_steps / dt, "unit": "clusters/s",
                "h2d_bytes_per_step": int(21 * nc + 8 * (nt + 1)), "d2h_bytes_per_step": int(100 * nt + nc),
                "ms_per_step": dt / args.e2e_steps * 1e3,
@@ -609,30 +627,31 @@ def run_serving(args, ws, rank, local, T, torch, dist, probe, leg: bool = False)
         with T.Fitter(device=local, hbm_budget_bytes=budget, max_slots=8) as fx:
             fx.wait(fx.submit(frames[0], res_for(0, frames[0])))  # warm-up: pool, streams, kernels
             out = {}
-            t0 = T.now() + 0.05
-            for i, a in enumerate(arr):
-                slot = i % len(ring)
-                if slot in out:
-                    tk, j = out.pop(slot)
+            with host_timed():
+                t0 = T.now() + 0.05
+                for i, a in enumerate(arr):
+                    slot = i % len(ring)
+                    if slot in out:
+                        tk, j = out.pop(slot)
+                        st, td = fx.wait(tk)
+                        assert st == T.DONE, st
+                        lat[j], t_done[j] = td - (t0 + arr[j]), td
+                    d = t0 + a - T.now()
+                    if d > 0:
+                        time.sleep(d)
+                    f = frames[pick[i]]
+                    out[slot] = (fx.submit(f, res_for(slot, f)), i)
+                for tk, j in out.values():
                     st, td = fx.wait(tk)
                     assert st == T.DONE, st
                     lat[j], t_done[j] = td - (t0 + arr[j]), td
-                d = t0 + a - T.now()
-                if d > 0:
-                    time.sleep(d)
-                f = frames[pick[i]]
-                out[slot] = (fx.submit(f, res_for(slot, f)), i)
-            for tk, j in out.values():
-                st, td = fx.wait(tk)
-                assert st == T.DONE, st
-                lat[j], t_done[j] = td - (t0 + arr[j]), td
             eng = fx.serve_stats()
         eng["parts_per_launch_mean"] = eng["parts"] / max(eng["launches"], 1)
         return lat, max(t_done) - (t0 + arr[0]), eng
 
     def sequential(arr):
         lat, t_end = [None] * len(arr), 0.0
-        with T.Fitter(device=local) as fx:
+        with T.Fitter(device=local) as fx, host_timed():
             fx.fit(frames[0], res_for(0, frames[0]))
             t0 = T.now() + 0.05
             for i, a in enumerate(arr):
@@ -1067,14 +1086,16 @@ def main():
             fx.fit(host, hres)
         if dist:
             dist.barrier()
-        t0 = time.perf_counter()
         step_ms = []
-        for _ in range(args.e2e_steps):
-            ts = time.perf_counter()
-            fx.fit(host, hres)
-            _ = float(hres["chi2"][0])  # the step's result read on the host
-            step_ms.append(round(1e3 * (time.perf_counter() - ts), 3))
-        dt = reduce_max(dist, torch, time.perf_counter() - t0)
+        with host_timed():
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                ts = time.perf_counter()
+                fx.fit(host, hres)
+                _ = float(hres["chi2"][0])  # the step's result read on the host
+                step_ms.append(round(1e3 * (time.perf_counter() - ts), 3))
+            dt = time.perf_counter() - t0
+        dt = reduce_max(dist, torch, dt)
         h2d_b, d2h_b = int(21 * nc + 8 * (nt + 1)), int(100 * nt + nc)
         # the same frame without x: its clusters lie on the pad-row planes, and
         # the library derives x from the rows on the device (17 B per cluster copied)
@@ -1085,11 +1106,12 @@ def main():
         for _ in range(max(3, args.warmup)):
             fx.fit(nox, hres)
         nox_ms = []
-        for _ in range(args.e2e_steps):
-            ts = time.perf_counter()
-            fx.fit(nox, hres)
-            _ = float(hres["chi2"][0])
-            nox_ms.append(round(1e3 * (time.perf_counter() - ts), 3))
+        with host_timed():
+            for _ in range(args.e2e_steps):
+                ts = time.perf_counter()
+                fx.fit(nox, hres)
+                _ = float(hres["chi2"][0])
+                nox_ms.append(round(1e3 * (time.perf_counter() - ts), 3))
         nox_s = reduce_max(dist, torch, sum(nox_ms) * 1e-3)
         nox_same = bool(torch.equal(ref_state.view(torch.int32), hres["state"].view(torch.int32))  # bitwise (NaN too)
                         and torch.equal(ref_accept, hres["accept"]))
