@@ -248,6 +248,9 @@ cudaError_t launch_residuals(const FitArgs &a, cudaStream_t stream);
 int fit_blocks_per_sm(int block);
 // tuned default residency (blocks per SM) for a block size
 int fit_default_blocks_per_sm(int block, bool variant);
-int fit_regs_per_thread(int block, bool variant, int blocks_per_sm);  // of the instantiation a handle launches
+// registers per thread of the instantiation a handle launches for frames of
+// more tracks than 4 blocks of 128 per SM hold (smaller frames run the
+// 4-block instantiation)
+int fit_regs_per_thread(int block, bool variant, int blocks_per_sm);
 
 }  // namespace tpcfit

@@ -258,6 +258,20 @@ def test_sorted_and_unsorted_orders_agree(T):
         assert np.array_equal(a[k], b[k], equal_nan=k in ('state', 'cov')), k
 
 
+def test_launch_shapes_bit_identical_on_a_large_frame(T):
+    """A frame with more tracks than 4 blocks of 128 per SM hold runs the
+    instantiation compiled for 5 resident blocks (fewer registers) by
+    default; 4 or 3 blocks per SM and blocks of 256 run others.  All give the
+    same bits: every operation's rounding is explicit."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f = tpcgen.generate("pbpb2m", n_tracks=4 * 128 * sms + 5_003)
+    ref = fit_gpu(T, f)  # the default: 5 blocks of 128 per SM
+    for bt, bps in ((128, 4), (128, 3), (256, 2)):
+        other = fit_gpu(T, f, block_threads=bt, blocks_per_sm=bps)
+        for k in ref:
+            assert np.array_equal(ref[k], other[k], equal_nan=k in ("state", "cov")), (bt, bps, k)
+
+
 def test_async_on_torch_stream_and_determinism(T):
     f = tpcgen.generate("detector50k", n_tracks=8_000)
     ref = fit_gpu(T, f)
